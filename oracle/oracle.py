@@ -1,0 +1,277 @@
+"""Python face of the CPU oracle (test infrastructure only).
+
+Wraps oracle/psi_oracle.c through ctypes and adds the few steps that are
+library routines: the stable sort of the key array (numpy's stable argsort),
+the per-tile ranges, and the FP64 query contraction of the decode step.
+
+Every function takes plain numpy arrays produced by the seeded scene
+generator; nothing here imports the CUDA package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+SPHERE, AABB, EXACT = 0, 1, 2
+ALPHA_MIN = 1.0 / 255.0
+T_EPS = 1e-4
+
+_lib = None
+_plant = 0
+
+
+def use_variant(plant: int = 0) -> None:
+    """Switch to a deliberately wrong build (plant > 0) or back to the real one.
+    Only the test that checks the pins catch planted mistakes calls this."""
+    global _lib, _plant
+    _plant = int(plant)
+    _lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build(plant=_plant)
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_double
+        L.or_bin_view.argtypes = [i64, P, P, P, P, P, P, f32, f32, i32, i32, i32, i32, P, P, P, P, P]
+        L.or_bin_view.restype = None
+        L.or_emit_view.argtypes = [i64, P, P, P, P, P, P, f32, f32, i32, i32, i32, i32,
+                                   ctypes.c_uint32, ctypes.c_uint32, P, P, i64]
+        L.or_emit_view.restype = i64
+        L.or_rho_opacity.argtypes = [f32]
+        L.or_rho_opacity.restype = f32
+        L.or_render.argtypes = [i64, P, P, P, P, P, P, P, i32, P, i32, P, P, i64, P, i32, f64,
+                                P, P, P, P, P, P, P, P]
+        L.or_render.restype = None
+        L.or_render_grad.argtypes = [i64, P, P, P, P, P, P, P, i32, P, i32, P, P, i64, P, i32, f64,
+                                     P, P, P, P, P, P, P, P, P, P]
+        L.or_render_grad.restype = None
+        L.or_pixel_walk.argtypes = [i64, P, P, P, P, P, P, i32, P, P, i32, i32, i32, f64, P, P, P, i32]
+        L.or_pixel_walk.restype = i32
+        L.or_num_threads.restype = i32
+        L.or_set_threads.argtypes = [i32]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+@dataclass
+class Opts:
+    """Render options shared by the oracle and the CUDA path (same meaning)."""
+    mode: int = EXACT
+    top_k: int = 0          # 0 = dense features
+    chi2: float = 9.0
+    z_near: float = 0.2
+    opacity_radius: bool = False
+    tile_w: int = 16
+    tile_h: int = 16
+    t_eps: float = T_EPS
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def rho_opacity(o: float) -> float:
+    return float(lib().or_rho_opacity(float(o)))
+
+
+def _surf32(s):
+    return (_c(s.mu, np.float32), _c(s.tu, np.float32), _c(s.tv, np.float32), _c(s.scale, np.float32),
+            _c(s.opacity, np.float32))
+
+
+def bin_view(s, cam, opts: Opts):
+    """Discrete (pinned float32) per-surfel results for one camera."""
+    mu, tu, tv, sc, o = _surf32(s)
+    n = s.n
+    camv = _c(cam.as_array(), np.float32)
+    count = np.zeros(n, np.uint32)
+    dbits = np.zeros(n, np.uint32)
+    r2 = np.zeros(n, np.float32)
+    rect = np.zeros((n, 4), np.int32)
+    ell = np.zeros((n, 9), np.float32)
+    lib().or_bin_view(n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(camv), opts.chi2, opts.z_near,
+                      int(opts.opacity_radius), int(opts.mode), opts.tile_w, opts.tile_h,
+                      _p(count), _p(dbits), _p(r2), _p(rect), _p(ell))
+    return dict(count=count, depth_bits=dbits, r2=r2, rect=rect, ell=ell, visible=rect[:, 0] >= 0)
+
+
+def tiles_per_view(cams, opts: Opts):
+    return [((c.width + opts.tile_w - 1) // opts.tile_w) * ((c.height + opts.tile_h - 1) // opts.tile_h) for c in cams]
+
+
+def emit_pairs(s, cams, opts: Opts):
+    """Unsorted (key, value) pairs of all views in emission order.
+
+    value = view * N + surfel; key = global tile << 32 | float bits of depth."""
+    mu, tu, tv, sc, o = _surf32(s)
+    n = s.n
+    keys_all, vals_all = [], []
+    base = 0
+    tpv = tiles_per_view(cams, opts)
+    for v, cam in enumerate(cams):
+        camv = _c(cam.as_array(), np.float32)
+        b = bin_view(s, cam, opts)
+        cap = int(b["count"].sum())
+        keys = np.zeros(max(cap, 1), np.uint64)
+        vals = np.zeros(max(cap, 1), np.uint32)
+        got = lib().or_emit_view(n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(camv), opts.chi2, opts.z_near,
+                                 int(opts.opacity_radius), int(opts.mode), opts.tile_w, opts.tile_h,
+                                 base, v * n, _p(keys), _p(vals), cap)
+        assert got == cap, (got, cap)
+        keys_all.append(keys[:cap])
+        vals_all.append(vals[:cap])
+        base += tpv[v]
+    return np.concatenate(keys_all), np.concatenate(vals_all)
+
+
+def sort_pairs(keys, vals):
+    """Stable sort by key (library routine: numpy's stable radix/merge sort)."""
+    perm = np.argsort(keys, kind="stable")
+    return keys[perm], vals[perm]
+
+
+def tile_ranges(sorted_keys, n_tiles_total):
+    """[n_tiles, 2] (start, end) of each global tile in the sorted key array."""
+    tiles = (sorted_keys >> np.uint64(32)).astype(np.int64)
+    idx = np.arange(n_tiles_total, dtype=np.int64)
+    start = np.searchsorted(tiles, idx, side="left")
+    end = np.searchsorted(tiles, idx, side="right")
+    return np.stack([start, end], 1).astype(np.uint32)
+
+
+def canonical_order(b):
+    """Non-culled surfels of one view sorted by (float32 depth bits, id)."""
+    ids = np.nonzero(b["visible"])[0]
+    return ids[np.lexsort((ids, b["depth_bits"][ids]))].astype(np.int32)
+
+
+def _surf64(s):
+    return tuple(_c(a, np.float64) for a in (s.mu, s.tu, s.tv, s.scale, s.opacity, s.rgb))
+
+
+def all_pixels(cam):
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    return np.stack([xs.reshape(-1), ys.reshape(-1)], 1).astype(np.int32)
+
+
+def render(s, cam, opts: Opts, feat=None, pixels=None, b=None):
+    """FP64 brute-force render of the given pixels ([P,2] x,y; default all).
+
+    feat: [N,D] array of the (dequantised) feature values, or None.
+    Returns dict with rgb [P,3], T [P], F [P,D], topk [P,K] (surfel ids in list
+    order, -1 padded), ncontrib, sumw, diag [P,6], hash."""
+    if b is None:
+        b = bin_view(s, cam, opts)
+    order = canonical_order(b)
+    r2 = b["r2"].astype(np.float64)
+    pix = all_pixels(cam) if pixels is None else _c(pixels, np.int32)
+    npix = pix.shape[0]
+    mu, tu, tv, sc, o, rgb = _surf64(s)
+    D = 0 if feat is None else int(feat.shape[1])
+    f64 = None if feat is None else _c(feat, np.float64)
+    K = int(opts.top_k)
+    out = dict(rgb=np.zeros((npix, 3)), T=np.zeros(npix), F=np.zeros((npix, max(D, 1))),
+               topk=np.full((npix, max(K, 1)), -1, np.int32), ncontrib=np.zeros(npix, np.int32),
+               sumw=np.zeros(npix), diag=np.zeros((npix, 6)), hash=np.zeros(npix, np.uint64))
+    camv = _c(cam.as_array(), np.float64)
+    lib().or_render(s.n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(rgb), _p(f64), D, _p(order), len(order),
+                    _p(r2), _p(camv), npix, _p(pix), K, opts.t_eps,
+                    _p(out["rgb"]), _p(out["T"]), _p(out["F"]) if D else None,
+                    _p(out["topk"]) if K > 0 else None, _p(out["ncontrib"]), _p(out["sumw"]), _p(out["diag"]),
+                    _p(out["hash"]))
+    if not D:
+        out["F"] = np.zeros((npix, 0))
+    out["pixels"] = pix
+    return out
+
+
+def pixel_walk(s, cam, opts: Opts, px: int, py: int, b=None, cap: int = 4096):
+    """Contributors of one pixel, front to back: dict(id, u, v, alpha, T, sel)."""
+    if b is None:
+        b = bin_view(s, cam, opts)
+    order = canonical_order(b)
+    r2 = b["r2"].astype(np.float64)
+    mu, tu, tv, sc, o, rgb = _surf64(s)
+    camv = _c(cam.as_array(), np.float64)
+    ids = np.zeros(cap, np.int32)
+    uvat = np.zeros((cap, 4))
+    sel = np.zeros(cap, np.uint8)
+    cnt = lib().or_pixel_walk(s.n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(order), len(order), _p(r2), _p(camv),
+                              int(px), int(py), int(opts.top_k), opts.t_eps, _p(ids), _p(uvat), _p(sel), cap)
+    cnt = min(cnt, cap)
+    return dict(id=ids[:cnt], u=uvat[:cnt, 0], v=uvat[:cnt, 1], alpha=uvat[:cnt, 2], T=uvat[:cnt, 3],
+                sel=sel[:cnt].astype(bool))
+
+
+def render_grad(s, cam, opts: Opts, gC, feat=None, gF=None, gT=None, pixels=None, b=None):
+    """FP64 gradient of L = sum gC.C + gF.F + gT.T over the given pixels."""
+    if b is None:
+        b = bin_view(s, cam, opts)
+    order = canonical_order(b)
+    r2 = b["r2"].astype(np.float64)
+    pix = all_pixels(cam) if pixels is None else _c(pixels, np.int32)
+    npix = pix.shape[0]
+    mu, tu, tv, sc, o, rgb = _surf64(s)
+    D = 0 if feat is None else int(feat.shape[1])
+    f64 = None if feat is None else _c(feat, np.float64)
+    n = s.n
+    g = dict(mu=np.zeros((n, 3)), tu=np.zeros((n, 3)), tv=np.zeros((n, 3)), scale=np.zeros((n, 2)),
+             opacity=np.zeros(n), rgb=np.zeros((n, 3)), feat=np.zeros((n, max(D, 1))))
+    camv = _c(cam.as_array(), np.float64)
+    gC = _c(gC, np.float64).reshape(npix, 3)
+    gF = None if (gF is None or D == 0) else _c(gF, np.float64).reshape(npix, D)
+    gT = None if gT is None else _c(gT, np.float64).reshape(npix)
+    lib().or_render_grad(n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(rgb), _p(f64), D, _p(order), len(order),
+                         _p(r2), _p(camv), npix, _p(pix), int(opts.top_k), opts.t_eps,
+                         _p(gC), _p(gF), _p(gT), _p(g["mu"]), _p(g["tu"]), _p(g["tv"]), _p(g["scale"]),
+                         _p(g["opacity"]), _p(g["rgb"]), _p(g["feat"]) if D else None)
+    if not D:
+        g["feat"] = np.zeros((n, 0))
+    return g
+
+
+def loss(out, gC, gF=None, gT=None):
+    """L = sum gC.C + gF.F + gT.T of a render result (FP64)."""
+    L = float(np.sum(out["rgb"] * np.asarray(gC, np.float64).reshape(out["rgb"].shape)))
+    if gF is not None and out["F"].shape[1]:
+        L += float(np.sum(out["F"] * np.asarray(gF, np.float64).reshape(out["F"].shape)))
+    if gT is not None:
+        L += float(np.sum(out["T"] * np.asarray(gT, np.float64).reshape(out["T"].shape)))
+    return L
+
+
+def decode(F, Q, T, empty_eps: float = 1e-4):
+    """FP64 query contraction (library matmul) and argmax, lowest index on ties.
+
+    F: [P,D] feature values (as the GPU stored them), Q: [Q,D], T: [P].
+    Returns (ids [P] int32, logits [P,Q] float64, gap [P] top-2 logit gap)."""
+    L = np.asarray(F, np.float64) @ np.asarray(Q, np.float64).T
+    ids = np.argmax(L, axis=1).astype(np.int32)
+    if L.shape[1] > 1:
+        part = -np.sort(-L, axis=1)
+        gap = part[:, 0] - part[:, 1]
+    else:
+        gap = np.full(L.shape[0], np.inf)
+    empty = (1.0 - np.asarray(T, np.float64)) < empty_eps
+    ids[empty] = -1
+    return ids, L, gap
