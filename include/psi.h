@@ -1,0 +1,237 @@
+/*
+ * psi.h -- C ABI of libpsi, a GB300 (sm_103a) implementation of the rendering
+ * hot path of "Psi-Map: Panoptic Surface Integrated Mapping Enables Real2Sim
+ * Transfer" (arXiv 2604.10982): tile-based differentiable rasterisation of 2D
+ * Gaussian surfels carrying RGB and a D-dimensional feature, with Precise Tile
+ * Intersection and Top-K Hard Selection (Sec. 5), and the query decode of the
+ * rendered feature map (Sec. 4.1, Eq. 4).
+ *
+ * General rules for every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller, unless a
+ *    comment says "host". The library never frees caller memory.
+ *  - Work is enqueued asynchronously on the caller's stream `stream`
+ *    (a cudaStream_t; NULL = legacy default stream). No entry point
+ *    synchronises the host, so a whole frame can be captured in a CUDA graph.
+ *  - Return value: PSI_OK or an error code; psi_last_error(ctx) then holds a
+ *    readable message. Host-side argument checks return PSI_ERR_INVALID_ARG
+ *    (or PSI_ERR_UNSUPPORTED) before anything is enqueued.
+ *  - Errors found on the device (pair-buffer overflow, a bounded wait that gave
+ *    up) are OR-ed into the context's device status word; read and clear it
+ *    with psi_status_fetch() after the stream has run.
+ *  - Camera convention: OpenCV axes (x right, y down, z forward),
+ *    x_cam = R x_world + t, pixel (px,py) samples the point (px+1/2, py+1/2).
+ *  - Views are concatenated: view v owns tiles [tile_base(v), tile_base(v) +
+ *    tiles_x*tiles_y) and pixels [pix_base(v), pix_base(v) + W*H), both
+ *    prefix sums over the views in order (see psi_view_layout).
+ *  - A "record" is one (view, surfel) pair with index r = v*N + i.
+ */
+#ifndef PSI_H
+#define PSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psi_ctx psi_ctx;
+typedef struct CUstream_st *psi_stream; /* same type as cudaStream_t */
+
+enum psi_status {
+    PSI_OK = 0,
+    PSI_ERR_INVALID_ARG = 1,
+    PSI_ERR_CUDA = 2,
+    PSI_ERR_CAPACITY = 3,  /* device: more (tile, surfel) pairs than the key buffer holds */
+    PSI_ERR_TIMEOUT = 4,   /* device: a bounded wait gave up (the results are invalid) */
+    PSI_ERR_UNSUPPORTED = 5
+};
+
+/* Tile-intersection modes (Sec. 5, "Precise Tile Intersection"):
+ *  SPHERE: square of radius chi*sqrt(lambda_max(Sigma')) -- the isotropic
+ *          bounding sphere the paper replaces (its "Baseline" row);
+ *  AABB:   the paper's box with half-widths sqrt(chi^2 Sigma'_11),
+ *          sqrt(chi^2 Sigma'_22) of the projected covariance;
+ *  EXACT:  per tile row, only the tiles whose pixel-centre columns meet the
+ *          projected ellipse itself. */
+enum psi_isect_mode { PSI_ISECT_SPHERE = 0, PSI_ISECT_AABB = 1, PSI_ISECT_EXACT = 2 };
+
+/* Storage types of the per-surfel feature table (FP32 accumulation always). */
+enum psi_dtype { PSI_F32 = 0, PSI_BF16 = 1, PSI_FP8_E4M3 = 2 };
+
+#define PSI_MAX_VIEWS 64
+#define PSI_RECORD_BYTES 64     /* render record per (view, surfel) */
+#define PSI_BIN_RECORD_BYTES 32 /* binning record per (view, surfel) */
+#define PSI_MAX_TOPK 32
+
+/* Surfels (Sec. 3.1): a 2D Gaussian in the plane through mu spanned by the
+ * tangent axes t_u, t_v with scales (s_u, s_v): P(u,v) = mu + s_u u t_u +
+ * s_v v t_v; opacity o; colour c. All float32, row-major, N rows. */
+typedef struct {
+    const float *mu;      /* [N,3] */
+    const float *tu;      /* [N,3] */
+    const float *tv;      /* [N,3] */
+    const float *scale;   /* [N,2] (s_u, s_v) */
+    const float *opacity; /* [N] */
+    const float *rgb;     /* [N,3] */
+    int64_t n;
+} psi_surfels;
+
+/* Pinhole camera (host struct). */
+typedef struct {
+    float R[9];  /* row-major world->camera rotation */
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} psi_camera;
+
+/* Per-surfel features f_i (Sec. 4.1): [N, dim] row-major in `dtype`.
+ * Value of channel c is q[i,c] * scale[c] (scale may be NULL for F32/BF16,
+ * meaning 1). dim must be a multiple of 8 and at most 256; rows must start on
+ * 16-byte boundaries. */
+typedef struct {
+    const void *data;
+    const float *scale; /* [dim] or NULL */
+    int32_t dtype;      /* enum psi_dtype */
+    int32_t dim;
+} psi_features;
+
+/* Options (host struct). Defaults: see psi_default_opts. */
+typedef struct {
+    int32_t mode;           /* enum psi_isect_mode */
+    int32_t top_k;          /* K of Top-K Hard Selection (Sec. 5); 0 = dense features */
+    float chi2;             /* squared support radius in (u,v) units (paper: "e.g. 3 sigma" -> 9) */
+    float z_near;           /* near plane; the whole support disc must lie beyond it */
+    int32_t opacity_radius; /* 1: shrink the radius to where o*exp(-d^2/2) reaches 1/255 */
+    int32_t tile_w, tile_h; /* tile size in pixels (16x16 supported) */
+    float t_eps;            /* stop a pixel after the surfel that takes T below this */
+} psi_render_opts;
+
+/* Forward outputs (device pointers; NULL = not written unless stated). Pixel p of
+ * view v is at index pix_base(v) + py*W + px.
+ *  rgb:      [3][P_total] planar per channel (channel c at c*P_total + p); required
+ *  T:        [P_total] final transmittance; required
+ *  n_last:   [P_total] int32, 1 + list position of the last surfel composited (0: none)
+ *  F:        [P_total, D] feature map in F_dtype (PSI_F32 or PSI_BF16)
+ *  topk_ids: [P_total, K] int32 surfel ids of the selected set in list order, -1 padded */
+typedef struct {
+    float *rgb;
+    float *T;
+    int32_t *n_last;
+    void *F;
+    int32_t F_dtype;
+    int32_t *topk_ids;
+} psi_fwd_out;
+
+/* Gradients (device, float32, ACCUMULATED into: the caller zeroes them). Any
+ * member may be NULL to skip it (feat is skipped automatically without g_F). */
+typedef struct {
+    float *mu;      /* [N,3] */
+    float *tu;      /* [N,3] */
+    float *tv;      /* [N,3] */
+    float *scale;   /* [N,2] */
+    float *opacity; /* [N] */
+    float *rgb;     /* [N,3] */
+    float *feat;    /* [N,D] gradient w.r.t. the dequantised feature values */
+} psi_grads;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (allocates a 16-byte device status
+ * word). *out receives the handle. */
+int psi_ctx_create(psi_ctx **out, int device);
+void psi_ctx_destroy(psi_ctx *ctx);
+/* Message of the last failing call on ctx (never NULL; "" if none). */
+const char *psi_last_error(const psi_ctx *ctx);
+/* Synchronises `stream`, copies the device status word to *status_out
+ * (0 = clean, else a PSI_ERR_* code) and *required_pairs (the pair count a
+ * capacity overflow needed; may be NULL), then clears the word. */
+int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *required_pairs);
+/* Fill *o with the defaults: EXACT, K=0, chi2=9, z_near=0.2, no opacity
+ * radius, 16x16 tiles, t_eps=1e-4. */
+void psi_default_opts(psi_render_opts *o);
+/* Host helper: tile_base[n_views+1] and pix_base[n_views+1] (host arrays). */
+int psi_view_layout(const psi_camera *cams, int n_views, const psi_render_opts *o, int64_t *tile_base,
+                    int64_t *pix_base);
+
+/* ---- workspace sizes (bytes of caller-allocated scratch, 256-B aligned) -- */
+int psi_intersect_workspace_size(int64_t n_records, size_t *bytes);
+int psi_sort_workspace_size(int64_t capacity, size_t *bytes);
+int psi_render_bwd_workspace_size(int64_t n_records, size_t *bytes);
+
+/* ---- a1: projection and ray-splat setup --------------------------------
+ * Per (view, surfel): camera transform, the pixel-homogeneous 3x3 map M of the
+ * surfel plane (the ray-splat intersection of Sec. 3.1 in homogeneous form),
+ * culling (opacity < 1/255, or any part of the support disc nearer than
+ * z_near), the support radius, the ellipse bounds of the projected covariance
+ * (Sec. 5, Precise Tile Intersection) and the tile count of `o->mode`.
+ *  records:       [n_views*N] x PSI_RECORD_BYTES, 64-byte aligned (written for visible records)
+ *  bin_records:   [n_views*N] x PSI_BIN_RECORD_BYTES, 16-byte aligned
+ *  tiles_touched: [n_views*N] uint32, 0 for culled records
+ * cams is a HOST array of n_views (<= PSI_MAX_VIEWS) cameras. */
+int psi_project_surfels(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cams, int n_views,
+                        const psi_render_opts *o, void *records, void *bin_records, uint32_t *tiles_touched,
+                        psi_stream stream);
+
+/* ---- a2: tile intersection and key emission (Sec. 5) -------------------
+ * Exclusive scan of tiles_touched, then one (key, value) pair per (tile,
+ * record): key = global_tile << 32 | float bits of the camera depth, value =
+ * record index; records in index order, tiles row-major within a record.
+ *  keys, vals:  [capacity]; d_num_pairs: device int64 receiving the pair count
+ *  workspace:   psi_intersect_workspace_size(n_views*N) bytes
+ * If the count exceeds capacity, pairs beyond it are dropped, *d_num_pairs is
+ * clamped to capacity and PSI_ERR_CAPACITY is raised on the device. */
+int psi_intersect_tiles(psi_ctx *ctx, const psi_camera *cams, int n_views, const psi_render_opts *o,
+                        int64_t n_surfels, const void *bin_records, const uint32_t *tiles_touched, uint64_t *keys,
+                        uint32_t *vals, int64_t capacity, int64_t *d_num_pairs, void *workspace,
+                        size_t workspace_bytes, psi_stream stream);
+
+/* ---- a3: key sort and tile ranges ----------------------------------------
+ * Stable LSD radix sort of the first *d_num_pairs (key, value) pairs on key
+ * bits [begin_bit, end_bit) (in place: results end in keys/vals), then
+ * tile_ranges[2*t] = start, [2*t+1] = end of global tile t (0,0 if empty).
+ * Pass begin_bit=0, end_bit=32+ceil(log2(n_tiles_total)) for the full order.
+ *  workspace: psi_sort_workspace_size(capacity) bytes. */
+int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity,
+                  int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *workspace,
+                  size_t workspace_bytes, psi_stream stream);
+
+/* ---- a4: per-tile compositing with Top-K Hard Selection -----------------
+ * Per pixel, front to back over its tile's list: alpha = min(0.99, o exp(-(u^2
+ * +v^2)/2)) (Sec. 3.1), skipped if u^2+v^2 > r^2 or alpha < 1/255; RGB blended
+ * densely with Eq. (1); the K largest weights omega_j = alpha_j T_j are kept
+ * and F = sum_{j in Top-K} f_j omega_j (Sec. 5), summed in list order;
+ * stop after the surfel that takes T below t_eps. K=0: dense features.
+ * f may be NULL (RGB only). records/vals/tile_ranges come from a1-a3 with the
+ * same cams and opts. */
+int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
+                   const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
+                   const psi_render_opts *o, const psi_fwd_out *out, psi_stream stream);
+
+/* ---- a5: adjoint of a4 ----------------------------------------------------
+ * Recomputes the front-to-back pass (and hence the same Top-K sets), then walks
+ * back to front with suffix sums: dL/dalpha_j = T_j s_j - (sum_{k>j} omega_k
+ * s_k + T_final g_T)/(1 - alpha_j), s_j = <gC, c_j> + [j in K]<gF, f_j>, and
+ * chains through alpha = o G, (u,v) of the homogeneous ray-splat map, to mu,
+ * t_u, t_v, s, o; also dL/dc, dL/df. g_F and g_T may be NULL.
+ *  g_rgb: [3][P_total] planar; g_F: [P_total, D] float32; g_T: [P_total]
+ *  workspace: psi_render_bwd_workspace_size(n_views*N) bytes. */
+int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
+                   const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
+                   const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
+                   const psi_grads *grads, void *workspace, size_t workspace_bytes, psi_stream stream);
+
+/* ---- a6: query decode (Sec. 4.1, Eq. 4 without the monotone sigmoid) -----
+ * logits[p,q] = sum_c F[p,c] Q[q,c] on the tensor cores (BF16 in, FP32
+ * accumulate), ids[p] = argmax_q (lowest q on ties), or -1 where 1 - T[p] <
+ * 1e-4 (nothing rendered).
+ *  F: [n_pix, D] BF16, 16-byte aligned rows; Q: [n_q, D] BF16; D in {64,128};
+ *  1 <= n_q <= 128; T: [n_pix] float; ids: [n_pix] int32; logits: [n_pix, n_q]
+ *  BF16 or NULL. */
+int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
+                       int32_t *ids, void *logits, psi_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSI_H */

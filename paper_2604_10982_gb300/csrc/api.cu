@@ -1,0 +1,352 @@
+// extern "C" entry points of libpsi: argument checks, context, status word.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+struct psi_ctx {
+    int device;
+    psi::DevStatus *status;
+    char err[512];
+};
+
+namespace {
+
+int fail(psi_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(psi_ctx *ctx, const char *where, cudaError_t e)
+{
+    return fail(ctx, PSI_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_opts(psi_ctx *ctx, const psi_render_opts *o)
+{
+    if (!o) return fail(ctx, PSI_ERR_INVALID_ARG, "opts is NULL");
+    if (o->mode < PSI_ISECT_SPHERE || o->mode > PSI_ISECT_EXACT) return fail(ctx, PSI_ERR_INVALID_ARG, "bad mode %d", o->mode);
+    if (o->tile_w != 16 || o->tile_h != 16)
+        return fail(ctx, PSI_ERR_UNSUPPORTED, "tile %dx%d unsupported (16x16 only)", o->tile_w, o->tile_h);
+    if (o->top_k < 0 || o->top_k > PSI_MAX_TOPK) return fail(ctx, PSI_ERR_INVALID_ARG, "top_k %d out of [0,32]", o->top_k);
+    if (!(o->chi2 > 0.0f) || !(o->chi2 < 1e4f)) return fail(ctx, PSI_ERR_INVALID_ARG, "chi2 must be in (0, 1e4)");
+    if (!(o->z_near > 0.0f)) return fail(ctx, PSI_ERR_INVALID_ARG, "z_near must be > 0");
+    if (!(o->t_eps >= 0.0f) || !(o->t_eps < 1.0f)) return fail(ctx, PSI_ERR_INVALID_ARG, "t_eps must be in [0,1)");
+    return PSI_OK;
+}
+
+int check_cams(psi_ctx *ctx, const psi_camera *cams, int n_views, const psi_render_opts *o)
+{
+    if (!cams) return fail(ctx, PSI_ERR_INVALID_ARG, "cams is NULL");
+    if (n_views < 1 || n_views > PSI_MAX_VIEWS)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "n_views %d out of [1,%d]", n_views, PSI_MAX_VIEWS);
+    int64_t tiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const psi_camera &c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 32768 || c.height > 32768)
+            return fail(ctx, PSI_ERR_INVALID_ARG, "view %d: size %dx%d out of [1,32768]", v, c.width, c.height);
+        if (!(c.fx > 0.0f) || !(c.fy > 0.0f)) return fail(ctx, PSI_ERR_INVALID_ARG, "view %d: focal must be > 0", v);
+        tiles += static_cast<int64_t>((c.width + o->tile_w - 1) / o->tile_w) * ((c.height + o->tile_h - 1) / o->tile_h);
+    }
+    if (tiles >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "too many tiles");
+    return PSI_OK;
+}
+
+int check_surfels(psi_ctx *ctx, const psi_surfels *s)
+{
+    if (!s) return fail(ctx, PSI_ERR_INVALID_ARG, "surfels is NULL");
+    if (s->n < 0 || s->n >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "surfel count out of range");
+    if (s->n > 0 && (!s->mu || !s->tu || !s->tv || !s->scale || !s->opacity || !s->rgb))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "a surfel array is NULL");
+    return PSI_OK;
+}
+
+int check_feat(psi_ctx *ctx, const psi_features *f, psi::FeatView &fv)
+{
+    fv = psi::FeatView{nullptr, nullptr, PSI_F32, 0};
+    if (!f || !f->data) return PSI_OK;
+    if (f->dtype != PSI_F32 && f->dtype != PSI_BF16 && f->dtype != PSI_FP8_E4M3)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "bad feature dtype %d", f->dtype);
+    if (f->dim < 16 || f->dim > 256 || f->dim % 16 != 0)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "feature dim %d must be a multiple of 16 in [16,256]", f->dim);
+    if (!aligned(f->data, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "feature rows must be 16-byte aligned");
+    fv = psi::FeatView{f->data, f->scale, f->dtype, f->dim};
+    return PSI_OK;
+}
+
+int64_t n_tiles_of(const psi_camera *cams, int n_views, const psi_render_opts *o)
+{
+    int64_t t = 0;
+    for (int v = 0; v < n_views; ++v)
+        t += static_cast<int64_t>((cams[v].width + o->tile_w - 1) / o->tile_w) * ((cams[v].height + o->tile_h - 1) / o->tile_h);
+    return t;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+} // namespace
+
+extern "C" {
+
+int psi_ctx_create(psi_ctx **out, int device)
+{
+    if (!out) return PSI_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return PSI_ERR_INVALID_ARG;
+    psi_ctx *c = new (std::nothrow) psi_ctx;
+    if (!c) return PSI_ERR_CUDA;
+    c->device = device;
+    c->status = nullptr;
+    c->err[0] = 0;
+    DeviceGuard g(device);
+    cudaError_t e = cudaMalloc(&c->status, sizeof(psi::DevStatus));
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(psi::DevStatus));
+    if (e != cudaSuccess) {
+        delete c;
+        return PSI_ERR_CUDA;
+    }
+    *out = c;
+    return PSI_OK;
+}
+
+void psi_ctx_destroy(psi_ctx *ctx)
+{
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        if (ctx->status) cudaFree(ctx->status);
+    }
+    delete ctx;
+}
+
+const char *psi_last_error(const psi_ctx *ctx) { return ctx ? ctx->err : "NULL context"; }
+
+int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *required_pairs)
+{
+    if (!ctx || !status_out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard g(ctx->device);
+    psi::DevStatus h{};
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "psi_status_fetch", e);
+    e = cudaMemcpy(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, "psi_status_fetch", e);
+    e = cudaMemset(ctx->status, 0, sizeof(h));
+    if (e != cudaSuccess) return cuda_fail(ctx, "psi_status_fetch", e);
+    int code = PSI_OK;
+    // report the most severe: timeout, then capacity, then invalid argument
+    if (h.flags & (1 << PSI_ERR_TIMEOUT))
+        code = PSI_ERR_TIMEOUT;
+    else if (h.flags & (1 << PSI_ERR_CAPACITY))
+        code = PSI_ERR_CAPACITY;
+    else if (h.flags & (1 << PSI_ERR_INVALID_ARG))
+        code = PSI_ERR_INVALID_ARG;
+    *status_out = code;
+    if (required_pairs) *required_pairs = static_cast<int64_t>(h.required_pairs);
+    return PSI_OK;
+}
+
+void psi_default_opts(psi_render_opts *o)
+{
+    if (!o) return;
+    o->mode = PSI_ISECT_EXACT;
+    o->top_k = 0;
+    o->chi2 = 9.0f;
+    o->z_near = 0.2f;
+    o->opacity_radius = 0;
+    o->tile_w = 16;
+    o->tile_h = 16;
+    o->t_eps = 1e-4f;
+}
+
+int psi_view_layout(const psi_camera *cams, int n_views, const psi_render_opts *o, int64_t *tile_base, int64_t *pix_base)
+{
+    if (!cams || !o || n_views < 0 || !tile_base || !pix_base) return PSI_ERR_INVALID_ARG;
+    if (o->tile_w < 1 || o->tile_h < 1) return PSI_ERR_INVALID_ARG;
+    tile_base[0] = 0;
+    pix_base[0] = 0;
+    for (int v = 0; v < n_views; ++v) {
+        tile_base[v + 1] = tile_base[v] + static_cast<int64_t>((cams[v].width + o->tile_w - 1) / o->tile_w) *
+                                              ((cams[v].height + o->tile_h - 1) / o->tile_h);
+        pix_base[v + 1] = pix_base[v] + static_cast<int64_t>(cams[v].width) * cams[v].height;
+    }
+    return PSI_OK;
+}
+
+int psi_intersect_workspace_size(int64_t n_records, size_t *bytes)
+{
+    if (!bytes || n_records < 0) return PSI_ERR_INVALID_ARG;
+    *bytes = psi::intersect_workspace_bytes(n_records);
+    return PSI_OK;
+}
+
+int psi_sort_workspace_size(int64_t capacity, size_t *bytes)
+{
+    if (!bytes || capacity < 0) return PSI_ERR_INVALID_ARG;
+    *bytes = psi::sort_workspace_bytes(capacity);
+    return PSI_OK;
+}
+
+int psi_render_bwd_workspace_size(int64_t n_records, size_t *bytes)
+{
+    if (!bytes || n_records < 0) return PSI_ERR_INVALID_ARG;
+    *bytes = psi::render_bwd_workspace_bytes(n_records);
+    return PSI_OK;
+}
+
+int psi_project_surfels(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cams, int n_views,
+                        const psi_render_opts *o, void *records, void *bin_records, uint32_t *tiles_touched,
+                        psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o)) || (rc = check_surfels(ctx, s))) return rc;
+    if (s->n > 0 && (!records || !bin_records || !tiles_touched))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "output array is NULL");
+    if (!aligned(records, 64) || !aligned(bin_records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 64-byte aligned, bin records 16");
+    if (s->n * n_views >= (int64_t(1) << 32)) return fail(ctx, PSI_ERR_INVALID_ARG, "n_views * N must be < 2^32");
+    DeviceGuard g(ctx->device);
+    psi::FrameParams fp;
+    psi::fill_frame_params(fp, cams, n_views, o, s->n);
+    cudaError_t e = psi::launch_project(fp, *s, static_cast<float4 *>(records), static_cast<float4 *>(bin_records),
+                                        tiles_touched, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_project_surfels", e);
+}
+
+int psi_intersect_tiles(psi_ctx *ctx, const psi_camera *cams, int n_views, const psi_render_opts *o,
+                        int64_t n_surfels, const void *bin_records, const uint32_t *tiles_touched, uint64_t *keys,
+                        uint32_t *vals, int64_t capacity, int64_t *d_num_pairs, void *workspace,
+                        size_t workspace_bytes, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o))) return rc;
+    if (n_surfels < 0 || n_surfels * n_views >= (int64_t(1) << 32))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "n_views * N must be in [0, 2^32)");
+    if (capacity < 0 || capacity >= (int64_t(1) << 32)) return fail(ctx, PSI_ERR_INVALID_ARG, "capacity must be in [0, 2^32)");
+    if (!d_num_pairs || (capacity > 0 && (!keys || !vals))) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL output");
+    if (n_surfels > 0 && (!bin_records || !tiles_touched)) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
+    const int64_t R = n_surfels * n_views;
+    const size_t need = psi::intersect_workspace_bytes(R);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
+    DeviceGuard g(ctx->device);
+    psi::FrameParams fp;
+    psi::fill_frame_params(fp, cams, n_views, o, n_surfels);
+    cudaError_t e = psi::launch_intersect(fp, static_cast<const float4 *>(bin_records), tiles_touched, keys, vals,
+                                          capacity, d_num_pairs, workspace, ctx->status,
+                                          reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_intersect_tiles", e);
+}
+
+int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity,
+                  int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *workspace,
+                  size_t workspace_bytes, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (begin_bit < 0 || end_bit > 64 || begin_bit >= end_bit)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "need 0 <= begin_bit < end_bit <= 64");
+    if (capacity < 0 || capacity >= (int64_t(1) << 32)) return fail(ctx, PSI_ERR_INVALID_ARG, "capacity must be in [0, 2^32)");
+    if (!d_num_pairs || (capacity > 0 && (!keys || !vals))) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (n_tiles_total < 0 || (n_tiles_total > 0 && !tile_ranges)) return fail(ctx, PSI_ERR_INVALID_ARG, "bad tile ranges");
+    const size_t need = psi::sort_workspace_bytes(capacity);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_sort(keys, vals, d_num_pairs, capacity, begin_bit, end_bit, tile_ranges, n_tiles_total,
+                                     workspace, ctx->status, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_sort_keys", e);
+}
+
+int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
+                   const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
+                   const psi_render_opts *o, const psi_fwd_out *out, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o))) return rc;
+    psi::FeatView fv;
+    if ((rc = check_feat(ctx, f, fv))) return rc;
+    if (!out || !out->rgb || !out->T) return fail(ctx, PSI_ERR_INVALID_ARG, "out.rgb and out.T are required");
+    if (out->F && out->F_dtype != PSI_F32 && out->F_dtype != PSI_BF16)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "F_dtype must be PSI_F32 or PSI_BF16");
+    if (out->F && !aligned(out->F, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "out.F must be 16-byte aligned");
+    if (!records || !vals || !tile_ranges) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
+    if (!aligned(records, 64)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 64-byte aligned");
+    if (n_surfels < 0) return fail(ctx, PSI_ERR_INVALID_ARG, "n_surfels < 0");
+    DeviceGuard g(ctx->device);
+    psi::FrameParams fp;
+    psi::fill_frame_params(fp, cams, n_views, o, n_surfels);
+    cudaError_t e = psi::launch_render_fwd(fp, fv, static_cast<const float4 *>(records), vals, tile_ranges, *out,
+                                           ctx->status, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_render_fwd", e);
+}
+
+int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
+                   const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
+                   const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
+                   const psi_grads *grads, void *workspace, size_t workspace_bytes, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o)) || (rc = check_surfels(ctx, s))) return rc;
+    psi::FeatView fv;
+    if ((rc = check_feat(ctx, f, fv))) return rc;
+    if (!records || !vals || !tile_ranges || !g_rgb || !grads) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
+    if (!aligned(records, 64)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 64-byte aligned");
+    if (g_F && !fv.data) return fail(ctx, PSI_ERR_INVALID_ARG, "g_F given without features");
+    const size_t need = psi::render_bwd_workspace_bytes(s->n * n_views);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
+    DeviceGuard g(ctx->device);
+    psi::FrameParams fp;
+    psi::fill_frame_params(fp, cams, n_views, o, s->n);
+    cudaError_t e = psi::launch_render_bwd(fp, *s, fv, static_cast<const float4 *>(records), vals, tile_ranges, g_rgb,
+                                           g_F, g_T, *grads, workspace, ctx->status,
+                                           reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_render_bwd", e);
+}
+
+int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
+                       int32_t *ids, void *logits, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (n_pix < 0 || n_pix >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "n_pix out of range");
+    if (D != 64 && D != 128) return fail(ctx, PSI_ERR_UNSUPPORTED, "D must be 64 or 128");
+    if (n_q < 1 || n_q > 128) return fail(ctx, PSI_ERR_INVALID_ARG, "n_q must be in [1,128]");
+    if (n_pix > 0 && (!F || !Q || !T || !ids)) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned(F, 16) || !aligned(Q, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "F and Q must be 16-byte aligned");
+    if (logits && (!aligned(logits, 4) || (n_q % 2) != 0))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "logits need an even n_q and 4-byte alignment");
+    if (n_pix == 0) return PSI_OK;
+    DeviceGuard g(ctx->device);
+    const char *why = nullptr;
+    cudaError_t e = psi::launch_decode(F, n_pix, D, Q, n_q, T, ids, logits, ctx->status,
+                                       reinterpret_cast<cudaStream_t>(stream), &why);
+    if (why) return fail(ctx, PSI_ERR_CUDA, "psi_decode_queries: %s", why);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_decode_queries", e);
+}
+
+} // extern "C"

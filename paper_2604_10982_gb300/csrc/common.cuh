@@ -1,0 +1,188 @@
+// Internal declarations shared by the libpsi translation units (sm_103a only).
+#pragma once
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/psi.h"
+
+namespace psi {
+
+// Device status word layout (see psi_status_fetch): [0] OR of error codes as
+// bits (1 << code), [1] unused, [2..3] int64 pairs required on overflow.
+struct DevStatus {
+    int32_t flags;
+    int32_t pad;
+    unsigned long long required_pairs;
+};
+
+__device__ __forceinline__ void raise_status(DevStatus *st, int code)
+{
+    if (st) atomicOr(&st->flags, 1 << code);
+}
+
+struct ViewParams {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    int32_t tiles_x, tiles_y;
+    uint32_t tile_base;
+    int32_t pad;
+    int64_t pix_base;
+};
+
+struct FrameParams {
+    int32_t n_views;
+    int32_t mode;
+    int64_t n;          // surfels
+    int32_t tile_w, tile_h;
+    float chi2, z_near, t_eps;
+    int32_t opacity_radius;
+    int32_t top_k;
+    uint32_t n_tiles_total;
+    int64_t n_pix_total;
+    ViewParams v[PSI_MAX_VIEWS];
+};
+
+// view that owns global tile t (views are few: linear scan)
+__device__ __forceinline__ int view_of_tile(const FrameParams &fp, uint32_t t)
+{
+    int v = 0;
+    for (int k = 1; k < fp.n_views; ++k)
+        if (t >= fp.v[k].tile_base) v = k;
+    return v;
+}
+
+// ---------------------------------------------------------------- waits
+// Every spin in this library is bounded by wall time read from %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull; // 1 s
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; returns false (and raises TIMEOUT) on give-up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DevStatus *st)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs) {
+            raise_status(st, PSI_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 1D bulk copy global -> shared through the TMA engine, completion counted on bar.
+__device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gsrc, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- launchers
+// (host side; defined in the kernel translation units)
+void fill_frame_params(FrameParams &fp, const psi_camera *cams, int n_views, const psi_render_opts *o, int64_t n);
+
+cudaError_t launch_project(const FrameParams &fp, const psi_surfels &s, float4 *records, float4 *bin_records,
+                           uint32_t *tiles_touched, cudaStream_t st);
+
+size_t intersect_workspace_bytes(int64_t n_records);
+cudaError_t launch_intersect(const FrameParams &fp, const float4 *bin_records, const uint32_t *tiles_touched,
+                             uint64_t *keys, uint32_t *vals, int64_t capacity, int64_t *d_num_pairs, void *ws,
+                             DevStatus *status, cudaStream_t st);
+
+size_t sort_workspace_bytes(int64_t capacity);
+cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity, int begin_bit,
+                        int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *ws, DevStatus *status,
+                        cudaStream_t st);
+
+struct FeatView {
+    const void *data;
+    const float *scale;
+    int dtype;
+    int dim;
+};
+
+cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const float4 *records, const uint32_t *vals,
+                              const uint32_t *ranges, const psi_fwd_out &out, DevStatus *status, cudaStream_t st);
+
+size_t render_bwd_workspace_bytes(int64_t n_records);
+cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
+                              const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
+                              const float *g_T, const psi_grads &g, void *ws, DevStatus *status, cudaStream_t st);
+
+cudaError_t launch_decode(const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T, int32_t *ids,
+                          void *logits, DevStatus *status, cudaStream_t st, const char **why);
+
+// Exclusive scan of uint32 counts into uint64 offsets (reduce-then-scan,
+// spin-free). Writes the total to *d_total (uint64). ws: scan_workspace_bytes(n).
+size_t scan_workspace_bytes(int64_t n);
+cudaError_t launch_scan_u32(const uint32_t *in, unsigned long long *out, int64_t n, unsigned long long *d_total,
+                            void *ws, cudaStream_t st);
+
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+} // namespace psi

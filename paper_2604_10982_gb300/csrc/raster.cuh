@@ -1,0 +1,194 @@
+// Per-pixel surfel evaluation shared by the forward (a4) and adjoint (a5)
+// compositing kernels, and the TMA staging of tile-list batches.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace psi {
+namespace raster {
+
+constexpr int kTile = 16;    // 16x16 pixels per CTA, one thread per pixel
+constexpr int kThreads = 256;
+constexpr int kBatch = 256;  // records staged per batch
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kNegHalfLog2e = -0.72134752044448170f; // -log2(e)/2: exp(-d2/2) = 2^(d2 * k)
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Staged render record after the per-tile transform: q = A (lx, ly, 1) with
+// (lx, ly) the pixel's integer offset inside the tile.
+struct Rec {
+    float a00, a01, c0, a10, a11, c1, a20, a21, c2;
+    float o, r2;
+};
+
+__device__ __forceinline__ Rec load_rec(const float4 *r)
+{
+    const float4 x = r[0], y = r[1], z = r[2], w = r[3];
+    Rec q;
+    q.a00 = x.x; q.a01 = x.y; q.c0 = x.z; q.a10 = x.w;
+    q.a11 = y.x; q.c1 = y.y; q.a20 = y.z; q.a21 = y.w;
+    q.c2 = z.x; q.o = z.w; q.r2 = w.x;
+    return q;
+}
+
+struct Eval {
+    float q0, q1, q2, d2, G, alpha;
+    bool clamped;
+};
+
+// alpha = min(0.99, o exp(-(u^2+v^2)/2)) of one surfel at one pixel (Sec. 3.1),
+// (u, v) = (q0/q2, q1/q2). Returns false if the pixel lies outside the support
+// disc (u^2+v^2 > r^2) or alpha < 1/255. Every operation is an explicitly
+// rounded intrinsic, so forward and adjoint kernels reproduce the same alpha
+// (and hence the same Top-K sets) bit for bit.
+__device__ __forceinline__ bool eval_alpha(const Rec &r, float lx, float ly, Eval &e)
+{
+    e.q0 = __fmaf_rn(r.a00, lx, __fmaf_rn(r.a01, ly, r.c0));
+    e.q1 = __fmaf_rn(r.a10, lx, __fmaf_rn(r.a11, ly, r.c1));
+    e.q2 = __fmaf_rn(r.a20, lx, __fmaf_rn(r.a21, ly, r.c2));
+    const float nn = __fmaf_rn(e.q0, e.q0, __fmul_rn(e.q1, e.q1));
+    const float dd = __fmul_rn(e.q2, e.q2);
+    if (!(nn <= __fmul_rn(r.r2, dd)) || !(dd > 0.0f)) return false;
+    e.d2 = __fmul_rn(nn, rcp_approx(dd));
+    e.G = ex2_approx(__fmul_rn(e.d2, kNegHalfLog2e));
+    const float a = __fmul_rn(r.o, e.G);
+    e.clamped = a > kAlphaMax;
+    e.alpha = e.clamped ? kAlphaMax : a;
+    return e.alpha >= kAlphaMin;
+}
+
+// ------------------------------------------------------------ staging
+struct Stage {
+    float4 rec[2][kBatch][4];
+    uint32_t val[2][kBatch];
+    uint64_t bar[2];
+};
+
+// Issued by warp 0: bulk-copy the records of list entries [b0, b0+cnt) into
+// buffer `buf` (one 64-byte TMA bulk copy per record), completion on bar[buf].
+__device__ __forceinline__ void issue_batch(Stage &S, int buf, const uint32_t *__restrict__ vals, int64_t list0,
+                                            int b0, int cnt, const float4 *__restrict__ records)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], static_cast<uint32_t>(cnt) * 64u);
+    __syncwarp();
+    for (int j = lane; j < cnt; j += 32) {
+        const uint32_t rid = vals[list0 + b0 + j];
+        S.val[buf][j] = rid;
+        bulk_g2s(&S.rec[buf][j][0], records + 4 * static_cast<size_t>(rid), 64u, &S.bar[buf]);
+    }
+}
+
+// Per-tile transform of the staged records: fold the tile origin into the
+// third column so that q = A (lx, ly, 1) with small, exact pixel offsets.
+__device__ __forceinline__ void transform_batch(Stage &S, int buf, int cnt, float tile_x0, float tile_y0)
+{
+    const int j = threadIdx.x;
+    if (j < cnt) {
+        float4 *r = S.rec[buf][j];
+        float4 x = r[0], y = r[1], z = r[2];
+        // record: a00 a01 a02 a10 | a11 a12 a20 a21 | a22 p0x p0y o | r2 r g b
+        const float ox = (tile_x0 + 0.5f) - z.y;
+        const float oy = (tile_y0 + 0.5f) - z.z;
+        x.z = __fmaf_rn(x.x, ox, __fmaf_rn(x.y, oy, x.z));
+        y.y = __fmaf_rn(x.w, ox, __fmaf_rn(y.x, oy, y.y));
+        z.x = __fmaf_rn(y.z, ox, __fmaf_rn(y.w, oy, z.x));
+        r[0] = x;
+        r[1] = y;
+        r[2] = z;
+    }
+}
+
+// ------------------------------------------------------------ features
+// CH (16 or 32) channels [c0, c0+CH) of feature row i as float32, before the
+// per-channel scale. Rows are read with 16-byte vector loads.
+template <int DT, int CH>
+__device__ __forceinline__ void load_feat(const void *__restrict__ base, int64_t i, int D, int c0, float *f)
+{
+    if constexpr (DT == PSI_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(base) + i * D + c0);
+#pragma unroll
+        for (int k = 0; k < CH / 4; ++k) {
+            const float4 v = __ldg(p + k);
+            f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+        }
+    } else if constexpr (DT == PSI_BF16) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(base) + i * D + c0);
+#pragma unroll
+        for (int k = 0; k < CH / 8; ++k) {
+            const uint4 v = __ldg(p + k);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                f[8 * k + 2 * h] = __uint_as_float(w[h] << 16);
+                f[8 * k + 2 * h + 1] = __uint_as_float(w[h] & 0xFFFF0000u);
+            }
+        }
+    } else {
+        // FP8 E4M3 (sign, 4 exponent bits with bias 7, 3 mantissa bits): placing
+        // the 7 magnitude bits at float bits [20, 27) gives 2^(e-127)(1+m/8)
+        // (or the denormal m 2^-129 when e = 0); times 2^120 that is exactly
+        // 2^(e-7)(1+m/8) (or m 2^-9).
+        const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(base) + i * D + c0);
+#pragma unroll
+        for (int k = 0; k < CH / 16; ++k) {
+            const uint4 v = __ldg(p + k);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t byte = (w[h] >> (8 * b)) & 0xFFu;
+                    const uint32_t bits = ((byte & 0x80u) << 24) | ((byte & 0x7Fu) << 20);
+                    f[16 * k + 4 * h + b] = __uint_as_float(bits) * 0x1p120f;
+                }
+            }
+        }
+    }
+}
+
+// Store CH channels (times scale) of one pixel's feature row as FP32 or BF16.
+template <int CH>
+__device__ __forceinline__ void store_feat(void *F, bool bf16, int64_t pix, int D, int c0, const float *acc,
+                                           const float *__restrict__ scale)
+{
+    float v[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) v[c] = scale ? acc[c] * __ldg(scale + c0 + c) : acc[c];
+    if (bf16) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(F) + pix * D + c0);
+#pragma unroll
+        for (int k = 0; k < CH / 8; ++k) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * k + 2 * h], v[8 * k + 2 * h + 1]);
+                w4[h] = *reinterpret_cast<const uint32_t *>(&p2);
+            }
+            dst[k] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+    } else {
+        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(F) + pix * D + c0);
+#pragma unroll
+        for (int k = 0; k < CH / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+}
+
+} // namespace raster
+} // namespace psi

@@ -1,0 +1,273 @@
+// a4: per-tile compositing with Top-K Hard Selection.
+//
+// One CTA per 16x16 tile, one thread per pixel. The tile's sorted list is
+// walked in batches of 256 records staged into shared memory by TMA bulk
+// copies (double buffered, mbarrier completion), so the next batch streams in
+// while the current one is composited. Per pixel (Sec. 3.1, Eq. 1): alpha =
+// min(0.99, o exp(-(u^2+v^2)/2)), RGB blended densely front to back with FP32
+// transmittance T, and the K largest weights omega_j = alpha_j T_j kept in
+// registers (Sec. 5, Top-K Hard Selection): the insertion runs under a
+// warp vote, so lanes pay one compare per surfel unless some lane of the warp
+// improves its set. After the walk the K selected features are gathered with
+// 16-byte vector loads and summed in list order in FP32:
+// F = scale * sum_{j in K} omega_j q_j.
+// Dense features (K = 0) accumulate 32 channels per pass over the list.
+#include "raster.cuh"
+
+namespace psi {
+namespace {
+
+using namespace raster;
+
+struct FwdArgs {
+    const float4 *records;
+    const uint32_t *vals;
+    const uint32_t *ranges;
+    const void *feat;
+    const float *fscale;
+    int D;
+    int c0;          // dense mode: first channel of this pass
+    int write_rgb;   // dense mode: only the first pass writes rgb / T / ids
+    float *rgb;
+    float *T;
+    int32_t *n_last;
+    void *F;
+    int F_bf16;
+    int32_t *topk_ids;
+    DevStatus *status;
+};
+
+template <int KMAX, int DT, int CH>
+__global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
+{
+    __shared__ __align__(128) Stage S;
+    const int tid = threadIdx.x, wid = tid >> 5;
+    const uint32_t tile = blockIdx.x;
+    const int v = view_of_tile(fp, tile);
+    const ViewParams &cam = fp.v[v];
+    const int local = static_cast<int>(tile - cam.tile_base);
+    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
+    const int lxi = tid & 15, lyi = tid >> 4;
+    const int px = tx * kTile + lxi, py = ty * kTile + lyi;
+    const bool inside = px < cam.W && py < cam.H;
+    const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
+    const int64_t list0 = a.ranges[2 * tile];
+    const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    const int nb = (n + kBatch - 1) / kBatch;
+    const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
+    const int K = KMAX > 0 ? fp.top_k : 0;
+
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (wid == 0) {
+        for (int b = 0; b < 2 && b < nb; ++b)
+            issue_batch(S, b, a.vals, list0, b * kBatch, min(kBatch, n - b * kBatch), a.records);
+    }
+
+    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    int last = 0;
+    bool done = !inside;
+    float kw[KMAX > 0 ? KMAX : 1];
+    int kp[KMAX > 0 ? KMAX : 1];
+    float worst_w = -1.0f;
+    int worst_p = 0x7fffffff, worst_i = 0;
+#pragma unroll
+    for (int s = 0; s < (KMAX > 0 ? KMAX : 1); ++s) {
+        kw[s] = (s < K) ? -1.0f : __int_as_float(0x7f800000);
+        kp[s] = 0x7fffffff;
+    }
+    float facc[KMAX == 0 ? CH : 1];
+#pragma unroll
+    for (int c = 0; c < (KMAX == 0 ? CH : 1); ++c) facc[c] = 0.0f;
+
+    int issued = min(nb, 2), consumed = 0;
+    bool ok = true;
+    for (int b = 0; b < nb; ++b) {
+        const int buf = b & 1;
+        ok = mbar_wait(&S.bar[buf], (b >> 1) & 1, a.status);
+        consumed = b + 1;
+        const int cnt = min(kBatch, n - b * kBatch);
+        if (ok) {
+            transform_batch(S, buf, cnt, static_cast<float>(tx * kTile), static_cast<float>(ty * kTile));
+            fence_proxy_async_smem();
+        }
+        if (__syncthreads_or(!ok)) break;
+        for (int j = 0; j < cnt; ++j) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const Rec r = load_rec(S.rec[buf][j]);
+            Eval e;
+            const bool hit = !done && eval_alpha(r, lx, ly, e);
+            const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
+            const int pos = b * kBatch + j;
+            if (hit) {
+                const float4 col = S.rec[buf][j][3];
+                cr = __fmaf_rn(w, col.y, cr);
+                cg = __fmaf_rn(w, col.z, cg);
+                cb = __fmaf_rn(w, col.w, cb);
+                if constexpr (KMAX == 0) {
+                    if (a.feat) {
+                        float f[CH];
+                        load_feat<DT, CH>(a.feat, static_cast<int64_t>(S.val[buf][j]) - surf0, a.D, a.c0, f);
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) facc[c] = __fmaf_rn(w, f[c], facc[c]);
+                    }
+                }
+            }
+            if constexpr (KMAX > 0) {
+                const bool better = hit && w > worst_w;
+                if (__any_sync(0xffffffffu, better)) {
+                    if (better) {
+#pragma unroll
+                        for (int s = 0; s < KMAX; ++s)
+                            if (s == worst_i) {
+                                kw[s] = w;
+                                kp[s] = pos;
+                            }
+                        worst_w = kw[0];
+                        worst_p = kp[0];
+                        worst_i = 0;
+#pragma unroll
+                        for (int s = 1; s < KMAX; ++s)
+                            if (kw[s] < worst_w || (kw[s] == worst_w && kp[s] > worst_p)) {
+                                worst_w = kw[s];
+                                worst_p = kp[s];
+                                worst_i = s;
+                            }
+                    }
+                }
+            }
+            if (hit) {
+                T = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
+                last = pos + 1;
+                if (T < fp.t_eps) done = true;
+            }
+        }
+        const int alive = __syncthreads_count(!done);
+        if (alive == 0) break;
+        if (wid == 0 && b + 2 < nb) {
+            issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
+            ++issued;
+        }
+    }
+    // drain copies still in flight before the CTA's shared memory is released
+    for (int b = consumed; b < issued; ++b) mbar_wait(&S.bar[b & 1], (b >> 1) & 1, a.status);
+    if (!ok) return;
+    if (!inside) return;
+
+    const int64_t pix = cam.pix_base + static_cast<int64_t>(py) * cam.W + px;
+    if (a.write_rgb) {
+        a.rgb[pix] = cr;
+        a.rgb[fp.n_pix_total + pix] = cg;
+        a.rgb[2 * fp.n_pix_total + pix] = cb;
+        a.T[pix] = T;
+        if (a.n_last) a.n_last[pix] = last;
+    }
+
+    if constexpr (KMAX == 0) {
+        if (a.F && a.feat) store_feat<CH>(a.F, a.F_bf16 != 0, pix, a.D, a.c0, facc, a.fscale);
+    } else {
+        // selected set in list order (odd-even transposition sort on position)
+#pragma unroll
+        for (int round = 0; round < KMAX; ++round) {
+#pragma unroll
+            for (int s = (round & 1); s + 1 < KMAX; s += 2) {
+                if (kp[s] > kp[s + 1]) {
+                    const int tp = kp[s];
+                    kp[s] = kp[s + 1];
+                    kp[s + 1] = tp;
+                    const float tw = kw[s];
+                    kw[s] = kw[s + 1];
+                    kw[s + 1] = tw;
+                }
+            }
+        }
+        int32_t sid[KMAX];
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s)
+            sid[s] = (s < K && kp[s] != 0x7fffffff) ? static_cast<int32_t>(static_cast<int64_t>(a.vals[list0 + kp[s]]) - surf0)
+                                                    : -1;
+        if (a.topk_ids) {
+            int32_t *dst = a.topk_ids + pix * K;
+            for (int s = 0; s < K; ++s) dst[s] = sid[s];
+        }
+        if (a.F && a.feat) {
+            for (int c0 = 0; c0 < a.D; c0 += CH) {
+                float acc[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) acc[c] = 0.0f;
+#pragma unroll
+                for (int s = 0; s < KMAX; ++s) {
+                    if (sid[s] < 0) continue;
+                    float f[CH];
+                    load_feat<DT, CH>(a.feat, sid[s], a.D, c0, f);
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) acc[c] = __fmaf_rn(kw[s], f[c], acc[c]);
+                }
+                store_feat<CH>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
+            }
+        }
+    }
+}
+
+template <int KMAX, int CH>
+cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
+{
+    const unsigned grid = fp.n_tiles_total;
+    switch (f.data ? f.dtype : PSI_F32) {
+    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    default: render_fwd_kernel<KMAX, PSI_F32, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FwdArgs &a, int ch, cudaStream_t st)
+{
+    if (fp.n_tiles_total == 0) return cudaSuccess;
+    return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
+}
+
+} // namespace
+
+cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const float4 *records, const uint32_t *vals,
+                              const uint32_t *ranges, const psi_fwd_out &out, DevStatus *status, cudaStream_t st)
+{
+    FwdArgs a{};
+    a.records = records;
+    a.vals = vals;
+    a.ranges = ranges;
+    a.feat = f.data;
+    a.fscale = f.scale;
+    a.D = f.dim;
+    a.c0 = 0;
+    a.write_rgb = 1;
+    a.rgb = out.rgb;
+    a.T = out.T;
+    a.n_last = out.n_last;
+    a.F = out.F;
+    a.F_bf16 = out.F_dtype == PSI_BF16;
+    a.topk_ids = out.topk_ids;
+    a.status = status;
+    const int K = fp.top_k;
+    const int ch = (f.dim % 32 == 0) ? 32 : 16;
+    if (K == 0) {
+        // dense: one pass per chunk of channels (the first also writes rgb/T)
+        cudaError_t e = launch_k<0>(fp, f, a, ch, st);
+        for (int c0 = ch; e == cudaSuccess && f.data && out.F && c0 < f.dim; c0 += ch) {
+            a.c0 = c0;
+            a.write_rgb = 0;
+            e = launch_k<0>(fp, f, a, ch, st);
+        }
+        return e;
+    }
+    if (K <= 8) return launch_k<8>(fp, f, a, ch, st);
+    if (K <= 16) return launch_k<16>(fp, f, a, ch, st);
+    return launch_k<32>(fp, f, a, ch, st);
+}
+
+} // namespace psi

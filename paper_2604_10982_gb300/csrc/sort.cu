@@ -1,0 +1,235 @@
+// a3: stable LSD radix sort of (uint64 key, uint32 value) pairs and the
+// per-tile [start, end) ranges of the sorted keys.
+//
+// Each pass sorts one digit with the spin-free reduce-then-scan scheme:
+// per-block digit histograms, one exclusive scan over the digit-major
+// histogram table, then a scatter in which every block ranks its items
+// stably (warp match on the digit, per-warp running counters, prefix over
+// warps) and writes them out through shared memory, so runs of one digit leave
+// the block as contiguous, coalesced stores. The number of passes is made even
+// (digit width <= 8 bits) so the result ends in the caller's buffers.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace psi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems; // 4096 pairs per block
+constexpr int kBins = 256;
+
+__global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *__restrict__ keys,
+                                                           const int64_t *__restrict__ d_n, int shift, int bits,
+                                                           uint32_t *__restrict__ hist, int nblk)
+{
+    __shared__ uint32_t h[kWarps][kBins];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kWarps * kBins; k += kThreads) (&h[0][0])[k] = 0;
+    __syncthreads();
+    const int64_t n = *d_n;
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + wid * (32 * kItems);
+    const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
+    if (static_cast<int64_t>(blockIdx.x) * kTile < n) {
+#pragma unroll 4
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t idx = base + i * 32 + lane;
+            if (idx < n) atomicAdd(&h[wid][static_cast<uint32_t>((keys[idx] >> shift) & mask)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kBins; d += kThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += h[w][d];
+        hist[static_cast<int64_t>(d) * nblk + blockIdx.x] = s;
+    }
+}
+
+struct ScatterSmem {
+    uint32_t warp_cnt[kWarps][kBins];
+    uint32_t digit_start[kBins];       // start of each digit in the block's local order
+    unsigned long long digit_base[kBins]; // global output offset of the block's first item of each digit
+    uint32_t warp_tot[kWarps + 1];
+    uint64_t xkeys[kTile];
+    uint32_t xvals[kTile];
+};
+
+__global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *__restrict__ keys_in,
+                                                           const uint32_t *__restrict__ vals_in,
+                                                           uint64_t *__restrict__ keys_out,
+                                                           uint32_t *__restrict__ vals_out,
+                                                           const int64_t *__restrict__ d_n, int shift, int bits,
+                                                           const unsigned long long *__restrict__ offs, int nblk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n = *d_n;
+    const int64_t blk0 = static_cast<int64_t>(blockIdx.x) * kTile;
+    if (blk0 >= n) return;
+    const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
+    for (int k = threadIdx.x; k < kWarps * kBins; k += kThreads) (&S.warp_cnt[0][0])[k] = 0;
+    for (int d = threadIdx.x; d < kBins; d += kThreads) S.digit_base[d] = offs[static_cast<int64_t>(d) * nblk + blockIdx.x];
+    __syncthreads();
+
+    // warp-striped items: item i of lane l is at blk0 + wid*512 + i*32 + l
+    uint64_t key[kItems];
+    uint32_t val[kItems];
+    uint32_t rank[kItems];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const int64_t idx = blk0 + wid * (32 * kItems) + i * 32 + lane;
+        const bool ok = idx < n;
+        key[i] = ok ? keys_in[idx] : 0ull;
+        val[i] = ok ? vals_in[idx] : 0u;
+        const uint32_t d = ok ? static_cast<uint32_t>((key[i] >> shift) & mask) : (kBins + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (ok) before = S.warp_cnt[wid][d];
+        __syncwarp();
+        if (ok && (peers & lt) == 0) S.warp_cnt[wid][d] = before + __popc(peers);
+        __syncwarp();
+        rank[i] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, and the block's digit count
+    uint32_t cnt = 0;
+    {
+        const int d = threadIdx.x; // kThreads == kBins
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = S.warp_cnt[w][d];
+            S.warp_cnt[w][d] = run;
+            run += c;
+        }
+        cnt = run;
+    }
+    // exclusive scan of the digit counts over the block (256 digits, one per thread)
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) S.warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t t = lane < kWarps ? S.warp_tot[lane] : 0u;
+        uint32_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += u;
+        }
+        if (lane < kWarps) S.warp_tot[lane] = ti - t;
+    }
+    __syncthreads();
+    S.digit_start[threadIdx.x] = S.warp_tot[wid] + inc - cnt;
+    __syncthreads();
+    // local (block) position, exchange through shared memory
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const int64_t idx = blk0 + wid * (32 * kItems) + i * 32 + lane;
+        if (idx < n) {
+            const uint32_t d = static_cast<uint32_t>((key[i] >> shift) & mask);
+            const uint32_t lp = S.digit_start[d] + S.warp_cnt[wid][d] + rank[i];
+            S.xkeys[lp] = key[i];
+            S.xvals[lp] = val[i];
+        }
+    }
+    __syncthreads();
+    const int nvalid = static_cast<int>(std::min<int64_t>(kTile, n - blk0));
+    for (int j = threadIdx.x; j < nvalid; j += kThreads) {
+        const uint64_t k = S.xkeys[j];
+        const uint32_t d = static_cast<uint32_t>((k >> shift) & mask);
+        const unsigned long long pos = S.digit_base[d] + static_cast<unsigned long long>(j - static_cast<int>(S.digit_start[d]));
+        keys_out[pos] = k;
+        vals_out[pos] = S.xvals[j];
+    }
+}
+
+__global__ void __launch_bounds__(256) ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *__restrict__ d_n,
+                                                     uint32_t *__restrict__ ranges, int64_t n_tiles, DevStatus *status)
+{
+    const int64_t n = *d_n;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t t = keys[i] >> 32;
+    if (t >= static_cast<uint64_t>(n_tiles)) {
+        raise_status(status, PSI_ERR_INVALID_ARG);
+        return;
+    }
+    if (i == 0 || (keys[i - 1] >> 32) != t) ranges[2 * t] = static_cast<uint32_t>(i);
+    if (i == n - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = static_cast<uint32_t>(i + 1);
+}
+
+} // namespace
+
+size_t sort_workspace_bytes(int64_t capacity)
+{
+    const int64_t cap = std::max<int64_t>(capacity, 1);
+    const int64_t nblk = (cap + kTile - 1) / kTile;
+    const int64_t nh = nblk * kBins;
+    return align_up(cap * 8, 256) + align_up(cap * 4, 256) + align_up(nh * 4, 256) + align_up(nh * 8, 256) +
+           scan_workspace_bytes(nh) + 256;
+}
+
+cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity, int begin_bit,
+                        int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *ws, DevStatus *status,
+                        cudaStream_t st)
+{
+    const int64_t cap = std::max<int64_t>(capacity, 1);
+    const int64_t nblk = (cap + kTile - 1) / kTile;
+    const int64_t nh = nblk * kBins;
+    char *p = static_cast<char *>(ws);
+    auto *alt_keys = reinterpret_cast<uint64_t *>(p);
+    p += align_up(cap * 8, 256);
+    auto *alt_vals = reinterpret_cast<uint32_t *>(p);
+    p += align_up(cap * 4, 256);
+    auto *hist = reinterpret_cast<uint32_t *>(p);
+    p += align_up(nh * 4, 256);
+    auto *offs = reinterpret_cast<unsigned long long *>(p);
+    p += align_up(nh * 8, 256);
+    void *scan_ws = p;
+    p += scan_workspace_bytes(nh);
+    auto *scan_total = reinterpret_cast<unsigned long long *>(p);
+
+    const int nbits = std::max(end_bit - begin_bit, 1);
+    int passes = std::max(2, (nbits + 7) / 8);
+    if (passes & 1) ++passes;
+    const int dbits = (nbits + passes - 1) / passes;
+    {
+        cudaError_t e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(sizeof(ScatterSmem)));
+        if (e != cudaSuccess) return e;
+    }
+    uint64_t *kin = keys, *kout = alt_keys;
+    uint32_t *vin = vals, *vout = alt_vals;
+    for (int ps = 0; ps < passes; ++ps) {
+        int shift = begin_bit + ps * dbits;
+        const int bits = std::max(0, std::min(dbits, end_bit - shift));
+        if (bits == 0) shift = 0; // identity pass (keeps the pass count even)
+        upsweep_kernel<<<static_cast<unsigned>(nblk), kThreads, 0, st>>>(kin, d_num_pairs, shift, bits, hist,
+                                                                         static_cast<int>(nblk));
+        cudaError_t e = launch_scan_u32(hist, offs, nh, scan_total, scan_ws, st);
+        if (e != cudaSuccess) return e;
+        scatter_kernel<<<static_cast<unsigned>(nblk), kThreads, sizeof(ScatterSmem), st>>>(
+            kin, vin, kout, vout, d_num_pairs, shift, bits, offs, static_cast<int>(nblk));
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    if (tile_ranges && n_tiles_total > 0) {
+        cudaError_t e = cudaMemsetAsync(tile_ranges, 0, static_cast<size_t>(n_tiles_total) * 8, st);
+        if (e != cudaSuccess) return e;
+        ranges_kernel<<<static_cast<unsigned>((cap + 255) / 256), 256, 0, st>>>(keys, d_num_pairs, tile_ranges,
+                                                                               n_tiles_total, status);
+    }
+    return cudaGetLastError();
+}
+
+} // namespace psi

@@ -1,0 +1,175 @@
+"""Device buffers and the call sequence of one frame (a1..a6) on top of the
+C ABI. PyTorch only allocates memory and supplies the stream; every step runs
+in libpsi's kernels (psi.py marshals the arguments).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import psi
+
+
+def quantize_features(f: torch.Tensor, dtype: int):
+    """Storage form of an [N, D] float32 feature table.
+
+    F32: as is. BF16: round to nearest even. FP8-E4M3: per-channel scale
+    amax_c / 448 and q = RNE(f / scale) (saturated to +-448), so that
+    f ~= q * scale[c]. Returns (q, scale or None)."""
+    f = f.contiguous()
+    if dtype == psi.F32:
+        return f, None
+    if dtype == psi.BF16:
+        return f.to(torch.bfloat16).contiguous(), None
+    if dtype == psi.FP8_E4M3:
+        amax = f.abs().amax(0).clamp_min(1e-30)
+        scale = (amax / 448.0).float().contiguous()
+        q = (f / scale).clamp(-448.0, 448.0).to(torch.float8_e4m3fn).contiguous()
+        return q, scale
+    raise ValueError(f"unknown feature dtype {dtype}")
+
+
+def dequantize(q: torch.Tensor, scale, dtype: int) -> np.ndarray:
+    """float64 values the kernels read from a stored feature table (host)."""
+    v = q.detach().to("cpu")
+    v = v.float().double() if dtype != psi.F32 else v.double()
+    if scale is not None:
+        v = v * scale.detach().to("cpu").double()[None, :]
+    return v.numpy()
+
+
+class DeviceScene:
+    """Surfels (float32 SoA) and the stored feature table on one device."""
+
+    def __init__(self, surfels, features=None, feat_dtype=psi.F32, device="cuda", requires_grad=False):
+        dev = torch.device(device)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+        self.mu, self.tu, self.tv = t(surfels.mu), t(surfels.tu), t(surfels.tv)
+        self.scale, self.opacity, self.rgb = t(surfels.scale), t(surfels.opacity), t(surfels.rgb)
+        self.n = int(surfels.mu.shape[0])
+        self.feat_dtype = feat_dtype
+        self.feat_f32 = None if features is None else t(features)
+        if features is None:
+            self.q, self.qscale = None, None
+        else:
+            self.q, self.qscale = quantize_features(self.feat_f32, feat_dtype)
+        self.D = 0 if features is None else int(features.shape[1])
+
+    def surfels_struct(self):
+        return psi.surfels_struct(self.mu, self.tu, self.tv, self.scale, self.opacity, self.rgb)
+
+    def features_struct(self):
+        return psi.features_struct(self.q, self.qscale, self.feat_dtype)
+
+
+def _key_bits(n_tiles_total: int) -> int:
+    return 32 + max(1, math.ceil(math.log2(max(n_tiles_total, 2))))
+
+
+@dataclass
+class FrameOutputs:
+    rgb: torch.Tensor      # [3, P_total]
+    T: torch.Tensor        # [P_total]
+    n_last: torch.Tensor   # [P_total]
+    F: torch.Tensor | None
+    topk_ids: torch.Tensor | None
+    num_pairs: torch.Tensor  # device int64 [1]
+
+
+class Renderer:
+    """Holds the per-frame device buffers for a fixed (N, cameras, opts)."""
+
+    def __init__(self, ctx: psi.Context, n_surfels: int, cams, opts: psi.PsiRenderOpts, capacity: int,
+                 D: int = 0, F_dtype: int = psi.F32, want_topk_ids: bool = False, device="cuda"):
+        self.ctx = ctx
+        self.dev = torch.device(device)
+        self.cams_py = list(cams)
+        self.cams = psi.cameras(cams)
+        self.V = len(cams)
+        self.n = int(n_surfels)
+        self.opts = opts
+        self.tile_base, self.pix_base = psi.view_layout(self.cams, self.V, opts)
+        self.n_tiles = int(self.tile_base[-1])
+        self.n_pix = int(self.pix_base[-1])
+        self.key_bits = _key_bits(self.n_tiles)
+        R = self.V * self.n
+        u8 = lambda nbytes: torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.dev)
+        self.records = u8(R * psi.RECORD_BYTES)
+        self.bins = u8(R * psi.BIN_RECORD_BYTES)
+        self.counts = torch.empty(max(R, 1), dtype=torch.int32, device=self.dev)
+        self.ws_isect = u8(psi.intersect_workspace_size(R))
+        self.set_capacity(capacity)
+        self.num_pairs = torch.zeros(1, dtype=torch.int64, device=self.dev)
+        self.ranges = torch.empty(max(self.n_tiles, 1) * 2, dtype=torch.int32, device=self.dev)
+        self.rgb = torch.empty(3, self.n_pix, dtype=torch.float32, device=self.dev)
+        self.T = torch.empty(self.n_pix, dtype=torch.float32, device=self.dev)
+        self.n_last = torch.empty(self.n_pix, dtype=torch.int32, device=self.dev)
+        self.D = D
+        self.F_dtype = F_dtype
+        fdt = torch.bfloat16 if F_dtype == psi.BF16 else torch.float32
+        self.F = torch.empty(self.n_pix, D, dtype=fdt, device=self.dev) if D else None
+        K = int(opts.top_k)
+        self.topk_ids = torch.empty(self.n_pix, K, dtype=torch.int32, device=self.dev) if (want_topk_ids and K) else None
+
+    def set_capacity(self, capacity: int):
+        self.capacity = int(max(capacity, 1))
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.dev)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=self.dev)
+        self.ws_sort = torch.empty(psi.sort_workspace_size(self.capacity), dtype=torch.uint8, device=self.dev)
+
+    # a1
+    def project(self, scene: DeviceScene, stream=None):
+        s = scene.surfels_struct()
+        psi.psi_project_surfels(self.ctx, s, self.cams, self.V, self.opts, self.records, self.bins, self.counts, stream)
+
+    # a2
+    def intersect(self, stream=None):
+        psi.psi_intersect_tiles(self.ctx, self.cams, self.V, self.opts, self.n, self.bins, self.counts, self.keys,
+                                self.vals, self.capacity, self.num_pairs, self.ws_isect, stream)
+
+    # a3
+    def sort(self, begin_bit=0, end_bit=None, stream=None):
+        psi.psi_sort_keys(self.ctx, self.keys, self.vals, self.num_pairs, self.capacity, begin_bit,
+                          end_bit or self.key_bits, self.ranges, self.n_tiles, self.ws_sort, stream)
+
+    # a4
+    def render(self, scene: DeviceScene, want_F: bool = True, stream=None):
+        feats = scene.features_struct()
+        out = psi.PsiFwdOut(psi._ptr(self.rgb), psi._ptr(self.T), psi._ptr(self.n_last),
+                            psi._ptr(self.F) if (want_F and self.F is not None) else None, int(self.F_dtype),
+                            psi._ptr(self.topk_ids))
+        psi.psi_render_fwd(self.ctx, feats, self.records, self.vals, self.ranges, self.cams, self.V, self.n, self.opts,
+                           out, stream)
+
+    def frame(self, scene: DeviceScene, want_F: bool = True, stream=None):
+        self.project(scene, stream)
+        self.intersect(stream)
+        self.sort(stream=stream)
+        self.render(scene, want_F, stream)
+
+    def required_pairs(self, scene: DeviceScene) -> int:
+        """Project and count the pairs of this frame (synchronises the host)."""
+        self.project(scene)
+        R = self.V * self.n
+        return int(self.counts[:R].to(torch.int64).sum().item()) if R else 0
+
+    def pixel_view(self, v: int, t: torch.Tensor):
+        """View v's block of a per-pixel tensor ([P_total, ...] or [3, P_total]) as an image."""
+        c = self.cams_py[v]
+        a, b = int(self.pix_base[v]), int(self.pix_base[v + 1])
+        if t.dim() == 2 and t.shape[0] == 3 and t.shape[1] == self.n_pix:
+            return t[:, a:b].reshape(3, c.height, c.width)
+        return t[a:b].reshape(c.height, c.width, *t.shape[1:])
+
+
+def make_renderer(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, want_topk_ids=False, headroom=1.25,
+                  min_capacity=1024):
+    """Renderer whose key buffer fits this scene and these cameras."""
+    r = Renderer(ctx, scene.n, cams, opts, min_capacity, D=D, F_dtype=F_dtype, want_topk_ids=want_topk_ids,
+                 device=scene.mu.device)
+    need = r.required_pairs(scene)
+    r.set_capacity(max(min_capacity, int(need * headroom) + 16))
+    return r
