@@ -73,6 +73,77 @@ __device__ __forceinline__ bool eval_alpha(const Rec &r, float lx, float ly, Eva
     return e.alpha >= kAlphaMin;
 }
 
+// ------------------------------------------------------------ Top-K
+// The K largest weights of one pixel with their list positions (Sec. 5, Top-K
+// Hard Selection). A new weight enters only if it is strictly larger than the
+// current worst, and among equal weights the later list position is the
+// worst: ties favour the earlier surfel. The insertion runs under a warp vote.
+template <int KMAX>
+struct TopK {
+    float w[KMAX];
+    int p[KMAX];
+    float worst_w;
+    int worst_p, worst_i;
+
+    __device__ __forceinline__ void init(int K)
+    {
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) {
+            w[s] = (s < K) ? -1.0f : __int_as_float(0x7f800000);
+            p[s] = 0x7fffffff;
+        }
+        worst_w = -1.0f;
+        worst_p = 0x7fffffff;
+        worst_i = 0;
+    }
+
+    __device__ __forceinline__ void offer(bool hit, float wt, int pos)
+    {
+        const bool better = hit && wt > worst_w;
+        if (__any_sync(0xffffffffu, better)) {
+            if (better) {
+#pragma unroll
+                for (int s = 0; s < KMAX; ++s)
+                    if (s == worst_i) {
+                        w[s] = wt;
+                        p[s] = pos;
+                    }
+                worst_w = w[0];
+                worst_p = p[0];
+                worst_i = 0;
+#pragma unroll
+                for (int s = 1; s < KMAX; ++s)
+                    if (w[s] < worst_w || (w[s] == worst_w && p[s] > worst_p)) {
+                        worst_w = w[s];
+                        worst_p = p[s];
+                        worst_i = s;
+                    }
+            }
+        }
+    }
+
+    // order the slots by list position (empty slots last)
+    __device__ __forceinline__ void sort_by_pos()
+    {
+#pragma unroll
+        for (int round = 0; round < KMAX; ++round) {
+#pragma unroll
+            for (int s = (round & 1); s + 1 < KMAX; s += 2) {
+                if (p[s] > p[s + 1]) {
+                    const int tp = p[s];
+                    p[s] = p[s + 1];
+                    p[s + 1] = tp;
+                    const float tw = w[s];
+                    w[s] = w[s + 1];
+                    w[s + 1] = tw;
+                }
+            }
+        }
+    }
+
+    __device__ __forceinline__ bool valid(int s, int K) const { return s < K && p[s] != 0x7fffffff; }
+};
+
 // ------------------------------------------------------------ staging
 struct Stage {
     float4 rec[2][kBatch][4];

@@ -1,18 +1,497 @@
-// a5: adjoint of the per-tile compositing (placeholder until the kernel lands).
+// a5: adjoint of the per-tile compositing with Top-K Hard Selection.
+//
+// Pass A recomputes the forward walk of each pixel with the same float32
+// operation sequence (shared eval_alpha and TopK helpers), which recovers the
+// same Top-K set, T_final and last surfel without storing per-pixel lists.
+// Pass B walks the tile's list back to front. With C = sum_j c_j alpha_j T_j
+// (Eq. 1), F = sum_{j in K} f_j omega_j (Sec. 5) and
+// L = <gC, C> + <gF, F> + gT T_final:
+//     s_j        = <gC, c_j> + [j in K] <gF, f_j>
+//     dL/dalpha_j = T_j s_j - (sum_{k>j} omega_k s_k + T_final gT) / (1 - alpha_j)
+//     dL/dc_j    += omega_j gC,     dL/df_j += [j in K] omega_j gF
+// T_j is recovered as T_{j+1} / (1 - alpha_j). Through alpha = o G (unless
+// clamped): dL/do = dL/dalpha G, and (u, v) enter via a = dL/dalpha * alpha:
+// with (u, v, 1) ~ M^-1 p the gradient of M is M^-T W, W = sum a (u, v,
+// -d^2)(u, v, 1)^T, so each (pixel, record) adds 7 moments of (u, v).
+// Per-surfel sums are reduced across the warp (a transposing butterfly: 16
+// values in 16 shuffles) and added with one atomic per value per warp; the
+// feature gradient is accumulated warp-cooperatively across channels.
+// A second kernel turns the per-record moments into gradients of mu, t_u,
+// t_v, s_u, s_v through the camera.
 #include "raster.cuh"
 
 namespace psi {
+namespace {
+
+using namespace raster;
+
+constexpr int kMoments = 8; // per record: dL/do, Suu, Suv, Svv, Su, Sv, Sdu, Sdv
+
+struct BwdArgs {
+    const float4 *records;
+    const uint32_t *vals;
+    const uint32_t *ranges;
+    const void *feat;
+    const float *fscale;
+    int D;
+    const float *g_rgb; // [3][P_total]
+    const float *g_F;   // [P_total, D] or NULL
+    const float *g_T;   // [P_total] or NULL
+    float *g_col;       // [N,3] or NULL
+    float *g_feat;      // [N,D] or NULL
+    float *moments;     // [R, 8]
+    DevStatus *status;
+};
+
+// Sum 16 per-lane values over the warp: afterwards lane l (and l^1) holds the
+// total of value index 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l).
+__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[k] : v[k + 8];
+        const float keep = hi ? v[k + 8] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[k] : v[k + 4];
+        const float keep = hi ? v[k + 4] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool hi = lane & 4;
+        const float send = hi ? v[k] : v[k + 2];
+        const float keep = hi ? v[k + 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1];
+        const float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
+template <int KMAX, int DT, int CH>
+__global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
+{
+    __shared__ __align__(128) Stage S;
+    __shared__ int s_maxlast;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const uint32_t tile = blockIdx.x;
+    const int v = view_of_tile(fp, tile);
+    const ViewParams &cam = fp.v[v];
+    const int local = static_cast<int>(tile - cam.tile_base);
+    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
+    const int lxi = tid & 15, lyi = tid >> 4;
+    const int px = tx * kTile + lxi, py = ty * kTile + lyi;
+    const bool inside = px < cam.W && py < cam.H;
+    const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
+    const int64_t list0 = a.ranges[2 * tile];
+    const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    const int nb = (n + kBatch - 1) / kBatch;
+    const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
+    const int K = KMAX > 0 ? fp.top_k : 0;
+    const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
+    const float tileX = static_cast<float>(tx * kTile), tileY = static_cast<float>(ty * kTile);
+
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+        s_maxlast = 0;
+    }
+    __syncthreads();
+    int uses[2] = {0, 0}; // completed phases per buffer (uniform over the CTA)
+
+    // ---------------- pass A: forward recompute
+    if (wid == 0)
+        for (int b = 0; b < 2 && b < nb; ++b)
+            issue_batch(S, b, a.vals, list0, b * kBatch, min(kBatch, n - b * kBatch), a.records);
+    float T = 1.0f;
+    int last = 0;
+    bool done = !inside;
+    TopK<(KMAX > 0 ? KMAX : 1)> top;
+    top.init(K);
+    int issued = min(nb, 2), consumed = 0;
+    bool ok = true;
+    for (int b = 0; b < nb; ++b) {
+        const int buf = b & 1;
+        ok = mbar_wait(&S.bar[buf], uses[buf] & 1, a.status);
+        ++uses[buf];
+        consumed = b + 1;
+        const int cnt = min(kBatch, n - b * kBatch);
+        if (ok) {
+            transform_batch(S, buf, cnt, tileX, tileY);
+            fence_proxy_async_smem();
+        }
+        if (__syncthreads_or(!ok)) break;
+        for (int j = 0; j < cnt; ++j) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const Rec r = load_rec(S.rec[buf][j]);
+            Eval e;
+            const bool hit = !done && eval_alpha(r, lx, ly, e);
+            const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
+            const int pos = b * kBatch + j;
+            if constexpr (KMAX > 0) top.offer(hit, w, pos);
+            if (hit) {
+                T = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
+                last = pos + 1;
+                if (T < fp.t_eps) done = true;
+            }
+        }
+        const int alive = __syncthreads_count(!done);
+        if (alive == 0) break;
+        if (wid == 0 && b + 2 < nb) {
+            issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
+            ++issued;
+        }
+    }
+    for (int b = consumed; b < issued; ++b) {
+        mbar_wait(&S.bar[b & 1], uses[b & 1] & 1, a.status);
+        ++uses[b & 1];
+    }
+    if (__syncthreads_or(!ok)) return;
+
+    // selected set and <gF, f_j> for each selected surfel
+    float kd[KMAX > 0 ? KMAX : 1];
+    int kpos[KMAX > 0 ? KMAX : 1];
+    if constexpr (KMAX > 0) {
+        top.sort_by_pos();
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) {
+            kpos[s] = (inside && top.valid(s, K)) ? top.p[s] : -1;
+            kd[s] = 0.0f;
+        }
+        if (a.g_F && a.feat && inside) {
+            for (int c0 = 0; c0 < a.D; c0 += CH) {
+                float g[CH];
+#pragma unroll
+                for (int c = 0; c < CH; c += 4) {
+                    const float4 q = __ldg(reinterpret_cast<const float4 *>(a.g_F + pix * a.D + c0 + c));
+                    const float sc0 = a.fscale ? __ldg(a.fscale + c0 + c) : 1.0f;
+                    const float sc1 = a.fscale ? __ldg(a.fscale + c0 + c + 1) : 1.0f;
+                    const float sc2 = a.fscale ? __ldg(a.fscale + c0 + c + 2) : 1.0f;
+                    const float sc3 = a.fscale ? __ldg(a.fscale + c0 + c + 3) : 1.0f;
+                    g[c] = q.x * sc0;
+                    g[c + 1] = q.y * sc1;
+                    g[c + 2] = q.z * sc2;
+                    g[c + 3] = q.w * sc3;
+                }
+#pragma unroll
+                for (int s = 0; s < KMAX; ++s) {
+                    if (kpos[s] < 0) continue;
+                    const int64_t sid = static_cast<int64_t>(a.vals[list0 + kpos[s]]) - surf0;
+                    float f[CH];
+                    load_feat<DT, CH>(a.feat, sid, a.D, c0, f);
+                    float acc = kd[s];
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) acc = __fmaf_rn(g[c], f[c], acc);
+                    kd[s] = acc;
+                }
+            }
+        }
+    }
+    if (inside && last > 0) atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+
+    // ---------------- pass B: back to front
+    const float gr = inside ? a.g_rgb[pix] : 0.0f;
+    const float gg = inside ? a.g_rgb[fp.n_pix_total + pix] : 0.0f;
+    const float gb = inside ? a.g_rgb[2 * fp.n_pix_total + pix] : 0.0f;
+    const float gt = (inside && a.g_T) ? a.g_T[pix] : 0.0f;
+    float Tc = T;                  // T after the current surfel, walking back
+    float suffix = __fmul_rn(T, gt); // sum_{k>j} omega_k s_k + T_final gT
+    const int nbB = (maxlast + kBatch - 1) / kBatch;
+    const bool want_feat = a.g_F && a.g_feat;
+    if (wid == 0)
+        for (int k = 0; k < 2 && k < nbB; ++k) {
+            const int bi = nbB - 1 - k;
+            issue_batch(S, k, a.vals, list0, bi * kBatch, min(kBatch, maxlast - bi * kBatch), a.records);
+        }
+    issued = min(nbB, 2);
+    consumed = 0;
+    for (int k = 0; k < nbB; ++k) {
+        const int buf = k & 1;
+        const int bi = nbB - 1 - k;
+        ok = mbar_wait(&S.bar[buf], uses[buf] & 1, a.status);
+        ++uses[buf];
+        consumed = k + 1;
+        const int cnt = min(kBatch, maxlast - bi * kBatch);
+        if (ok) {
+            transform_batch(S, buf, cnt, tileX, tileY);
+            fence_proxy_async_smem();
+        }
+        if (__syncthreads_or(!ok)) break;
+        for (int j = cnt - 1; j >= 0; --j) {
+            const int pos = bi * kBatch + j;
+            const Rec r = load_rec(S.rec[buf][j]);
+            Eval e;
+            const bool act = inside && pos < last && eval_alpha(r, lx, ly, e);
+            if (!__any_sync(0xffffffffu, act)) continue;
+            const uint32_t rid = S.val[buf][j];
+            const int64_t sid = static_cast<int64_t>(rid) - surf0;
+            float vals[16];
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) vals[k2] = 0.0f;
+            float w = 0.0f;
+            bool sel = false;
+            if (act) {
+                const float one_m = __fsub_rn(1.0f, e.alpha);
+                const float inv = __frcp_rn(one_m);
+                const float Tj = Tc * inv;
+                w = e.alpha * Tj;
+                float dot = 0.0f;
+                if constexpr (KMAX > 0) {
+#pragma unroll
+                    for (int s = 0; s < KMAX; ++s)
+                        if (kpos[s] == pos) {
+                            sel = true;
+                            dot = kd[s];
+                        }
+                } else if (a.g_F && a.feat) {
+                    // dense features: every composited surfel is selected
+                    sel = true;
+                    for (int c0 = 0; c0 < a.D; c0 += CH) {
+                        float f[CH];
+                        load_feat<DT, CH>(a.feat, sid, a.D, c0, f);
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            const float sc = a.fscale ? __ldg(a.fscale + c0 + c) : 1.0f;
+                            dot = fmaf(__ldg(a.g_F + pix * a.D + c0 + c) * sc, f[c], dot);
+                        }
+                    }
+                }
+                const float4 col = S.rec[buf][j][3];
+                const float sj = gr * col.y + gg * col.z + gb * col.w + dot;
+                const float dLda = Tj * sj - suffix * inv;
+                suffix = fmaf(w, sj, suffix);
+                Tc = Tj;
+                vals[0] = w * gr;
+                vals[1] = w * gg;
+                vals[2] = w * gb;
+                if (!e.clamped) {
+                    const float rq = __frcp_rn(e.q2);
+                    const float u = e.q0 * rq, vv = e.q1 * rq;
+                    const float d2 = u * u + vv * vv;
+                    const float aa = dLda * e.alpha;
+                    vals[3] = dLda * e.G;
+                    vals[4] = aa * u * u;
+                    vals[5] = aa * u * vv;
+                    vals[6] = aa * vv * vv;
+                    vals[7] = aa * u;
+                    vals[8] = aa * vv;
+                    vals[9] = aa * d2 * u;
+                    vals[10] = aa * d2 * vv;
+                }
+            }
+            const float tot = warp_transpose_sum16(vals, lane);
+            const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+            if ((lane & 1) == 0 && idx < 11 && tot != 0.0f) {
+                if (idx < 3) {
+                    if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
+                } else {
+                    atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (idx - 3), tot);
+                }
+            }
+            if (want_feat) {
+                uint32_t selmask = __ballot_sync(0xffffffffu, act && sel);
+                if (selmask) {
+                    // lanes own channels lane, lane+32, ... of the surfel's feature gradient
+                    float acc[8];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) acc[m] = 0.0f;
+                    while (selmask) {
+                        const int L = __ffs(selmask) - 1;
+                        selmask &= selmask - 1;
+                        const float wL = __shfl_sync(0xffffffffu, w, L);
+                        const int64_t pL = __shfl_sync(0xffffffffu, pix, L);
+                        const float *grow = a.g_F + pL * a.D;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            const int c = lane + 32 * m;
+                            if (c < a.D) acc[m] = fmaf(wL, __ldg(grow + c), acc[m]);
+                        }
+                    }
+                    float *dst = a.g_feat + sid * a.D;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const int c = lane + 32 * m;
+                        if (c < a.D) atomicAdd(dst + c, acc[m]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (wid == 0 && k + 2 < nbB) {
+            const int bi2 = nbB - 1 - (k + 2);
+            issue_batch(S, buf, a.vals, list0, bi2 * kBatch, min(kBatch, maxlast - bi2 * kBatch), a.records);
+            ++issued;
+        }
+    }
+    for (int k = consumed; k < issued; ++k) {
+        mbar_wait(&S.bar[k & 1], uses[k & 1] & 1, a.status);
+        ++uses[k & 1];
+    }
+}
+
+// Per record: dL/dM = T^T M'^-T W (M' = T M is the map shifted to the projected
+// centre), then through M = [K R s_u t_u | K R s_v t_v | K (R mu + t)].
+__global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ FrameParams fp, psi_surfels s,
+                                                    const float4 *__restrict__ moments, psi_grads g)
+{
+    const int64_t total = fp.n * fp.n_views;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= total) return;
+    const float4 m0 = moments[2 * r], m1 = moments[2 * r + 1];
+    if (m0.x == 0.0f && m0.y == 0.0f && m0.z == 0.0f && m0.w == 0.0f && m1.x == 0.0f && m1.y == 0.0f &&
+        m1.z == 0.0f && m1.w == 0.0f)
+        return;
+    const int v = static_cast<int>(r / fp.n);
+    const int64_t i = r - static_cast<int64_t>(v) * fp.n;
+    const ViewParams &cam = fp.v[v];
+    const float *R = cam.R;
+    if (g.opacity) atomicAdd(g.opacity + i, m0.x);
+    const float Suu = m0.y, Suv = m0.z, Svv = m0.w, Su = m1.x, Sv = m1.y, Sdu = m1.z, Sdv = m1.w;
+
+    float mu[3], tu[3], tv[3];
+    for (int k = 0; k < 3; ++k) {
+        mu[k] = s.mu[3 * i + k];
+        tu[k] = s.tu[3 * i + k];
+        tv[k] = s.tv[3 * i + k];
+    }
+    const float su = s.scale[2 * i], sv = s.scale[2 * i + 1];
+    float xc[3], au[3], av[3];
+    for (int k = 0; k < 3; ++k) {
+        xc[k] = R[3 * k] * mu[0] + R[3 * k + 1] * mu[1] + R[3 * k + 2] * mu[2] + cam.t[k];
+        au[k] = R[3 * k] * tu[0] + R[3 * k + 1] * tu[1] + R[3 * k + 2] * tu[2];
+        av[k] = R[3 * k] * tv[0] + R[3 * k + 1] * tv[1] + R[3 * k + 2] * tv[2];
+    }
+    const float fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
+    const float w = xc[2];
+    const float p0x = (fx * xc[0] + cx * w) / w, p0y = (fy * xc[1] + cy * w) / w;
+    // shifted columns of M'
+    const float c0[3] = {fx * su * au[0] + (cx - p0x) * su * au[2], fy * su * au[1] + (cy - p0y) * su * au[2], su * au[2]};
+    const float c1[3] = {fx * sv * av[0] + (cx - p0x) * sv * av[2], fy * sv * av[1] + (cy - p0y) * sv * av[2], sv * av[2]};
+    const float c2[3] = {fx * xc[0] + (cx - p0x) * w, fy * xc[1] + (cy - p0y) * w, w};
+    // rows of adj(M') (adj = det * M'^-1): c1 x c2, c2 x c0, c0 x c1
+    float A[3][3];
+    A[0][0] = c1[1] * c2[2] - c1[2] * c2[1];
+    A[0][1] = c1[2] * c2[0] - c1[0] * c2[2];
+    A[0][2] = c1[0] * c2[1] - c1[1] * c2[0];
+    A[1][0] = c2[1] * c0[2] - c2[2] * c0[1];
+    A[1][1] = c2[2] * c0[0] - c2[0] * c0[2];
+    A[1][2] = c2[0] * c0[1] - c2[1] * c0[0];
+    A[2][0] = c0[1] * c1[2] - c0[2] * c1[1];
+    A[2][1] = c0[2] * c1[0] - c0[0] * c1[2];
+    A[2][2] = c0[0] * c1[1] - c0[1] * c1[0];
+    const float det = c0[0] * A[0][0] + c0[1] * A[0][1] + c0[2] * A[0][2];
+    if (!(fabsf(det) > 0.0f)) return;
+    const float idet = 1.0f / det;
+    const float W[3][3] = {{Suu, Suv, Su}, {Suv, Svv, Sv}, {-Sdu, -Sdv, -(Suu + Svv)}};
+    // G' = M'^-T W = adj^T W / det
+    float G[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) G[a][b] = (A[0][a] * W[0][b] + A[1][a] * W[1][b] + A[2][a] * W[2][b]) * idet;
+    // dL/dM = T^T G': third row picks up -p0x row0 - p0y row1
+    for (int b = 0; b < 3; ++b) G[2][b] = G[2][b] - p0x * G[0][b] - p0y * G[1][b];
+    // columns through K^T
+    float guu[3], gvv[3], gxc[3];
+    guu[0] = fx * G[0][0];
+    guu[1] = fy * G[1][0];
+    guu[2] = cx * G[0][0] + cy * G[1][0] + G[2][0];
+    gvv[0] = fx * G[0][1];
+    gvv[1] = fy * G[1][1];
+    gvv[2] = cx * G[0][1] + cy * G[1][1] + G[2][1];
+    gxc[0] = fx * G[0][2];
+    gxc[1] = fy * G[1][2];
+    gxc[2] = cx * G[0][2] + cy * G[1][2] + G[2][2];
+    // uu = s_u R t_u, vv = s_v R t_v, xc = R mu + t
+    float gsu = 0.0f, gsv = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        gsu += au[k] * guu[k];
+        gsv += av[k] * gvv[k];
+    }
+    for (int k = 0; k < 3; ++k) {
+        const float rtu = R[k] * guu[0] + R[3 + k] * guu[1] + R[6 + k] * guu[2];
+        const float rtv = R[k] * gvv[0] + R[3 + k] * gvv[1] + R[6 + k] * gvv[2];
+        const float rtx = R[k] * gxc[0] + R[3 + k] * gxc[1] + R[6 + k] * gxc[2];
+        if (g.tu) atomicAdd(g.tu + 3 * i + k, su * rtu);
+        if (g.tv) atomicAdd(g.tv + 3 * i + k, sv * rtv);
+        if (g.mu) atomicAdd(g.mu + 3 * i + k, rtx);
+    }
+    if (g.scale) {
+        atomicAdd(g.scale + 2 * i, gsu);
+        atomicAdd(g.scale + 2 * i + 1, gsv);
+    }
+}
+
+template <int KMAX, int CH>
+cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+{
+    const unsigned grid = fp.n_tiles_total;
+    switch (f.data ? f.dtype : PSI_F32) {
+    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    default: render_bwd_kernel<KMAX, PSI_F32, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const BwdArgs &a, int ch, cudaStream_t st)
+{
+    return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
+}
+
+} // namespace
 
 size_t render_bwd_workspace_bytes(int64_t n_records)
 {
-    return align_up(static_cast<size_t>(std::max<int64_t>(n_records, 1)) * 32, 256);
+    return align_up(static_cast<size_t>(std::max<int64_t>(n_records, 1)) * kMoments * sizeof(float), 256);
 }
 
-cudaError_t launch_render_bwd(const FrameParams &, const psi_surfels &, const FeatView &, const float4 *,
-                              const uint32_t *, const uint32_t *, const float *, const float *, const float *,
-                              const psi_grads &, void *, DevStatus *, cudaStream_t)
+cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
+                              const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
+                              const float *g_T, const psi_grads &g, void *ws, DevStatus *status, cudaStream_t st)
 {
-    return cudaErrorNotSupported;
+    const int64_t R = fp.n * fp.n_views;
+    cudaError_t e = cudaMemsetAsync(ws, 0, render_bwd_workspace_bytes(R), st);
+    if (e != cudaSuccess || R == 0 || fp.n_tiles_total == 0) return e;
+    BwdArgs a{};
+    a.records = records;
+    a.vals = vals;
+    a.ranges = ranges;
+    a.feat = f.data;
+    a.fscale = f.scale;
+    a.D = f.dim;
+    a.g_rgb = g_rgb;
+    a.g_F = f.data ? g_F : nullptr;
+    a.g_T = g_T;
+    a.g_col = g.rgb;
+    a.g_feat = f.data ? g.feat : nullptr;
+    a.moments = static_cast<float *>(ws);
+    a.status = status;
+    const int ch = (f.dim % 32 == 0) ? 32 : 16;
+    const int K = fp.top_k;
+    if (K == 0)
+        e = launch_k<0>(fp, f, a, ch, st);
+    else if (K <= 8)
+        e = launch_k<8>(fp, f, a, ch, st);
+    else if (K <= 16)
+        e = launch_k<16>(fp, f, a, ch, st);
+    else
+        e = launch_k<32>(fp, f, a, ch, st);
+    if (e != cudaSuccess) return e;
+    chain_kernel<<<static_cast<unsigned>((R + 255) / 256), 256, 0, st>>>(fp, s, static_cast<const float4 *>(ws), g);
+    return cudaGetLastError();
 }
 
 } // namespace psi

@@ -71,15 +71,8 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     int last = 0;
     bool done = !inside;
-    float kw[KMAX > 0 ? KMAX : 1];
-    int kp[KMAX > 0 ? KMAX : 1];
-    float worst_w = -1.0f;
-    int worst_p = 0x7fffffff, worst_i = 0;
-#pragma unroll
-    for (int s = 0; s < (KMAX > 0 ? KMAX : 1); ++s) {
-        kw[s] = (s < K) ? -1.0f : __int_as_float(0x7f800000);
-        kp[s] = 0x7fffffff;
-    }
+    TopK<(KMAX > 0 ? KMAX : 1)> top;
+    top.init(K);
     float facc[KMAX == 0 ? CH : 1];
 #pragma unroll
     for (int c = 0; c < (KMAX == 0 ? CH : 1); ++c) facc[c] = 0.0f;
@@ -117,29 +110,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
                     }
                 }
             }
-            if constexpr (KMAX > 0) {
-                const bool better = hit && w > worst_w;
-                if (__any_sync(0xffffffffu, better)) {
-                    if (better) {
-#pragma unroll
-                        for (int s = 0; s < KMAX; ++s)
-                            if (s == worst_i) {
-                                kw[s] = w;
-                                kp[s] = pos;
-                            }
-                        worst_w = kw[0];
-                        worst_p = kp[0];
-                        worst_i = 0;
-#pragma unroll
-                        for (int s = 1; s < KMAX; ++s)
-                            if (kw[s] < worst_w || (kw[s] == worst_w && kp[s] > worst_p)) {
-                                worst_w = kw[s];
-                                worst_p = kp[s];
-                                worst_i = s;
-                            }
-                    }
-                }
-            }
+            if constexpr (KMAX > 0) top.offer(hit, w, pos);
             if (hit) {
                 T = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
                 last = pos + 1;
@@ -170,29 +141,16 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
     if constexpr (KMAX == 0) {
         if (a.F && a.feat) store_feat<CH>(a.F, a.F_bf16 != 0, pix, a.D, a.c0, facc, a.fscale);
     } else {
-        // selected set in list order (odd-even transposition sort on position)
-#pragma unroll
-        for (int round = 0; round < KMAX; ++round) {
-#pragma unroll
-            for (int s = (round & 1); s + 1 < KMAX; s += 2) {
-                if (kp[s] > kp[s + 1]) {
-                    const int tp = kp[s];
-                    kp[s] = kp[s + 1];
-                    kp[s + 1] = tp;
-                    const float tw = kw[s];
-                    kw[s] = kw[s + 1];
-                    kw[s + 1] = tw;
-                }
-            }
-        }
+        top.sort_by_pos();
         int32_t sid[KMAX];
 #pragma unroll
         for (int s = 0; s < KMAX; ++s)
-            sid[s] = (s < K && kp[s] != 0x7fffffff) ? static_cast<int32_t>(static_cast<int64_t>(a.vals[list0 + kp[s]]) - surf0)
-                                                    : -1;
+            sid[s] = top.valid(s, K) ? static_cast<int32_t>(static_cast<int64_t>(a.vals[list0 + top.p[s]]) - surf0) : -1;
         if (a.topk_ids) {
             int32_t *dst = a.topk_ids + pix * K;
-            for (int s = 0; s < K; ++s) dst[s] = sid[s];
+#pragma unroll
+            for (int s = 0; s < KMAX; ++s)
+                if (s < K) dst[s] = sid[s];
         }
         if (a.F && a.feat) {
             for (int c0 = 0; c0 < a.D; c0 += CH) {
@@ -205,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
                     float f[CH];
                     load_feat<DT, CH>(a.feat, sid[s], a.D, c0, f);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) acc[c] = __fmaf_rn(kw[s], f[c], acc[c]);
+                    for (int c = 0; c < CH; ++c) acc[c] = __fmaf_rn(top.w[s], f[c], acc[c]);
                 }
                 store_feat<CH>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
             }

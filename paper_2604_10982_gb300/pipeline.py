@@ -144,6 +144,26 @@ class Renderer:
         psi.psi_render_fwd(self.ctx, feats, self.records, self.vals, self.ranges, self.cams, self.V, self.n, self.opts,
                            out, stream)
 
+    # a5
+    def backward(self, scene: DeviceScene, g_rgb, g_F=None, g_T=None, grads=None, stream=None):
+        """Gradients (float32, [N, ...]) of L = <g_rgb, rgb> + <g_F, F> + <g_T, T>
+        for the frame last rendered by this renderer."""
+        dev = self.dev
+        n, D = self.n, scene.D
+        if grads is None:
+            grads = dict(mu=torch.zeros(n, 3, device=dev), tu=torch.zeros(n, 3, device=dev),
+                         tv=torch.zeros(n, 3, device=dev), scale=torch.zeros(n, 2, device=dev),
+                         opacity=torch.zeros(n, device=dev), rgb=torch.zeros(n, 3, device=dev),
+                         feat=torch.zeros(n, D, device=dev) if D else None)
+        if not hasattr(self, "ws_bwd"):
+            self.ws_bwd = torch.empty(psi.render_bwd_workspace_size(self.V * self.n), dtype=torch.uint8, device=dev)
+        gs = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
+        psi.psi_render_bwd(self.ctx, scene.surfels_struct(), scene.features_struct(), self.records, self.vals,
+                           self.ranges, self.cams, self.V, self.opts, g_rgb.contiguous(),
+                           None if g_F is None else g_F.contiguous(), None if g_T is None else g_T.contiguous(),
+                           gs, self.ws_bwd, stream)
+        return grads
+
     def frame(self, scene: DeviceScene, want_F: bool = True, stream=None):
         self.project(scene, stream)
         self.intersect(stream)
@@ -173,3 +193,31 @@ def make_renderer(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, wan
     need = r.required_pairs(scene)
     r.set_capacity(max(min_capacity, int(need * headroom) + 16))
     return r
+
+
+class PsiRender(torch.autograd.Function):
+    """Differentiable frame: (mu, tu, tv, scale, opacity, rgb, feat) -> (rgb image
+    [3, P], feature map [P, D], transmittance [P]). The backward pass is the
+    library's hand-written adjoint (psi_render_bwd), which recomputes the Top-K
+    sets instead of storing per-pixel lists. The tensors must be the ones held
+    by ``scene``; one frame per renderer may be in flight between forward and
+    backward (the renderer's buffers hold it)."""
+
+    @staticmethod
+    def forward(ctx, renderer, scene, mu, tu, tv, scale, opacity, rgb, feat):
+        renderer.frame(scene)
+        ctx.renderer, ctx.scene = renderer, scene
+        F = renderer.F.float().clone() if renderer.F is not None else torch.zeros(0, device=mu.device)
+        return renderer.rgb.clone(), F, renderer.T.clone()
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_F, g_T):
+        r, sc = ctx.renderer, ctx.scene
+        g = r.backward(sc, g_rgb, g_F if (g_F is not None and g_F.numel()) else None, g_T)
+        return (None, None, g["mu"], g["tu"], g["tv"], g["scale"], g["opacity"], g["rgb"], g["feat"])
+
+
+def render_autograd(renderer, scene):
+    """Run one differentiable frame through PsiRender."""
+    return PsiRender.apply(renderer, scene, scene.mu, scene.tu, scene.tv, scene.scale, scene.opacity, scene.rgb,
+                           scene.q)

@@ -1,0 +1,144 @@
+"""Hand-written adjoint vs the oracle's FP64 gradient (needs a GPU).
+
+Upstream gradients are zeroed on pixels the forward comparison excuses
+(threshold straddles, near ties, ill-conditioned), on both sides, so the
+comparison is exact apart from float32 rounding: the gradient is linear in
+the upstream gradient."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc
+from paper_2604_10982_gb300 import scenegen as sg
+
+from .gpu_common import flags, multi_cams, opts_of
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_10982_gb300 import psi
+    return psi.Context(0)
+
+
+def _upstream(cams, D, seed, pixel_mask=None):
+    P = sum(c.width * c.height for c in cams)
+    gC = sg.make_upstream(3 * P, seed, 0).reshape(3, P)
+    gF = sg.make_upstream(D * P, seed, 1).reshape(P, D) if D else None
+    gT = sg.make_upstream(P, seed, 2)
+    if pixel_mask is not None:
+        gC = gC * pixel_mask[None, :]
+        gT = gT * pixel_mask
+        if gF is not None:
+            gF = gF * pixel_mask[:, None]
+    return gC, gF, gT
+
+
+def _grad_compare(ctx, w, cams, o, D, tol=1e-3, sample_pixels=None):
+    from paper_2604_10982_gb300 import pipeline as pl
+    scene = pl.DeviceScene(w.surfels, w.features if D else None)
+    r = pl.make_renderer(ctx, scene, cams, opts_of(o), D=D)
+    r.frame(scene)
+    # excusal mask from the oracle's forward diagnostics, evaluated only on the
+    # pixels that carry upstream gradient (all, or a sample)
+    P = int(r.pix_base[-1])
+    mask = np.zeros(P, np.float32)
+    cand = np.arange(P) if sample_pixels is None else np.asarray(sample_pixels)
+    for v, cam in enumerate(cams):
+        a, b = int(r.pix_base[v]), int(r.pix_base[v + 1])
+        idx = cand[(cand >= a) & (cand < b)] - a
+        if len(idx) == 0:
+            continue
+        ref = orc.render(w.surfels, cam, o, feat=w.features if D else None, pixels=orc.all_pixels(cam)[idx])
+        st, ic, nt = flags(ref, cam)
+        mask[a + idx] = (~(st | ic | nt)).astype(np.float32)
+    gC, gF, gT = _upstream(cams, D, 3, mask)
+    tgC = torch.from_numpy(np.ascontiguousarray(gC)).cuda()
+    tgF = torch.from_numpy(np.ascontiguousarray(gF)).cuda() if D else None
+    tgT = torch.from_numpy(gT).cuda()
+    g = r.backward(scene, tgC, tgF, tgT)
+    torch.cuda.synchronize()
+    st, _ = ctx.status_fetch()
+    assert st == 0
+    # oracle gradient, summed over views
+    ref = {k: 0.0 for k in KEYS}
+    for v, cam in enumerate(cams):
+        a, b = int(r.pix_base[v]), int(r.pix_base[v + 1])
+        sel = np.nonzero(mask[a:b])[0]
+        pix = orc.all_pixels(cam)[sel]
+        gv = orc.render_grad(w.surfels, cam, o, gC[:, a:b].T[sel], feat=w.features if D else None,
+                             gF=gF[a:b][sel] if D else None, gT=gT[a:b][sel], pixels=pix)
+        for k in KEYS:
+            ref[k] = ref[k] + gv[k]
+    report = {}
+    for k in KEYS:
+        if k == "feat" and not D:
+            continue
+        gk = g[k].cpu().numpy().astype(np.float64).reshape(ref[k].shape)
+        den = np.linalg.norm(ref[k])
+        rel = np.linalg.norm(gk - ref[k]) / max(den, 1e-30)
+        report[k] = rel
+        assert den > 0, k
+        assert rel < tol, (k, rel)
+    return report
+
+
+def test_grad_crop_topk(ctx):
+    w = sg.crop_scene(n=500, d=32, size=64)
+    o = orc.Opts(mode=orc.EXACT, top_k=16)
+    rep = _grad_compare(ctx, w, w.cameras, o, 32)
+    print(rep)
+
+
+def test_grad_crop_dense(ctx):
+    w = sg.crop_scene(n=500, d=32, size=64)
+    o = orc.Opts(mode=orc.AABB, top_k=0)
+    _grad_compare(ctx, w, w.cameras, o, 32)
+
+
+@pytest.mark.parametrize("K", [1, 8])
+def test_grad_box_multiview(ctx, K):
+    w = sg.dense_box(n=4000, d=16)
+    o = orc.Opts(mode=orc.EXACT, top_k=K, opacity_radius=True)
+    _grad_compare(ctx, w, multi_cams(), o, 16)
+
+
+def test_grad_rgb_only(ctx):
+    w = sg.dense_box(n=3000, d=16)
+    o = orc.Opts(mode=orc.SPHERE, top_k=0)
+    _grad_compare(ctx, w, multi_cams()[:1], o, 0)
+
+
+def test_grad_full_size_sampled_pixels(ctx):
+    """960x540, 500k surfels, D=128, K=16: upstream gradient on 48 sampled
+    pixels, full gradient vectors compared."""
+    w = sg.grad_scene()
+    cam = w.cameras[0]
+    rng = np.random.default_rng(1)
+    pix = rng.choice(cam.width * cam.height, 48, replace=False)
+    o = orc.Opts(mode=orc.EXACT, top_k=16)
+    _grad_compare(ctx, w, w.cameras, o, 128, sample_pixels=pix)
+
+
+def test_autograd_function(ctx):
+    from paper_2604_10982_gb300 import pipeline as pl
+    w = sg.crop_scene(n=300, d=16, size=48)
+    o = orc.Opts(mode=orc.EXACT, top_k=8)
+    scene = pl.DeviceScene(w.surfels, w.features)
+    for t in (scene.mu, scene.tu, scene.tv, scene.scale, scene.opacity, scene.rgb, scene.q):
+        t.requires_grad_(True)
+    r = pl.make_renderer(ctx, scene, w.cameras, opts_of(o), D=16)
+    rgb, F, T = pl.render_autograd(r, scene)
+    loss = (rgb * 0.3).sum() + (F * 0.1).sum() - T.sum()
+    loss.backward()
+    g = r.backward(scene, torch.full_like(rgb, 0.3), torch.full_like(F, 0.1), torch.full_like(T, -1.0))
+    torch.cuda.synchronize()
+    assert torch.allclose(scene.mu.grad, g["mu"], rtol=1e-4, atol=1e-6)
+    assert torch.allclose(scene.q.grad, g["feat"], rtol=1e-4, atol=1e-6)
+    assert float(scene.opacity.grad.abs().sum()) > 0
