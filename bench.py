@@ -1,0 +1,513 @@
+#!/usr/bin/env python3
+"""Benchmark of the surfel rendering hot path on GB300.
+
+Workload (the configuration the headline metric is quoted on): 3M surfels on a
+synthetic 60 m street (ground + two facades), a 32-frame trajectory of
+1920x1080 pinhole views (f=960, y from 5 m to 55 m), D=128 features stored in
+BF16, Top-K Hard Selection with K=8, EXACT ellipse-vs-tile binning, Q=100 BF16
+queries. One step = one frame through every step of the path: project,
+intersect, sort, Top-K render, tensor-core decode, and the hand-written
+adjoint with seeded N(0,1) upstream gradients. Each stage of each frame is a
+captured CUDA graph; frames are timed with CUDA events on the launching
+stream. The plain FP32 form (SPHERE bounds, dense FP32 features) is measured
+beside it, and the CPU oracle on a bounded pixel sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl psi|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "frames/s at 1080p, 3M surfels, D=128 (fwd; fwd+bwd ms) vs plain FP32, 1×GB300"
+PAPER_CONTEXT = ("Table 3 of the paper: Full Method 22 ms / 45 FPS, Baseline 46 ms / 22 FPS, on an RTX A6000, "
+                 "resolution / surfel count / D / K not stated (different hardware and data: context only)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="psi", choices=["psi", "reference"])
+    ap.add_argument("--surfels", type=int, default=3_000_000)
+    ap.add_argument("--frames", type=int, default=32)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=16)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def roofline_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2604_10982_gb300", "csrc", e["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return e["bytes_per_launch"] if h == e.get("sha256_16") else None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_frame_sample(w, cam, q_bf16_deq, Qm, gC_fn, target_s, opts_kw, max_pixels=4096):
+    """Time the CPU oracle on one frame: the per-frame setup (binning of all
+    surfels, canonical order) plus a pixel sample of the per-pixel work
+    (forward, gradient, decode), extrapolated to the whole frame."""
+    from oracle import oracle as orc
+    o = orc.Opts(**opts_kw)
+    t0 = time.perf_counter()
+    b = orc.bin_view(w.surfels, cam, o)
+    orc.canonical_order(b)
+    t_fixed = time.perf_counter() - t0
+    P = cam.width * cam.height
+    rng = np.random.default_rng(0)
+    n_pix = 8
+    t_pix = None
+    while True:
+        pix = orc.all_pixels(cam)[rng.choice(P, n_pix, replace=False)]
+        t1 = time.perf_counter()
+        out = orc.render(w.surfels, cam, o, feat=q_bf16_deq, pixels=pix, b=b)
+        gC, gF, gT = gC_fn(n_pix)
+        orc.render_grad(w.surfels, cam, o, gC, feat=q_bf16_deq, gF=gF, gT=gT, pixels=pix, b=b)
+        orc.decode(out["F"], Qm, out["T"])
+        dt = time.perf_counter() - t1
+        t_pix = dt / n_pix
+        if dt >= 0.25 * target_s or n_pix >= max_pixels:
+            break
+        n_pix = min(max_pixels, max(n_pix * 2, int(n_pix * 0.5 * target_s / max(dt, 1e-3))))
+    frame_s = t_fixed + t_pix * P
+    return dict(frame_s=frame_s, t_fixed=t_fixed, t_pix=t_pix, sample_pixels=n_pix,
+                threads=orc.num_threads())
+
+
+def run_reference(args):
+    """The oracle, timed on the host cores, as the reference arm."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2604_10982_gb300 import scenegen as sg
+    w = sg.panoptic_scene(n=args.surfels, frames=args.frames, with_features=True)
+    deq = bf16_round(w.features).astype(np.float64)
+    Qm = bf16_round(w.queries).astype(np.float64)
+    D = w.features.shape[1]
+    gfn = lambda n: (sg.make_upstream(3 * n, 3, 0).reshape(n, 3), sg.make_upstream(D * n, 3, 1).reshape(n, D),
+                     sg.make_upstream(n, 3, 2))
+    kw = dict(mode=2, top_k=8, opacity_radius=True)
+    times = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        cam = w.cameras[k % len(w.cameras)]
+        info = oracle_frame_sample(w, cam, deq, Qm, gfn, args.cpu_seconds / max(args.steps + args.warmup, 1), kw,
+                                   max_pixels=64)
+        if k >= args.warmup:
+            times.append(info["frame_s"])
+    fps = 1.0 / float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / fps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, graph=False),
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": info["threads"], "kind": "oracle",
+                             "sample": f"per step: binning of all {args.surfels} surfels + forward, gradient and "
+                                       f"decode of {info['sample_pixels']} random pixels of one 1920x1080 frame, "
+                                       f"extrapolated to the frame's {1920 * 1080} pixels"},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round float32 to the nearest BF16 value (ties to even), as float32."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def workload_config(args, graph=True):
+    return {"workload": f"panoptic street: {args.surfels} surfels, {args.frames}-frame trajectory of 1920x1080 views "
+                        f"(f=960), D=128 BF16 features, Top-K K=8, EXACT tiles, Q=100 BF16 queries",
+            "surfels": args.surfels, "resolution": "1920x1080", "feat_dim": 128, "feat_storage": "bf16",
+            "top_k": 8, "queries": 100, "isect": "exact+opacity-radius", "frames": args.frames,
+            "step": "project+intersect+sort+render+decode+backward of one frame", "cuda_graph": graph,
+            "l2": "inputs larger than L2 (surfels 180 MB + BF16 features 768 MB read per frame; 129 MB L2)"}
+
+
+# ---------------------------------------------------------------- main arm
+def run_psi(args):
+    import torch
+
+    from paper_2604_10982_gb300 import pipeline as pl, psi, scenegen as sg
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_setup = time.time()
+    w = sg.panoptic_scene(n=args.surfels, frames=args.frames, with_features=True)
+    cams = w.cameras
+    D, K, nq = 128, 8, 100
+    ctx = psi.Context(local)
+    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.BF16, device=dev)
+    Qd = torch.from_numpy(w.queries).to(dev).to(torch.bfloat16).contiguous()
+    P = cams[0].width * cams[0].height
+    gC_h = torch.from_numpy(sg.make_upstream(3 * P, 3, 0).reshape(3, P)).pin_memory()
+    gF_h = torch.from_numpy(sg.make_upstream(D * P, 3, 1).reshape(P, D)).pin_memory()
+    gT_h = torch.from_numpy(sg.make_upstream(P, 3, 2)).pin_memory()
+    gC, gF, gT = gC_h.to(dev), gF_h.to(dev), gT_h.to(dev)
+
+    opts = psi.default_opts(mode=psi.EXACT, top_k=K, opacity_radius=1)
+    r = pl.Renderer(ctx, scene.n, [cams[0]], opts, 1024, D=D, F_dtype=psi.BF16, device=dev)
+    need = 0
+    for c in cams:
+        r.set_cameras([c])
+        need = max(need, r.required_pairs(scene))
+    r.set_capacity(int(need * 1.15) + 1024)
+    ids = torch.empty(r.n_pix, dtype=torch.int32, device=dev)
+    grads = dict(mu=torch.zeros(scene.n, 3, device=dev), tu=torch.zeros(scene.n, 3, device=dev),
+                 tv=torch.zeros(scene.n, 3, device=dev), scale=torch.zeros(scene.n, 2, device=dev),
+                 opacity=torch.zeros(scene.n, device=dev), rgb=torch.zeros(scene.n, 3, device=dev),
+                 feat=torch.zeros(scene.n, D, device=dev))
+
+    def stage_fns(f):
+        def proj():
+            r.set_cameras([cams[f]])
+            r.project(scene)
+
+        def isect():
+            r.set_cameras([cams[f]])
+            r.intersect()
+
+        def srt():
+            r.sort()
+
+        def rend():
+            r.set_cameras([cams[f]])
+            r.render(scene)
+
+        def dec():
+            psi.psi_decode_queries(ctx, r.F, r.n_pix, D, Qd, nq, r.T, ids)
+
+        def bwd():
+            for g in grads.values():
+                g.zero_()
+            r.set_cameras([cams[f]])
+            r.backward(scene, gC, gF, gT, grads=grads)
+
+        return [proj, isect, srt, rend, dec, bwd]
+
+    names = ["project", "intersect", "sort", "render_fwd", "decode", "render_bwd"]
+    # warm every code path once (lazy buffers, function attributes), then capture
+    for fn in stage_fns(0):
+        fn()
+    torch.cuda.synchronize()
+    use_graph = not args.no_graph
+    graphs = None
+    if use_graph:
+        cap_stream = torch.cuda.Stream(device=dev)
+        graphs = []
+        for f in range(len(cams)):
+            gs = []
+            for fn in stage_fns(f):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=cap_stream, capture_error_mode="relaxed"):
+                    fn()
+                gs.append(g)
+            graphs.append(gs)
+        torch.cuda.synchronize()
+
+    def run_frame(f, evs=None):
+        stages = graphs[f] if use_graph else stage_fns(f)
+        for i, st in enumerate(stages):
+            st.replay() if use_graph else st()
+            if evs is not None:
+                evs[i + 1].record()
+
+    def frame_index(k):
+        return (k + rank * 7) % len(cams)
+
+    for k in range(args.warmup):
+        run_frame(frame_index(k))
+    torch.cuda.synchronize()
+    st, req = ctx.status_fetch()
+    assert st == 0, f"device status {st} (required pairs {req})"
+    setup_s = time.time() - t_setup
+
+    # ---- timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start.record()
+    for k in range(args.steps):
+        evs[k][0].record()
+        run_frame(frame_index(k), evs[k])
+    t_end.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(len(names))] for k in range(args.steps)])
+    st, req = ctx.status_fetch()
+    assert st == 0, f"device status {st}"
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frame_ms = stage.sum(1)
+    fwd_ms = stage[:, :5].sum(1)
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- per-frame statistics (outside the timed region)
+    pairs, nlast_sum, nonempty = [], [], []
+    for f in sorted(set(frame_index(k) for k in range(args.steps))):
+        run_frame(f)
+        torch.cuda.synchronize()
+        pairs.append(int(r.num_pairs.item()))
+        nlast_sum.append(float(r.n_last.to(torch.float64).sum().item()))
+        nonempty.append(int(((1.0 - r.T) >= 1e-4).sum().item()))
+    n_tiles = r.n_tiles
+
+    # ---- roofline of the dominant kernel
+    mean_stage = stage.mean(0)
+    dom = int(np.argmax(mean_stage))
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    launch_s = mean_stage[dom] / 1000.0
+    kname = names[dom]
+    if kname == "render_fwd":
+        flop = 20.0 * np.mean(nlast_sum) + 2.0 * K * D * np.mean(nonempty)
+        roof = {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": flop / launch_s / 1e12,
+                "peak": fp32_peak, "unit": "TFLOP/s",
+                "work": "20 FP32 flop per (pixel, list entry up to its last composited surfel) + 2KD per pixel"}
+    elif kname == "render_bwd":
+        flop = 90.0 * np.mean(nlast_sum) + 4.0 * K * D * np.mean(nonempty)
+        roof = {"kernel": "render_bwd_kernel", "bound": "alu", "achieved": flop / launch_s / 1e12,
+                "peak": fp32_peak, "unit": "TFLOP/s",
+                "work": "90 FP32 flop per (pixel, list entry up to its last composited surfel) + 4KD per pixel"}
+    elif kname == "sort":
+        key_bits = r.key_bits
+        passes = max(2, (key_bits + 7) // 8)
+        passes += passes & 1
+        byts = passes * np.mean(pairs) * 32.0
+        roof = {"kernel": "radix sort passes", "bound": "hbm", "achieved": byts / launch_s / 1e9,
+                "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                "work": "32 B per pair per pass (key+value read twice, written once)"}
+    else:
+        byts = 64.0 * args.surfels
+        roof = {"kernel": kname, "bound": "hbm", "achieved": byts / launch_s / 1e9,
+                "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "work": "64 B per surfel"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_source"] = ("measured HBM (MEASURED_PEAKS.json)" if roof["bound"] == "hbm" else
+                           f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz")
+    roof["traffic"] = roofline_traffic(roof["kernel"])
+    roof["launch_ms"] = float(mean_stage[dom])
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        ids_h = torch.empty(r.n_pix, dtype=torch.int32).pin_memory()
+        rgb_h = torch.empty(3, r.n_pix, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(args.e2e_steps):
+            gC.copy_(gC_h, non_blocking=True)
+            gF.copy_(gF_h, non_blocking=True)
+            gT.copy_(gT_h, non_blocking=True)
+            run_frame(frame_index(k))
+            ids_h.copy_(ids, non_blocking=True)
+            rgb_h.copy_(r.rgb, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * args.e2e_steps / (e2e_ms / 1000.0), "unit": "frames/s",
+               "h2d_bytes_per_step": int(gC_h.numel() * 4 + gF_h.numel() * 4 + gT_h.numel() * 4),
+               "d2h_bytes_per_step": int(ids_h.numel() * 4 + rgb_h.numel() * 4),
+               "what": "per step: upstream gradients copied from pinned host memory, the frame (all stages), "
+                       "ids and RGB read back to pinned host memory"}
+
+    # ---- plain FP32 form (paper's Baseline row): SPHERE bounds, dense FP32 features
+    plain = None
+    if args.plain_steps > 0:
+        del graphs
+        torch.cuda.empty_cache()
+        scene32 = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.F32, device=dev)
+        po = psi.default_opts(mode=psi.SPHERE, top_k=0, opacity_radius=0)
+        rp = pl.Renderer(ctx, scene.n, [cams[0]], po, 1024, D=D, F_dtype=psi.F32, device=dev)
+        need = 0
+        for f in range(min(args.plain_steps + 1, len(cams))):
+            rp.set_cameras([cams[frame_index(f)]])
+            need = max(need, rp.required_pairs(scene32))
+        rp.set_capacity(int(need * 1.15) + 1024)
+        pt = []
+        for k in range(args.plain_steps + 1):
+            f = frame_index(k)
+            rp.set_cameras([cams[f]])
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            rp.frame(scene32)
+            e[1].record()
+            for g in grads.values():
+                g.zero_()
+            rp.backward(scene32, gC, gF, gT, grads=grads)
+            e[2].record()
+            torch.cuda.synchronize()
+            if k > 0:
+                pt.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), int(rp.num_pairs.item())))
+        pt = np.array(pt)
+        plain = {"fwd_ms": float(pt[:, 0].mean()), "fwd_bwd_ms": float((pt[:, 0] + pt[:, 1]).mean()),
+                 "fwd_frames_per_s": float(1000.0 / pt[:, 0].mean()),
+                 "frames_per_s": float(1000.0 / (pt[:, 0] + pt[:, 1]).mean()),
+                 "pairs_per_frame": float(pt[:, 2].mean()), "frames": int(len(pt)),
+                 "form": "SPHERE tiles, dense FP32 features (no Top-K), single view per launch, no graph, no decode"}
+        del scene32, rp
+
+    # ---- CPU oracle on a bounded sample (rank 0)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        deq = bf16_round(w.features).astype(np.float64)
+        Qm = bf16_round(w.queries).astype(np.float64)
+        gfn = lambda n: (gC_h.numpy()[:, :n].T.astype(np.float64), gF_h.numpy()[:n].astype(np.float64),
+                         gT_h.numpy()[:n].astype(np.float64))
+        info = oracle_frame_sample(w, cams[0], deq, Qm, gfn, args.cpu_seconds,
+                                   dict(mode=2, top_k=K, opacity_radius=True))
+        cpu = {"value": 1.0 / info["frame_s"], "unit": "frames/s", "cores": info["threads"], "kind": "oracle",
+               "sample": f"frame 0: binning + canonical order of all {args.surfels} surfels ({info['t_fixed']:.2f} s) "
+                         f"and forward+gradient+decode of {info['sample_pixels']} random pixels "
+                         f"({info['t_pix'] * 1e3:.1f} ms/pixel), extrapolated to {P} pixels"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, use_graph),
+        "fwd_frames_per_s": float(1000.0 / fwd_ms.mean()), "fwd_bwd_ms": float(frame_ms.mean()),
+        "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
+        "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)},
+        "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
+        "plain_fp32": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),
+        "clocks": clk, "paper_context": PAPER_CONTEXT, "setup_s": setup_s,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_psi(args)
+
+
+if __name__ == "__main__":
+    main()

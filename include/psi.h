@@ -144,9 +144,12 @@ void psi_ctx_destroy(psi_ctx *ctx);
 /* Message of the last failing call on ctx (never NULL; "" if none). */
 const char *psi_last_error(const psi_ctx *ctx);
 /* Synchronises `stream`, copies the device status word to *status_out
- * (0 = clean, else a PSI_ERR_* code) and *required_pairs (the pair count a
- * capacity overflow needed; may be NULL), then clears the word. */
-int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *required_pairs);
+ * (0 = clean, else a PSI_ERR_* code; TIMEOUT before CAPACITY before
+ * INVALID_ARG) and *detail (may be NULL): for PSI_ERR_CAPACITY the pair count
+ * the overflowing frame needed, for PSI_ERR_TIMEOUT the code of the first wait
+ * that gave up (1 render, 2/3 adjoint passes, 4-6 decode, 7 drain); then
+ * clears the word. */
+int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *detail);
 /* Fill *o with the defaults: EXACT, K=0, chi2=9, z_near=0.2, no opacity
  * radius, 16x16 tiles, t_eps=1e-4. */
 void psi_default_opts(psi_render_opts *o);

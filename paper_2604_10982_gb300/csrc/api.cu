@@ -144,7 +144,7 @@ void psi_ctx_destroy(psi_ctx *ctx)
 
 const char *psi_last_error(const psi_ctx *ctx) { return ctx ? ctx->err : "NULL context"; }
 
-int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *required_pairs)
+int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *detail)
 {
     if (!ctx || !status_out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard g(ctx->device);
@@ -164,7 +164,7 @@ int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64
     else if (h.flags & (1 << PSI_ERR_INVALID_ARG))
         code = PSI_ERR_INVALID_ARG;
     *status_out = code;
-    if (required_pairs) *required_pairs = static_cast<int64_t>(h.required_pairs);
+    if (detail) *detail = code == PSI_ERR_TIMEOUT ? static_cast<int64_t>(h.wait_site) : static_cast<int64_t>(h.required_pairs);
     return PSI_OK;
 }
 

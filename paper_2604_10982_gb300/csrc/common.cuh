@@ -11,10 +11,11 @@
 namespace psi {
 
 // Device status word layout (see psi_status_fetch): [0] OR of error codes as
-// bits (1 << code), [1] unused, [2..3] int64 pairs required on overflow.
+// bits (1 << code), [1] code of the first bounded wait that gave up,
+// [2..3] int64 pairs required on overflow.
 struct DevStatus {
     int32_t flags;
-    int32_t pad;
+    int32_t wait_site;
     unsigned long long required_pairs;
 };
 
@@ -22,6 +23,17 @@ __device__ __forceinline__ void raise_status(DevStatus *st, int code)
 {
     if (st) atomicOr(&st->flags, 1 << code);
 }
+
+// wait sites (reported by psi_status_fetch on PSI_ERR_TIMEOUT)
+enum WaitSite {
+    kSiteRenderFwd = 1,
+    kSiteRenderBwdA = 2,
+    kSiteRenderBwdB = 3,
+    kSiteDecodeQ = 4,
+    kSiteDecodeLoad = 5,
+    kSiteDecodeMma = 6,
+    kSiteDrain = 7
+};
 
 struct ViewParams {
     float R[9];
@@ -111,14 +123,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; returns false (and raises TIMEOUT) on give-up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DevStatus *st)
+// Bounded wait on an mbarrier phase; returns false (and raises TIMEOUT with
+// the wait site) on give-up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DevStatus *st, int site = 0)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
         if (global_ns() - t0 > kWaitLimitNs) {
-            raise_status(st, PSI_ERR_TIMEOUT);
+            if (st) {
+                atomicCAS(&st->wait_site, 0, site);
+                raise_status(st, PSI_ERR_TIMEOUT);
+            }
             return false;
         }
     }

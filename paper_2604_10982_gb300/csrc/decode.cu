@@ -169,9 +169,9 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(const __grid_consta
         for (int a = 0; a < atoms; ++a) tma_load_2d(q_smem + a * q_atom_bytes, &map_q, a * 64, 0, &q_bar);
         q_pending = true;
         for (; t_issued < kStages && t_issued < my_n; ++t_issued) issue_tile(t_issued);
-        fail = !mbar_wait(&q_bar, 0, p.status);
+        fail = !mbar_wait(&q_bar, 0, p.status, kSiteDecodeQ);
         q_pending = fail;
-        if (!fail) fail = !mbar_wait(&full[0], 0, p.status);
+        if (!fail) fail = !mbar_wait(&full[0], 0, p.status, kSiteDecodeLoad);
         if (!fail) {
             t_waited = 1;
             tc_fence_after();
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(const __grid_consta
     for (int i = 0; i < my_n && !stop; ++i) {
         fail = false;
         if (tid == 0 && i + 1 < my_n) {
-            if (mbar_wait(&full[(i + 1) % kStages], ((i + 1) / kStages) & 1, p.status)) {
+            if (mbar_wait(&full[(i + 1) % kStages], ((i + 1) / kStages) & 1, p.status, kSiteDecodeLoad)) {
                 t_waited = i + 2;
                 tc_fence_after();
                 issue_mma(i + 1);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(const __grid_consta
                 fail = true;
             }
         }
-        if (mbar_wait(&mma_bar[i & 1], (i >> 1) & 1, p.status))
+        if (mbar_wait(&mma_bar[i & 1], (i >> 1) & 1, p.status, kSiteDecodeMma))
             m_waited = i + 1;
         else
             fail = true;

@@ -108,7 +108,14 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
         s_maxlast = 0;
     }
     __syncthreads();
-    int uses[2] = {0, 0}; // completed phases per buffer (uniform over the CTA)
+    int uses0 = 0, uses1 = 0; // completed phases per buffer (uniform over the CTA)
+    auto parity = [&](int buf) { return static_cast<uint32_t>((buf ? uses1 : uses0) & 1); };
+    auto used = [&](int buf) {
+        if (buf)
+            ++uses1;
+        else
+            ++uses0;
+    };
 
     // ---------------- pass A: forward recompute
     if (wid == 0)
@@ -123,8 +130,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
     bool ok = true;
     for (int b = 0; b < nb; ++b) {
         const int buf = b & 1;
-        ok = mbar_wait(&S.bar[buf], uses[buf] & 1, a.status);
-        ++uses[buf];
+        ok = mbar_wait(&S.bar[buf], parity(buf), a.status, kSiteRenderBwdA);
+        used(buf);
         consumed = b + 1;
         const int cnt = min(kBatch, n - b * kBatch);
         if (ok) {
@@ -148,14 +155,16 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
         }
         const int alive = __syncthreads_count(!done);
         if (alive == 0) break;
-        if (wid == 0 && b + 2 < nb) {
-            issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
+        if (b + 2 < nb) {
+            // every thread counts the batch (uniform phase bookkeeping); warp 0 issues it
+            if (wid == 0)
+                issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
             ++issued;
         }
     }
     for (int b = consumed; b < issued; ++b) {
-        mbar_wait(&S.bar[b & 1], uses[b & 1] & 1, a.status);
-        ++uses[b & 1];
+        mbar_wait(&S.bar[b & 1], parity(b & 1), a.status, kSiteDrain);
+        used(b & 1);
     }
     if (__syncthreads_or(!ok)) return;
 
@@ -221,8 +230,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
     for (int k = 0; k < nbB; ++k) {
         const int buf = k & 1;
         const int bi = nbB - 1 - k;
-        ok = mbar_wait(&S.bar[buf], uses[buf] & 1, a.status);
-        ++uses[buf];
+        ok = mbar_wait(&S.bar[buf], parity(buf), a.status, kSiteRenderBwdB);
+        used(buf);
         consumed = k + 1;
         const int cnt = min(kBatch, maxlast - bi * kBatch);
         if (ok) {
@@ -330,15 +339,16 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
             }
         }
         __syncthreads();
-        if (wid == 0 && k + 2 < nbB) {
+        if (k + 2 < nbB) {
             const int bi2 = nbB - 1 - (k + 2);
-            issue_batch(S, buf, a.vals, list0, bi2 * kBatch, min(kBatch, maxlast - bi2 * kBatch), a.records);
+            if (wid == 0)
+                issue_batch(S, buf, a.vals, list0, bi2 * kBatch, min(kBatch, maxlast - bi2 * kBatch), a.records);
             ++issued;
         }
     }
     for (int k = consumed; k < issued; ++k) {
-        mbar_wait(&S.bar[k & 1], uses[k & 1] & 1, a.status);
-        ++uses[k & 1];
+        mbar_wait(&S.bar[k & 1], parity(k & 1), a.status, kSiteDrain);
+        used(k & 1);
     }
 }
 

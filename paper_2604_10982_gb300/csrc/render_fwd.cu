@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
     bool ok = true;
     for (int b = 0; b < nb; ++b) {
         const int buf = b & 1;
-        ok = mbar_wait(&S.bar[buf], (b >> 1) & 1, a.status);
+        ok = mbar_wait(&S.bar[buf], (b >> 1) & 1, a.status, kSiteRenderFwd);
         consumed = b + 1;
         const int cnt = min(kBatch, n - b * kBatch);
         if (ok) {
@@ -119,13 +119,15 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
         }
         const int alive = __syncthreads_count(!done);
         if (alive == 0) break;
-        if (wid == 0 && b + 2 < nb) {
-            issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
+        if (b + 2 < nb) {
+            // every thread counts the batch (uniform phase bookkeeping); warp 0 issues it
+            if (wid == 0)
+                issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
             ++issued;
         }
     }
     // drain copies still in flight before the CTA's shared memory is released
-    for (int b = consumed; b < issued; ++b) mbar_wait(&S.bar[b & 1], (b >> 1) & 1, a.status);
+    for (int b = consumed; b < issued; ++b) mbar_wait(&S.bar[b & 1], (b >> 1) & 1, a.status, kSiteDrain);
     if (!ok) return;
     if (!inside) return;
 

@@ -114,6 +114,31 @@ class Renderer:
         K = int(opts.top_k)
         self.topk_ids = torch.empty(self.n_pix, K, dtype=torch.int32, device=self.dev) if (want_topk_ids and K) else None
 
+    def set_cameras(self, cams):
+        """Switch to other cameras with the same view count and image sizes."""
+        cams = list(cams)
+        assert len(cams) == self.V and all(
+            (a.width, a.height) == (b.width, b.height) for a, b in zip(cams, self.cams_py)), "camera layout differs"
+        self.cams_py = cams
+        self.cams = psi.cameras(cams)
+
+    def kernel_launches(self, with_decode: bool = False, with_bwd: bool = False) -> int:
+        """Number of library kernels one frame launches (memsets excluded)."""
+        R = self.V * self.n
+        n = 1 if R else 0                                  # project
+        n += (5 if R else 1)                               # scan (3) + finalize + emit
+        nbits = max(self.key_bits, 1)
+        passes = max(2, (nbits + 7) // 8)
+        passes += passes & 1
+        n += passes * 5 + 1                                # upsweep + scan(3) + scatter per pass, ranges
+        K = int(self.opts.top_k)
+        D = self.D
+        ch = 32 if D % 32 == 0 else 16
+        n += 1 if (K or not D) else max(1, D // ch)        # render (dense: one pass per channel chunk)
+        n += 1 if with_decode else 0
+        n += 2 if with_bwd else 0                          # adjoint + chain
+        return n
+
     def set_capacity(self, capacity: int):
         self.capacity = int(max(capacity, 1))
         self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.dev)

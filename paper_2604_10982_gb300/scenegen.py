@@ -54,11 +54,18 @@ def uniform(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
 
 
 def normal(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
-    """n standard normals (Box-Muller on two interleaved uniform draws)."""
-    u = uniform(seed, stream, 2 * n, 2 * offset)
-    u1 = 1.0 - u[0::2]  # (0, 1]
-    u2 = u[1::2]
-    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    """n standard normals: Box-Muller on uniform pairs (u1, u2) of the stream,
+    normal 2k = r cos(2 pi u2), 2k+1 = r sin(2 pi u2), r = sqrt(-2 ln(1-u1))."""
+    k0 = offset // 2
+    k1 = (offset + n + 1) // 2
+    u = uniform(seed, stream, 2 * (k1 - k0), 2 * k0)
+    r = np.sqrt(-2.0 * np.log(1.0 - u[0::2]))
+    th = 2.0 * math.pi * u[1::2]
+    z = np.empty(2 * (k1 - k0))
+    z[0::2] = r * np.cos(th)
+    z[1::2] = r * np.sin(th)
+    s = offset - 2 * k0
+    return z[s:s + n]
 
 
 # stream ids (one per drawn quantity)
@@ -150,13 +157,25 @@ def make_surfels(n: int, planes, seed: int, scale_median: float = 0.05) -> Surfe
 
 
 def make_features(n: int, d: int, seed: int, chunk: int = 1 << 22) -> np.ndarray:
-    """[N, D] float32 features ~ N(0,1), generated in chunks to bound memory."""
+    """[N, D] float32 features ~ N(0,1), generated in independent chunks of the
+    counter-based stream (threads in parallel; numpy releases the GIL)."""
+    import concurrent.futures as cf
+    import os
     out = np.empty((n, d), dtype=np.float32)
     flat = out.reshape(-1)
     total = n * d
-    for s in range(0, total, chunk):
+
+    def fill(s):
         m = min(chunk, total - s)
         flat[s:s + m] = normal(seed, _S_FEAT, m, offset=s)
+
+    starts = list(range(0, total, chunk))
+    if len(starts) <= 1:
+        for s in starts:
+            fill(s)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 4, 32)) as ex:
+            list(ex.map(fill, starts))
     return out
 
 

@@ -142,3 +142,11 @@ def test_autograd_function(ctx):
     assert torch.allclose(scene.mu.grad, g["mu"], rtol=1e-4, atol=1e-6)
     assert torch.allclose(scene.q.grad, g["feat"], rtol=1e-4, atol=1e-6)
     assert float(scene.opacity.grad.abs().sum()) > 0
+
+
+def test_grad_long_lists_early_exit(ctx):
+    """Tile lists spanning many 256-record batches with early termination:
+    exercises the adjoint's batch staging in both directions."""
+    w = sg.dense_box(n=20000, d=16, width=64, height=48, scale_median=0.25)
+    o = orc.Opts(mode=orc.AABB, top_k=8)
+    _grad_compare(ctx, w, w.cameras, o, 16)

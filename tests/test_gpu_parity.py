@@ -270,3 +270,23 @@ def test_capacity_overflow_reported(ctx, box):
     assert int(r.num_pairs.item()) == 100
     st, _ = ctx.status_fetch()
     assert st == 0
+
+
+def _long_list_scene():
+    """Large, dense surfels seen by a small view: tile lists of thousands of
+    entries (many 256-record batches) and early termination of every pixel."""
+    w = sg.dense_box(n=20000, d=16, width=64, height=48, scale_median=0.25)
+    return w
+
+
+def test_render_long_lists_early_exit(ctx):
+    w = _long_list_scene()
+    o = orc.Opts(mode=orc.AABB, top_k=8)
+    scene, r = _renderer(ctx, w, w.cameras, o, D=16, topk_ids=True)
+    r.frame(scene)
+    torch.cuda.synchronize()
+    st, site = ctx.status_fetch()
+    assert st == 0, (st, site)
+    rg = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    assert (rg[:, 1] - rg[:, 0]).max() > 3 * 256  # several batches per tile
+    _compare_render(r, scene, w, w.cameras, o, 16, w.features.astype(np.float64))
