@@ -199,6 +199,27 @@ int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d
                   int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *workspace,
                   size_t workspace_bytes, psi_stream stream);
 
+/* ---- a3 without caller scratch (no counterpart in the paper) ------------
+ * Same result as psi_sort_keys, for callers that cannot allocate device memory
+ * for a workspace: code recorded into a CUDA graph whose capture forbids
+ * allocation, real-time loops that must not stall on an allocator, or plug-ins
+ * running under a host framework that owns every device allocation. The
+ * scratch is a fixed array inside the library (PSI_SORT_NOALLOC_SCRATCH_BYTES
+ * per device, reserved when the library's module loads on that device and held
+ * until the process exits); this call allocates and frees nothing.
+ *  - capacity must be <= PSI_SORT_NOALLOC_MAX_PAIRS, else PSI_ERR_INVALID_ARG.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address; make that first call before any stream capture.
+ *  - All calls on a device share the one array and it keeps the previous
+ *    call's contents (the sort needs nothing zeroed in it): calls that overlap
+ *    on the GPU (different streams, or concurrent host threads) race and give
+ *    wrong results. Serialise them on one stream. */
+#define PSI_SORT_NOALLOC_MAX_PAIRS (1 << 20)
+#define PSI_SORT_NOALLOC_SCRATCH_BYTES (13 << 20)
+int psi_sort_keys_noalloc(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs,
+                          int64_t capacity, int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total,
+                          psi_stream stream);
+
 /* ---- a4: per-tile compositing with Top-K Hard Selection -----------------
  * Per pixel, front to back over its tile's list: alpha = min(0.99, o exp(-(u^2
  * +v^2)/2)) (Sec. 3.1), skipped if u^2+v^2 > r^2 or alpha < 1/255; RGB blended

@@ -280,6 +280,26 @@ int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_sort_keys", e);
 }
 
+int psi_sort_keys_noalloc(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs,
+                          int64_t capacity, int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total,
+                          psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (begin_bit < 0 || end_bit > 64 || begin_bit >= end_bit)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "need 0 <= begin_bit < end_bit <= 64");
+    if (capacity < 0 || capacity > PSI_SORT_NOALLOC_MAX_PAIRS)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "psi_sort_keys_noalloc: capacity %lld outside [0, %lld]",
+                    static_cast<long long>(capacity), static_cast<long long>(PSI_SORT_NOALLOC_MAX_PAIRS));
+    if (!d_num_pairs || (capacity > 0 && (!keys || !vals))) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (n_tiles_total < 0 || (n_tiles_total > 0 && !tile_ranges)) return fail(ctx, PSI_ERR_INVALID_ARG, "bad tile ranges");
+    DeviceGuard g(ctx->device);
+    const char *why = nullptr;
+    cudaError_t e = psi::launch_sort_noalloc(keys, vals, d_num_pairs, capacity, begin_bit, end_bit, tile_ranges,
+                                             n_tiles_total, ctx->status, reinterpret_cast<cudaStream_t>(stream), &why);
+    if (why) return fail(ctx, e == cudaErrorInvalidValue ? PSI_ERR_INVALID_ARG : PSI_ERR_CUDA, "psi_sort_keys_noalloc: %s", why);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_sort_keys_noalloc", e);
+}
+
 int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
                    const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
                    const psi_render_opts *o, const psi_fwd_out *out, psi_stream stream)

@@ -175,6 +175,11 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pai
                         int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *ws, DevStatus *status,
                         cudaStream_t st);
 
+constexpr int PSI_MAX_DEVICES_NOALLOC = 64;
+cudaError_t launch_sort_noalloc(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity,
+                                int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total,
+                                DevStatus *status, cudaStream_t st, const char **why);
+
 struct FeatView {
     const void *data;
     const float *scale;

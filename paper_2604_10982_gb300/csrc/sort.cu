@@ -9,6 +9,7 @@
 // the block as contiguous, coalesced stores. The number of passes is made even
 // (digit width <= 8 bits) so the result ends in the caller's buffers.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -230,6 +231,62 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pai
                                                                                n_tiles_total, status);
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------
+// Variant with library-owned scratch, for callers that cannot allocate device
+// memory. The scratch is a file-scope device array: the driver allocates it
+// when the module is loaded on a device and every device that loads the
+// library keeps it until the process exits. Host code must not use the
+// array's name as a pointer (on the host it names a host-side stand-in); the
+// device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(13) << 20; // 13 MiB: sort scratch for 2^20 pairs
+static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[PSI_MAX_DEVICES_NOALLOC] = {};
+
+} // namespace
+
+cudaError_t launch_sort_noalloc(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity,
+                                int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total,
+                                DevStatus *status, cudaStream_t st, const char **why)
+{
+    if (capacity > PSI_SORT_NOALLOC_MAX_PAIRS) {
+        *why = "capacity exceeds PSI_SORT_NOALLOC_MAX_PAIRS (use psi_sort_keys with a caller workspace)";
+        return cudaErrorInvalidValue;
+    }
+    if (sort_workspace_bytes(capacity) > kNoAllocScratchBytes) {
+        *why = "static scratch too small for this capacity";
+        return cudaErrorInvalidValue;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= PSI_MAX_DEVICES_NOALLOC) {
+        *why = "device index beyond the no-allocation table";
+        return cudaErrorInvalidValue;
+    }
+    void *ptr = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            // first call on this device (the current device): look up the
+            // array's device address; not capturable, so make this first call
+            // outside any stream capture
+            e = cudaGetSymbolAddress(&ptr, g_sort_scratch);
+            if (e != cudaSuccess) {
+                *why = "cudaGetSymbolAddress of the static sort scratch failed";
+                return e;
+            }
+            g_scratch_ptr[dev] = ptr;
+        }
+        ptr = g_scratch_ptr[dev];
+    }
+    return launch_sort(keys, vals, d_num_pairs, capacity, begin_bit, end_bit, tile_ranges, n_tiles_total, ptr, status,
+                       st);
 }
 
 } // namespace psi

@@ -86,6 +86,7 @@ def lib():
         L.psi_intersect_tiles.argtypes = [_P, ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts),
                                           _i64, _P, _P, _P, _P, _i64, _P, _P, sz, _P]
         L.psi_sort_keys.argtypes = [_P, _P, _P, _P, _i64, ctypes.c_int, ctypes.c_int, _P, _i64, _P, sz, _P]
+        L.psi_sort_keys_noalloc.argtypes = [_P, _P, _P, _P, _i64, ctypes.c_int, ctypes.c_int, _P, _i64, _P]
         L.psi_render_fwd.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _P, _P, ctypes.POINTER(PsiCamera),
                                      ctypes.c_int, _i64, ctypes.POINTER(PsiRenderOpts), ctypes.POINTER(PsiFwdOut), _P]
         L.psi_render_bwd.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures), _P, _P, _P,
@@ -232,6 +233,13 @@ def psi_sort_keys(ctx, keys, vals, d_num_pairs, capacity, begin_bit, end_bit, ti
     ctx.check(lib().psi_sort_keys(ctx.handle, _ptr(keys), _ptr(vals), _ptr(d_num_pairs), int(capacity), int(begin_bit),
                                   int(end_bit), _ptr(tile_ranges), int(n_tiles_total), _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), _stream(stream)), "psi_sort_keys")
+
+
+def psi_sort_keys_noalloc(ctx, keys, vals, d_num_pairs, capacity, begin_bit, end_bit, tile_ranges, n_tiles_total,
+                          stream=None):
+    ctx.check(lib().psi_sort_keys_noalloc(ctx.handle, _ptr(keys), _ptr(vals), _ptr(d_num_pairs), int(capacity),
+                                          int(begin_bit), int(end_bit), _ptr(tile_ranges), int(n_tiles_total),
+                                          _stream(stream)), "psi_sort_keys_noalloc")
 
 
 def psi_render_fwd(ctx, feats, records, vals, tile_ranges, cams_arr, n_views, n_surfels, opts, out: PsiFwdOut,
