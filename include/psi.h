@@ -60,7 +60,7 @@ enum psi_isect_mode { PSI_ISECT_SPHERE = 0, PSI_ISECT_AABB = 1, PSI_ISECT_EXACT 
 enum psi_dtype { PSI_F32 = 0, PSI_BF16 = 1, PSI_FP8_E4M3 = 2 };
 
 #define PSI_MAX_VIEWS 64
-#define PSI_RECORD_BYTES 64     /* render record per (view, surfel) */
+#define PSI_RECORD_BYTES 80     /* render record per (view, surfel) */
 #define PSI_BIN_RECORD_BYTES 32 /* binning record per (view, surfel) */
 #define PSI_MAX_TOPK 32
 
@@ -168,7 +168,7 @@ int psi_render_bwd_workspace_size(int64_t n_records, size_t *bytes);
  * culling (opacity < 1/255, or any part of the support disc nearer than
  * z_near), the support radius, the ellipse bounds of the projected covariance
  * (Sec. 5, Precise Tile Intersection) and the tile count of `o->mode`.
- *  records:       [n_views*N] x PSI_RECORD_BYTES, 64-byte aligned (written for visible records)
+ *  records:       [n_views*N] x PSI_RECORD_BYTES, 16-byte aligned (written for visible records)
  *  bin_records:   [n_views*N] x PSI_BIN_RECORD_BYTES, 16-byte aligned
  *  tiles_touched: [n_views*N] uint32, 0 for culled records
  * cams is a HOST array of n_views (<= PSI_MAX_VIEWS) cameras. */

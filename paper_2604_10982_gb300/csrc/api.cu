@@ -225,7 +225,7 @@ int psi_project_surfels(psi_ctx *ctx, const psi_surfels *s, const psi_camera *ca
     if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o)) || (rc = check_surfels(ctx, s))) return rc;
     if (s->n > 0 && (!records || !bin_records || !tiles_touched))
         return fail(ctx, PSI_ERR_INVALID_ARG, "output array is NULL");
-    if (!aligned(records, 64) || !aligned(bin_records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 64-byte aligned, bin records 16");
+    if (!aligned(records, 16) || !aligned(bin_records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records and bin records must be 16-byte aligned");
     if (s->n * n_views >= (int64_t(1) << 32)) return fail(ctx, PSI_ERR_INVALID_ARG, "n_views * N must be < 2^32");
     DeviceGuard g(ctx->device);
     psi::FrameParams fp;
@@ -314,7 +314,7 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
         return fail(ctx, PSI_ERR_INVALID_ARG, "F_dtype must be PSI_F32 or PSI_BF16");
     if (out->F && !aligned(out->F, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "out.F must be 16-byte aligned");
     if (!records || !vals || !tile_ranges) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
-    if (!aligned(records, 64)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 64-byte aligned");
+    if (!aligned(records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 16-byte aligned");
     if (n_surfels < 0) return fail(ctx, PSI_ERR_INVALID_ARG, "n_surfels < 0");
     DeviceGuard g(ctx->device);
     psi::FrameParams fp;
@@ -335,7 +335,7 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
     psi::FeatView fv;
     if ((rc = check_feat(ctx, f, fv))) return rc;
     if (!records || !vals || !tile_ranges || !g_rgb || !grads) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
-    if (!aligned(records, 64)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 64-byte aligned");
+    if (!aligned(records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 16-byte aligned");
     if (g_F && !fv.data) return fail(ctx, PSI_ERR_INVALID_ARG, "g_F given without features");
     const size_t need = psi::render_bwd_workspace_bytes(s->n * n_views);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256))

@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Fr
     counts[r] = count_tiles(b, fp.mode, fp.tile_w, fp.tile_h);
     store_bin(bins + 2 * r, b, w);
 
-    // render record: rows of adj(M') (q = adj(M') (x - p0x, y - p0y, 1)),
-    // projected centre, opacity, support radius^2 and colour
+    // render record (80 bytes): rows of adj(M') (q = adj(M') (x - p0x, y - p0y, 1)),
+    // projected centre, opacity, support radius^2, colour, covered-pixel rectangle
     const float a00 = mv_[1] * mc_[2] - mv_[2] * mc_[1];
     const float a01 = mv_[2] * mc_[0] - mv_[0] * mc_[2];
     const float a02 = mv_[0] * mc_[1] - mv_[1] * mc_[0];
@@ -177,11 +177,16 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Fr
     const float a20 = mu_[1] * mv_[2] - mu_[2] * mv_[1];
     const float a21 = mu_[2] * mv_[0] - mu_[0] * mv_[2];
     const float a22 = mu_[0] * mv_[1] - mu_[1] * mv_[0];
-    float4 *rec = records + 4 * r;
+    float4 *rec = records + 5 * r;
     rec[0] = make_float4(a00, a01, a02, a10);
     rec[1] = make_float4(a11, a12, a20, a21);
     rec[2] = make_float4(a22, p0x, p0y, o);
     rec[3] = make_float4(r2, s.rgb[3 * i], s.rgb[3 * i + 1], s.rgb[3 * i + 2]);
+    // rectangle of pixel indices whose centres the binning ellipse may cover
+    // (the one the tile lists come from): lets each warp skip whole records
+    rec[4] = make_float4(__uint_as_float(static_cast<uint32_t>(b.px0) | (static_cast<uint32_t>(b.px1) << 16)),
+                         __uint_as_float(static_cast<uint32_t>(b.py0) | (static_cast<uint32_t>(b.py1) << 16)), 0.0f,
+                         0.0f);
 }
 
 } // namespace

@@ -10,6 +10,7 @@ namespace psi {
 namespace raster {
 
 constexpr int kTile = 16;    // 16x16 pixels per CTA, one thread per pixel
+constexpr int kRecF4 = 5;    // render record: 80 bytes = 5 float4
 constexpr int kThreads = 256;
 constexpr int kBatch = 256;  // records staged per batch
 constexpr float kAlphaMin = 1.0f / 255.0f;
@@ -28,6 +29,15 @@ __device__ __forceinline__ float rcp_approx(float x)
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Thread -> pixel inside the 16x16 tile: warp w owns the 8x4 block at
+// ((w & 1) * 8, (w >> 1) * 4); lane l is pixel (l & 7, l >> 3) of the block.
+__device__ __forceinline__ void pixel_of_thread(int tid, int &lx, int &ly)
+{
+    const int w = tid >> 5, l = tid & 31;
+    lx = (w & 1) * 8 + (l & 7);
+    ly = (w >> 1) * 4 + (l >> 3);
 }
 
 // Staged render record after the per-tile transform: q = A (lx, ly, 1) with
@@ -146,7 +156,7 @@ struct TopK {
 
 // ------------------------------------------------------------ staging
 struct Stage {
-    float4 rec[2][kBatch][4];
+    float4 rec[2][kBatch][kRecF4];
     uint32_t val[2][kBatch];
     uint64_t bar[2];
 };
@@ -157,26 +167,39 @@ __device__ __forceinline__ void issue_batch(Stage &S, int buf, const uint32_t *_
                                             int b0, int cnt, const float4 *__restrict__ records)
 {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], static_cast<uint32_t>(cnt) * 64u);
+    if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], static_cast<uint32_t>(cnt) * (16u * kRecF4));
     __syncwarp();
     for (int j = lane; j < cnt; j += 32) {
         const uint32_t rid = vals[list0 + b0 + j];
         S.val[buf][j] = rid;
-        bulk_g2s(&S.rec[buf][j][0], records + 4 * static_cast<size_t>(rid), 64u, &S.bar[buf]);
+        bulk_g2s(&S.rec[buf][j][0], records + kRecF4 * static_cast<size_t>(rid), 16u * kRecF4, &S.bar[buf]);
     }
 }
 
 // Per-tile transform of the staged records: fold the tile origin into the
-// third column so that q = A (lx, ly, 1) with small, exact pixel offsets.
-__device__ __forceinline__ void transform_batch(Stage &S, int buf, int cnt, float tile_x0, float tile_y0)
+// third column so that q = A (lx, ly, 1) with small, exact pixel offsets, and
+// replace the covered-pixel rectangle by the mask of the 8x4 warp blocks it
+// meets (bit w = warp w), so a warp skips a record with one shared load.
+__device__ __forceinline__ void transform_batch(Stage &S, int buf, int cnt, int tile_x0, int tile_y0)
 {
     const int j = threadIdx.x;
     if (j < cnt) {
         float4 *r = S.rec[buf][j];
+        const float4 q = r[4];
+        const uint32_t bx = __float_as_uint(q.x), by = __float_as_uint(q.y);
+        const int x0 = static_cast<int>(bx & 0xFFFFu) - tile_x0, x1 = static_cast<int>(bx >> 16) - tile_x0;
+        const int y0 = static_cast<int>(by & 0xFFFFu) - tile_y0, y1 = static_cast<int>(by >> 16) - tile_y0;
+        uint32_t mask = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int cx = (w & 1) * 8, cy = (w >> 1) * 4;
+            if (x0 <= cx + 7 && x1 >= cx && y0 <= cy + 3 && y1 >= cy) mask |= 1u << w;
+        }
+        r[4] = make_float4(q.x, q.y, __uint_as_float(mask), 0.0f);
         float4 x = r[0], y = r[1], z = r[2];
         // record: a00 a01 a02 a10 | a11 a12 a20 a21 | a22 p0x p0y o | r2 r g b
-        const float ox = (tile_x0 + 0.5f) - z.y;
-        const float oy = (tile_y0 + 0.5f) - z.z;
+        const float ox = (static_cast<float>(tile_x0) + 0.5f) - z.y;
+        const float oy = (static_cast<float>(tile_y0) + 0.5f) - z.z;
         x.z = __fmaf_rn(x.x, ox, __fmaf_rn(x.y, oy, x.z));
         y.y = __fmaf_rn(x.w, ox, __fmaf_rn(y.x, oy, y.y));
         z.x = __fmaf_rn(y.z, ox, __fmaf_rn(y.w, oy, z.x));
@@ -184,6 +207,12 @@ __device__ __forceinline__ void transform_batch(Stage &S, int buf, int cnt, floa
         r[1] = y;
         r[2] = z;
     }
+}
+
+// does record j of buffer buf touch warp w's pixel block?
+__device__ __forceinline__ bool warp_hits(const Stage &S, int buf, int j, int w)
+{
+    return (__float_as_uint(S.rec[buf][j][4].z) >> w) & 1u;
 }
 
 // ------------------------------------------------------------ features

@@ -79,7 +79,8 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
 }
 
 template <int KMAX, int DT, int CH>
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
+__global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
+    render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
 {
     __shared__ __align__(128) Stage S;
     __shared__ int s_maxlast;
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);
     const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-    const int lxi = tid & 15, lyi = tid >> 4;
+    int lxi, lyi;
+    pixel_of_thread(tid, lxi, lyi);
     const int px = tx * kTile + lxi, py = ty * kTile + lyi;
     const bool inside = px < cam.W && py < cam.H;
     const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
     const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
     const int K = KMAX > 0 ? fp.top_k : 0;
     const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
-    const float tileX = static_cast<float>(tx * kTile), tileY = static_cast<float>(ty * kTile);
+    const int tileX = tx * kTile, tileY = ty * kTile;
 
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
         if (__syncthreads_or(!ok)) break;
         for (int j = 0; j < cnt; ++j) {
             if (__all_sync(0xffffffffu, done)) break;
+            if (!warp_hits(S, buf, j, wid)) continue; // record misses this warp's pixel block
             const Rec r = load_rec(S.rec[buf][j]);
             Eval e;
             const bool hit = !done && eval_alpha(r, lx, ly, e);
@@ -179,10 +182,10 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
             kd[s] = 0.0f;
         }
         if (a.g_F && a.feat && inside) {
-            for (int c0 = 0; c0 < a.D; c0 += CH) {
-                float g[CH];
+            for (int c0 = 0; c0 < a.D; c0 += 16) {
+                float g[16];
 #pragma unroll
-                for (int c = 0; c < CH; c += 4) {
+                for (int c = 0; c < 16; c += 4) {
                     const float4 q = __ldg(reinterpret_cast<const float4 *>(a.g_F + pix * a.D + c0 + c));
                     const float sc0 = a.fscale ? __ldg(a.fscale + c0 + c) : 1.0f;
                     const float sc1 = a.fscale ? __ldg(a.fscale + c0 + c + 1) : 1.0f;
@@ -197,11 +200,11 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
                 for (int s = 0; s < KMAX; ++s) {
                     if (kpos[s] < 0) continue;
                     const int64_t sid = static_cast<int64_t>(a.vals[list0 + kpos[s]]) - surf0;
-                    float f[CH];
-                    load_feat<DT, CH>(a.feat, sid, a.D, c0, f);
+                    float f[16];
+                    load_feat<DT, 16>(a.feat, sid, a.D, c0, f);
                     float acc = kd[s];
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) acc = __fmaf_rn(g[c], f[c], acc);
+                    for (int c = 0; c < 16; ++c) acc = __fmaf_rn(g[c], f[c], acc);
                     kd[s] = acc;
                 }
             }
@@ -240,6 +243,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const __grid_const
         }
         if (__syncthreads_or(!ok)) break;
         for (int j = cnt - 1; j >= 0; --j) {
+            if (!warp_hits(S, buf, j, wid)) continue; // record misses this warp's pixel block
             const int pos = bi * kBatch + j;
             const Rec r = load_rec(S.rec[buf][j]);
             Eval e;

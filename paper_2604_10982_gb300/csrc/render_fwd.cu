@@ -38,7 +38,8 @@ struct FwdArgs {
 };
 
 template <int KMAX, int DT, int CH>
-__global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
+__global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 4 : 1)
+    render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
 {
     __shared__ __align__(128) Stage S;
     const int tid = threadIdx.x, wid = tid >> 5;
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);
     const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-    const int lxi = tid & 15, lyi = tid >> 4;
+    int lxi, lyi;
+    pixel_of_thread(tid, lxi, lyi);
     const int px = tx * kTile + lxi, py = ty * kTile + lyi;
     const bool inside = px < cam.W && py < cam.H;
     const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
@@ -85,12 +87,13 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
         consumed = b + 1;
         const int cnt = min(kBatch, n - b * kBatch);
         if (ok) {
-            transform_batch(S, buf, cnt, static_cast<float>(tx * kTile), static_cast<float>(ty * kTile));
+            transform_batch(S, buf, cnt, tx * kTile, ty * kTile);
             fence_proxy_async_smem();
         }
         if (__syncthreads_or(!ok)) break;
         for (int j = 0; j < cnt; ++j) {
             if (__all_sync(0xffffffffu, done)) break;
+            if (!warp_hits(S, buf, j, wid)) continue; // record misses this warp's pixel block
             const Rec r = load_rec(S.rec[buf][j]);
             Eval e;
             const bool hit = !done && eval_alpha(r, lx, ly, e);
@@ -155,19 +158,22 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const __grid_const
                 if (s < K) dst[s] = sid[s];
         }
         if (a.F && a.feat) {
-            for (int c0 = 0; c0 < a.D; c0 += CH) {
-                float acc[CH];
+            // 16 channels per chunk keeps the gather's registers low (one
+            // 32-byte BF16 row slice = two 16-byte loads per selected surfel)
+            constexpr int CB = 16;
+            for (int c0 = 0; c0 < a.D; c0 += CB) {
+                float acc[CB];
 #pragma unroll
-                for (int c = 0; c < CH; ++c) acc[c] = 0.0f;
+                for (int c = 0; c < CB; ++c) acc[c] = 0.0f;
 #pragma unroll
                 for (int s = 0; s < KMAX; ++s) {
                     if (sid[s] < 0) continue;
-                    float f[CH];
-                    load_feat<DT, CH>(a.feat, sid[s], a.D, c0, f);
+                    float f[CB];
+                    load_feat<DT, CB>(a.feat, sid[s], a.D, c0, f);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) acc[c] = __fmaf_rn(top.w[s], f[c], acc[c]);
+                    for (int c = 0; c < CB; ++c) acc[c] = __fmaf_rn(top.w[s], f[c], acc[c]);
                 }
-                store_feat<CH>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
+                store_feat<CB>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
             }
         }
     }

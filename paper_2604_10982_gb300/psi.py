@@ -19,7 +19,7 @@ PSI_OK, PSI_ERR_INVALID_ARG, PSI_ERR_CUDA, PSI_ERR_CAPACITY, PSI_ERR_TIMEOUT, PS
 SPHERE, AABB, EXACT = 0, 1, 2
 F32, BF16, FP8_E4M3 = 0, 1, 2
 MAX_VIEWS = 64
-RECORD_BYTES = 64
+RECORD_BYTES = 80
 BIN_RECORD_BYTES = 32
 MAX_TOPK = 32
 
