@@ -116,6 +116,30 @@ def dist_env():
     return world, rank, local
 
 
+def frame_index(k: int, rank: int, n_frames: int) -> int:
+    """Frame of the trajectory that rank `rank` renders at step k. Weak
+    scaling: every rank renders its own K frames (no data-path collective:
+    frames are independent given the replicated scene), ranks start at
+    different points of the trajectory."""
+    return (k + rank * 7) % n_frames
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank timing over all ranks (the job's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps_per_rank: int, world: int, max_ms: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * steps_per_rank / (max_ms / 1000.0)
+
+
 def roofline_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current source of that kernel (else None)."""
@@ -318,11 +342,11 @@ def run_psi(args):
             if evs is not None:
                 evs[i + 1].record()
 
-    def frame_index(k):
-        return (k + rank * 7) % len(cams)
+    def fidx(k):
+        return frame_index(k, rank, len(cams))
 
     for k in range(args.warmup):
-        run_frame(frame_index(k))
+        run_frame(fidx(k))
     torch.cuda.synchronize()
     st, req = ctx.status_fetch()
     assert st == 0, f"device status {st} (required pairs {req})"
@@ -340,7 +364,7 @@ def run_psi(args):
     t_start.record()
     for k in range(args.steps):
         evs[k][0].record()
-        run_frame(frame_index(k), evs[k])
+        run_frame(fidx(k), evs[k])
     t_end.record()
     torch.cuda.synchronize()
     if world > 1:
@@ -350,17 +374,14 @@ def run_psi(args):
     stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(len(names))] for k in range(args.steps)])
     st, req = ctx.status_fetch()
     assert st == 0, f"device status {st}"
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     frame_ms = stage.sum(1)
     fwd_ms = stage[:, :5].sum(1)
-    value = world * args.steps / (total_ms / 1000.0)
+    value = job_throughput(args.steps, world, total_ms)
 
     # ---- per-frame statistics (outside the timed region)
     pairs, nlast_sum, nonempty = [], [], []
-    for f in sorted(set(frame_index(k) for k in range(args.steps))):
+    for f in sorted(set(fidx(k) for k in range(args.steps))):
         run_frame(f)
         torch.cuda.synchronize()
         pairs.append(int(r.num_pairs.item()))
@@ -416,17 +437,13 @@ def run_psi(args):
             gC.copy_(gC_h, non_blocking=True)
             gF.copy_(gF_h, non_blocking=True)
             gT.copy_(gT_h, non_blocking=True)
-            run_frame(frame_index(k))
+            run_frame(fidx(k))
             ids_h.copy_(ids, non_blocking=True)
             rgb_h.copy_(r.rgb, non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * args.e2e_steps / (e2e_ms / 1000.0), "unit": "frames/s",
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": job_throughput(args.e2e_steps, world, e2e_ms), "unit": "frames/s",
                "h2d_bytes_per_step": int(gC_h.numel() * 4 + gF_h.numel() * 4 + gT_h.numel() * 4),
                "d2h_bytes_per_step": int(ids_h.numel() * 4 + rgb_h.numel() * 4),
                "what": "per step: upstream gradients copied from pinned host memory, the frame (all stages), "
@@ -442,12 +459,12 @@ def run_psi(args):
         rp = pl.Renderer(ctx, scene.n, [cams[0]], po, 1024, D=D, F_dtype=psi.F32, device=dev)
         need = 0
         for f in range(min(args.plain_steps + 1, len(cams))):
-            rp.set_cameras([cams[frame_index(f)]])
+            rp.set_cameras([cams[fidx(f)]])
             need = max(need, rp.required_pairs(scene32))
         rp.set_capacity(int(need * 1.15) + 1024)
         pt = []
         for k in range(args.plain_steps + 1):
-            f = frame_index(k)
+            f = fidx(k)
             rp.set_cameras([cams[f]])
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record()
