@@ -192,7 +192,11 @@ int psi_intersect_tiles(psi_ctx *ctx, const psi_camera *cams, int n_views, const
 /* ---- a3: key sort and tile ranges ----------------------------------------
  * Stable LSD radix sort of the first *d_num_pairs (key, value) pairs on key
  * bits [begin_bit, end_bit) (in place: results end in keys/vals), then
- * tile_ranges[2*t] = start, [2*t+1] = end of global tile t (0,0 if empty).
+ * tile_ranges[2*t] = start, [2*t+1] = end of global tile t (0,0 if empty),
+ * and tile_ranges[2*n_tiles_total + i], i < n_tiles_total, the launch order of
+ * the compositing kernels (tiles by descending list length; the order among
+ * tiles of similar length is arbitrary and never changes a result). The
+ * tile_ranges buffer therefore holds 3*n_tiles_total uint32.
  * Pass begin_bit=0, end_bit=32+ceil(log2(n_tiles_total)) for the full order.
  *  workspace: psi_sort_workspace_size(capacity) bytes. */
 int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity,
@@ -238,7 +242,8 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
  * s_k + T_final g_T)/(1 - alpha_j), s_j = <gC, c_j> + [j in K]<gF, f_j>, and
  * chains through alpha = o G, (u,v) of the homogeneous ray-splat map, to mu,
  * t_u, t_v, s, o; also dL/dc, dL/df. g_F and g_T may be NULL.
- *  g_rgb: [3][P_total] planar; g_F: [P_total, D] float32; g_T: [P_total]
+ *  g_rgb: [3][P_total] planar; g_F: [P_total, D] float32, 16-byte aligned
+ *  (as grads->feat); g_T: [P_total]
  *  workspace: psi_render_bwd_workspace_size(n_views*N) bytes. */
 int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
                    const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,

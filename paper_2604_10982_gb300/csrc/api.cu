@@ -337,6 +337,8 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
     if (!records || !vals || !tile_ranges || !g_rgb || !grads) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
     if (!aligned(records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 16-byte aligned");
     if (g_F && !fv.data) return fail(ctx, PSI_ERR_INVALID_ARG, "g_F given without features");
+    if (!aligned(g_F, 16) || !aligned(grads->feat, 16))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "g_F and grads->feat must be 16-byte aligned");
     const size_t need = psi::render_bwd_workspace_bytes(s->n * n_views);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
         return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);

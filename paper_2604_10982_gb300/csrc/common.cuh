@@ -6,7 +6,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/psi.h"
+#include "psi.h" // include/ is on the include path
 
 namespace psi {
 

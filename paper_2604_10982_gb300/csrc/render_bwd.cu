@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     __shared__ __align__(128) Stage S;
     __shared__ int s_maxlast;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = a.ranges[2 * fp.n_tiles_total + blockIdx.x]; // longest lists first
     const int v = view_of_tile(fp, tile);
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);
@@ -213,6 +213,10 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     if (inside && last > 0) atomicMax(&s_maxlast, last);
     __syncthreads();
     const int maxlast = s_maxlast;
+    // entries at or beyond every lane's last composited surfel are skipped by the warp
+    int warp_last = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
 
     // ---------------- pass B: back to front
     const float gr = inside ? a.g_rgb[pix] : 0.0f;
@@ -242,13 +246,14 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
             fence_proxy_async_smem();
         }
         if (__syncthreads_or(!ok)) break;
-        for (int j = cnt - 1; j >= 0; --j) {
+        for (int j = min(cnt, warp_last - bi * kBatch) - 1; j >= 0; --j) {
             if (!warp_hits(S, buf, j, wid)) continue; // record misses this warp's pixel block
             const int pos = bi * kBatch + j;
             const Rec r = load_rec(S.rec[buf][j]);
             Eval e;
             const bool act = inside && pos < last && eval_alpha(r, lx, ly, e);
-            if (!__any_sync(0xffffffffu, act)) continue;
+            const uint32_t amask = __ballot_sync(0xffffffffu, act);
+            if (!amask) continue;
             const uint32_t rid = S.val[buf][j];
             const int64_t sid = static_cast<int64_t>(rid) - surf0;
             float vals[16];
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
             bool sel = false;
             if (act) {
                 const float one_m = __fsub_rn(1.0f, e.alpha);
-                const float inv = __frcp_rn(one_m);
+                const float inv = rcp_approx(one_m); // one_m >= 0.01
                 const float Tj = Tc * inv;
                 w = e.alpha * Tj;
                 float dot = 0.0f;
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                 vals[1] = w * gg;
                 vals[2] = w * gb;
                 if (!e.clamped) {
-                    const float rq = __frcp_rn(e.q2);
+                    const float rq = rcp_approx(e.q2);
                     const float u = e.q0 * rq, vv = e.q1 * rq;
                     const float d2 = u * u + vv * vv;
                     const float aa = dLda * e.alpha;
@@ -305,40 +310,77 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                     vals[10] = aa * d2 * vv;
                 }
             }
-            const float tot = warp_transpose_sum16(vals, lane);
-            const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-            if ((lane & 1) == 0 && idx < 11 && tot != 0.0f) {
-                if (idx < 3) {
-                    if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
-                } else {
-                    atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (idx - 3), tot);
+            if (__popc(amask) == 1) {
+                // a single contributing lane adds its values directly
+                if (act) {
+#pragma unroll
+                    for (int k2 = 0; k2 < 11; ++k2) {
+                        if (vals[k2] == 0.0f) continue;
+                        if (k2 < 3) {
+                            if (a.g_col) atomicAdd(a.g_col + 3 * sid + k2, vals[k2]);
+                        } else {
+                            atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (k2 - 3), vals[k2]);
+                        }
+                    }
+                }
+            } else {
+                const float tot = warp_transpose_sum16(vals, lane);
+                const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                if ((lane & 1) == 0 && idx < 11 && tot != 0.0f) {
+                    if (idx < 3) {
+                        if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
+                    } else {
+                        atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (idx - 3), tot);
+                    }
                 }
             }
             if (want_feat) {
                 uint32_t selmask = __ballot_sync(0xffffffffu, act && sel);
                 if (selmask) {
-                    // lanes own channels lane, lane+32, ... of the surfel's feature gradient
-                    float acc[8];
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) acc[m] = 0.0f;
+                    // lane l owns channels [4l, 4l+4) (+128 for D=256) of the surfel's
+                    // feature gradient; up to four selecting pixels per round so
+                    // their g_F loads are in flight together
+                    const int nv = a.D >> 2; // float4 chunks per row
+                    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
                     while (selmask) {
-                        const int L = __ffs(selmask) - 1;
-                        selmask &= selmask - 1;
-                        const float wL = __shfl_sync(0xffffffffu, w, L);
-                        const int64_t pL = __shfl_sync(0xffffffffu, pix, L);
-                        const float *grow = a.g_F + pL * a.D;
+                        int Ls[4];
+                        int nL = 0;
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) {
-                            const int c = lane + 32 * m;
-                            if (c < a.D) acc[m] = fmaf(wL, __ldg(grow + c), acc[m]);
+                        for (int q = 0; q < 4; ++q) {
+                            Ls[q] = selmask ? __ffs(selmask) - 1 : -1;
+                            if (selmask) {
+                                selmask &= selmask - 1;
+                                ++nL;
+                            }
+                        }
+                        float wq[4];
+                        float4 g0[4], g1[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int L = Ls[q] < 0 ? 0 : Ls[q];
+                            wq[q] = __shfl_sync(0xffffffffu, w, L);
+                            const int pL = __shfl_sync(0xffffffffu, static_cast<int>(pix), L);
+                            const float4 *grow = reinterpret_cast<const float4 *>(a.g_F + static_cast<int64_t>(pL) * a.D);
+                            const bool on = q < nL;
+                            g0[q] = (on && lane < nv) ? __ldg(grow + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            g1[q] = (on && lane + 32 < nv) ? __ldg(grow + lane + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (!on) wq[q] = 0.0f;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            acc0.x = fmaf(wq[q], g0[q].x, acc0.x);
+                            acc0.y = fmaf(wq[q], g0[q].y, acc0.y);
+                            acc0.z = fmaf(wq[q], g0[q].z, acc0.z);
+                            acc0.w = fmaf(wq[q], g0[q].w, acc0.w);
+                            acc1.x = fmaf(wq[q], g1[q].x, acc1.x);
+                            acc1.y = fmaf(wq[q], g1[q].y, acc1.y);
+                            acc1.z = fmaf(wq[q], g1[q].z, acc1.z);
+                            acc1.w = fmaf(wq[q], g1[q].w, acc1.w);
                         }
                     }
-                    float *dst = a.g_feat + sid * a.D;
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const int c = lane + 32 * m;
-                        if (c < a.D) atomicAdd(dst + c, acc[m]);
-                    }
+                    float4 *dst = reinterpret_cast<float4 *>(a.g_feat + sid * a.D);
+                    if (lane < nv) atomicAdd(dst + lane, acc0);
+                    if (lane + 32 < nv) atomicAdd(dst + lane + 32, acc1);
                 }
             }
         }

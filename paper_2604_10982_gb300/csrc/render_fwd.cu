@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 4 : 1)
 {
     __shared__ __align__(128) Stage S;
     const int tid = threadIdx.x, wid = tid >> 5;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = a.ranges[2 * fp.n_tiles_total + blockIdx.x]; // longest lists first
     const int v = view_of_tile(fp, tile);
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);

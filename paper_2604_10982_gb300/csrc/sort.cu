@@ -169,6 +169,42 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t *__restrict_
     if (i == n - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = static_cast<uint32_t>(i + 1);
 }
 
+// Launch order of the compositing CTAs: tiles by descending list length
+// (64 buckets, two per octave; empty tiles last), so the longest tiles start
+// first instead of forming the kernel's tail. Order inside a bucket is
+// arbitrary (a schedule only: every tile's result is independent of it).
+__device__ __forceinline__ int cost_bucket(uint32_t len)
+{
+    if (len == 0) return 63;
+    const int l2 = 31 - __clz(len);
+    const int half = (l2 > 0) ? static_cast<int>((len >> (l2 - 1)) & 1u) : 0;
+    return 62 - min(2 * l2 + half, 62);
+}
+
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t *__restrict__ ranges, int64_t n_tiles,
+                                                          uint32_t *__restrict__ order)
+{
+    __shared__ unsigned int hist[64];
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        atomicAdd(&hist[cost_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int b = 0; b < 64; ++b) {
+            const unsigned int c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const unsigned int pos = atomicAdd(&hist[cost_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+        order[pos] = static_cast<uint32_t>(t);
+    }
+}
+
 } // namespace
 
 size_t sort_workspace_bytes(int64_t capacity)
@@ -229,6 +265,7 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pai
         if (e != cudaSuccess) return e;
         ranges_kernel<<<static_cast<unsigned>((cap + 255) / 256), 256, 0, st>>>(keys, d_num_pairs, tile_ranges,
                                                                                n_tiles_total, status);
+        tile_order_kernel<<<1, 1024, 0, st>>>(tile_ranges, n_tiles_total, tile_ranges + 2 * n_tiles_total);
     }
     return cudaGetLastError();
 }

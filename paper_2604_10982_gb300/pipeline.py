@@ -103,7 +103,8 @@ class Renderer:
         self.ws_isect = u8(psi.intersect_workspace_size(R))
         self.set_capacity(capacity)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=self.dev)
-        self.ranges = torch.empty(max(self.n_tiles, 1) * 2, dtype=torch.int32, device=self.dev)
+        # [start, end) per tile, then the compositing launch order
+        self.ranges = torch.empty(max(self.n_tiles, 1) * 3, dtype=torch.int32, device=self.dev)
         self.rgb = torch.empty(3, self.n_pix, dtype=torch.float32, device=self.dev)
         self.T = torch.empty(self.n_pix, dtype=torch.float32, device=self.dev)
         self.n_last = torch.empty(self.n_pix, dtype=torch.int32, device=self.dev)

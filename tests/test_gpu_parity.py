@@ -78,8 +78,14 @@ def test_keys_sort_ranges_bitexact(ctx, box, mode):
     gk = r.keys[:P].cpu().numpy().view(np.uint64)
     gv = r.vals[:P].cpu().numpy().view(np.uint32)
     assert np.array_equal(gk, sk) and np.array_equal(gv, sv), "sorted order differs"
-    rg = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    rall = r.ranges.cpu().numpy().view(np.uint32)
+    rg = rall[: 2 * r.n_tiles].reshape(-1, 2).astype(np.int64)
     ro = orc.tile_ranges(sk, r.n_tiles).astype(np.int64)
+    # launch order: a permutation of the tiles, longest lists first (by octave)
+    order = rall[2 * r.n_tiles: 3 * r.n_tiles].astype(np.int64)
+    assert np.array_equal(np.sort(order), np.arange(r.n_tiles))
+    ln = (ro[:, 1] - ro[:, 0])[order]
+    assert (np.diff(np.floor(np.log2(np.maximum(ln, 1)))) <= 0).all()
     assert np.array_equal(rg[:, 1] - rg[:, 0], ro[:, 1] - ro[:, 0])
     nonempty = ro[:, 1] > ro[:, 0]
     assert np.array_equal(rg[nonempty], ro[nonempty])
@@ -104,7 +110,7 @@ def test_sort_random_keys_vs_stable_argsort(ctx):
         npairs = torch.tensor([n], dtype=torch.int64, device="cuda")
         ws = torch.empty(psi.sort_workspace_size(cap), dtype=torch.uint8, device="cuda")
         nt = 1 << (bits - 32)
-        ranges = torch.empty(nt * 2, dtype=torch.int32, device="cuda")
+        ranges = torch.empty(nt * 3, dtype=torch.int32, device="cuda")
         psi.psi_sort_keys(ctx, kk, vv, npairs, cap, 0, bits, ranges, nt, ws)
         torch.cuda.synchronize()
         perm = np.argsort(keys, kind="stable")
@@ -287,6 +293,6 @@ def test_render_long_lists_early_exit(ctx):
     torch.cuda.synchronize()
     st, site = ctx.status_fetch()
     assert st == 0, (st, site)
-    rg = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    rg = r.ranges.cpu().numpy().view(np.uint32)[: 2 * r.n_tiles].reshape(-1, 2).astype(np.int64)
     assert (rg[:, 1] - rg[:, 0]).max() > 3 * 256  # several batches per tile
     _compare_render(r, scene, w, w.cameras, o, 16, w.features.astype(np.float64))

@@ -39,15 +39,18 @@ def _sort_both(ctx, keys, vals, cap, bits, n_tiles):
         kk[:n] = torch.from_numpy(keys.view(np.int64)).cuda()
         vv[:n] = torch.from_numpy(vals.view(np.int32)).cuda()
         npairs = torch.tensor([n], dtype=torch.int64, device="cuda")
-        ranges = torch.full((n_tiles * 2,), -1, dtype=torch.int32, device="cuda")
+        ranges = torch.full((n_tiles * 3,), -1, dtype=torch.int32, device="cuda")
         if noalloc:
             psi.psi_sort_keys_noalloc(ctx, kk, vv, npairs, cap, 0, bits, ranges, n_tiles)
         else:
             ws = torch.empty(psi.sort_workspace_size(cap), dtype=torch.uint8, device="cuda")
             psi.psi_sort_keys(ctx, kk, vv, npairs, cap, 0, bits, ranges, n_tiles, ws)
         torch.cuda.synchronize()
-        out.append((kk[:n].cpu().numpy().view(np.uint64), vv[:n].cpu().numpy().view(np.uint32),
-                    ranges.cpu().numpy()))
+        # tile ranges; the launch-order tail is a schedule (arbitrary among
+        # tiles of similar length), so only its being a permutation is checked
+        rr = ranges.cpu().numpy()
+        assert np.array_equal(np.sort(rr[2 * n_tiles:]), np.arange(n_tiles))
+        out.append((kk[:n].cpu().numpy().view(np.uint64), vv[:n].cpu().numpy().view(np.uint32), rr[: 2 * n_tiles]))
     return out
 
 
@@ -77,7 +80,7 @@ def test_noalloc_sort_rejects_capacity_beyond_limit(ctx):
     kk = torch.zeros(cap, dtype=torch.int64, device="cuda")
     vv = torch.zeros(cap, dtype=torch.int32, device="cuda")
     npairs = torch.tensor([10], dtype=torch.int64, device="cuda")
-    ranges = torch.zeros(2, dtype=torch.int32, device="cuda")
+    ranges = torch.zeros(3, dtype=torch.int32, device="cuda")
     with pytest.raises(psi.PsiError) as e:
         psi.psi_sort_keys_noalloc(ctx, kk, vv, npairs, cap, 0, 33, ranges, 1)
     assert e.value.code == psi.PSI_ERR_INVALID_ARG
