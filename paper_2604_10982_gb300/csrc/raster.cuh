@@ -85,49 +85,43 @@ __device__ __forceinline__ bool eval_alpha(const Rec &r, float lx, float ly, Eva
 
 // ------------------------------------------------------------ Top-K
 // The K largest weights of one pixel with their list positions (Sec. 5, Top-K
-// Hard Selection). A new weight enters only if it is strictly larger than the
-// current worst, and among equal weights the later list position is the
-// worst: ties favour the earlier surfel. The insertion runs under a warp vote.
+// Hard Selection), kept sorted by weight (descending; among equal weights the
+// earlier list position first), so the worst kept weight is always the last
+// slot. A new weight enters only if it is strictly larger than that worst one
+// -- it comes later in the list than everything kept, so ties favour the
+// earlier surfel -- by one compare-and-shift pass. With a runtime K below
+// KMAX the first KMAX-K slots hold +inf and never move. The insertion runs
+// under a warp vote, so lanes pay one compare per surfel unless some lane of
+// the warp improves its set.
 template <int KMAX>
 struct TopK {
     float w[KMAX];
     int p[KMAX];
-    float worst_w;
-    int worst_p, worst_i;
 
     __device__ __forceinline__ void init(int K)
     {
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) {
-            w[s] = (s < K) ? -1.0f : __int_as_float(0x7f800000);
+            w[s] = (s < KMAX - K) ? __int_as_float(0x7f800000) : -1.0f;
             p[s] = 0x7fffffff;
         }
-        worst_w = -1.0f;
-        worst_p = 0x7fffffff;
-        worst_i = 0;
     }
 
     __device__ __forceinline__ void offer(bool hit, float wt, int pos)
     {
-        const bool better = hit && wt > worst_w;
+        const bool better = hit && wt > w[KMAX - 1];
         if (__any_sync(0xffffffffu, better)) {
             if (better) {
+                bool gt[KMAX];
 #pragma unroll
-                for (int s = 0; s < KMAX; ++s)
-                    if (s == worst_i) {
-                        w[s] = wt;
-                        p[s] = pos;
-                    }
-                worst_w = w[0];
-                worst_p = p[0];
-                worst_i = 0;
+                for (int s = 0; s < KMAX; ++s) gt[s] = wt > w[s];
 #pragma unroll
-                for (int s = 1; s < KMAX; ++s)
-                    if (w[s] < worst_w || (w[s] == worst_w && p[s] > worst_p)) {
-                        worst_w = w[s];
-                        worst_p = p[s];
-                        worst_i = s;
-                    }
+                for (int s = KMAX - 1; s > 0; --s) {
+                    w[s] = gt[s - 1] ? w[s - 1] : (gt[s] ? wt : w[s]);
+                    p[s] = gt[s - 1] ? p[s - 1] : (gt[s] ? pos : p[s]);
+                }
+                w[0] = gt[0] ? wt : w[0];
+                p[0] = gt[0] ? pos : p[0];
             }
         }
     }
@@ -213,6 +207,198 @@ __device__ __forceinline__ void transform_batch(Stage &S, int buf, int cnt, int 
 __device__ __forceinline__ bool warp_hits(const Stage &S, int buf, int j, int w)
 {
     return (__float_as_uint(S.rec[buf][j][4].z) >> w) & 1u;
+}
+
+// ------------------------------------------------------------ decoupled pipeline
+// A tile's list is streamed through kPS shared-memory stages of kPB records. A
+// dedicated producer warp (warp 8) fills a stage with one TMA bulk copy per
+// record (completion on full[s]), transforms the records for the tile once
+// (ready[s]), and refills the stage after all eight pixel warps released it
+// (empty[s], 8 arrivals). Pixel warps only wait for ready stages, so a warp
+// with little work in a batch runs ahead instead of waiting at a CTA barrier.
+// Every wait is bounded; `alive` counts pixel warps with pixels still
+// compositing (the producer stops when it reaches zero).
+constexpr int kPS = 4;            // stages
+constexpr int kPB = 128;          // records per stage (four 32-bit hit words per warp)
+constexpr int kPixelWarps = 8;
+constexpr int kPipeThreads = 32 * (kPixelWarps + 1);
+
+struct Pipe {
+    float4 rec[kPS][kPB][kRecF4];
+    uint32_t val[kPS][kPB];
+    uint64_t full[kPS], ready[kPS], empty[kPS];
+    int alive;
+    int abort;
+};
+
+__device__ __forceinline__ int vload(const int &x) { return *reinterpret_cast<const volatile int *>(&x); }
+
+// thread 0; the caller synchronises the CTA afterwards
+__device__ __forceinline__ void pipe_init(Pipe &P, int alive)
+{
+    for (int s = 0; s < kPS; ++s) {
+        mbar_init(&P.full[s], 1);
+        mbar_init(&P.ready[s], 1);
+        mbar_init(&P.empty[s], kPixelWarps);
+    }
+    P.alive = alive;
+    P.abort = 0;
+    fence_mbar_init();
+}
+
+// Batch b of a walk over n list entries (forward: from the front; reverse:
+// from the back); returns the first list position and sets the count.
+__device__ __forceinline__ int batch_range(int b, int n, bool reverse, int &cnt)
+{
+    const int nb = (n + kPB - 1) / kPB;
+    const int bi = reverse ? nb - 1 - b : b;
+    cnt = min(kPB, n - bi * kPB);
+    return bi * kPB;
+}
+
+// transform one staged record for the tile (see transform_batch)
+__device__ __forceinline__ void transform_record(float4 *r, int tile_x0, int tile_y0)
+{
+    const float4 q = r[4];
+    const uint32_t bx = __float_as_uint(q.x), by = __float_as_uint(q.y);
+    const int x0 = static_cast<int>(bx & 0xFFFFu) - tile_x0, x1 = static_cast<int>(bx >> 16) - tile_x0;
+    const int y0 = static_cast<int>(by & 0xFFFFu) - tile_y0, y1 = static_cast<int>(by >> 16) - tile_y0;
+    uint32_t mask = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const int cx = (w & 1) * 8, cy = (w >> 1) * 4;
+        if (x0 <= cx + 7 && x1 >= cx && y0 <= cy + 3 && y1 >= cy) mask |= 1u << w;
+    }
+    r[4] = make_float4(q.x, q.y, __uint_as_float(mask), 0.0f);
+    float4 x = r[0], y = r[1], z = r[2];
+    const float ox = (static_cast<float>(tile_x0) + 0.5f) - z.y;
+    const float oy = (static_cast<float>(tile_y0) + 0.5f) - z.z;
+    x.z = __fmaf_rn(x.x, ox, __fmaf_rn(x.y, oy, x.z));
+    y.y = __fmaf_rn(x.w, ox, __fmaf_rn(y.x, oy, y.y));
+    z.x = __fmaf_rn(y.z, ox, __fmaf_rn(y.w, oy, z.x));
+    r[0] = x;
+    r[1] = y;
+    r[2] = z;
+}
+
+// Producer warp: walks batches 0..nb-1 of the list (entries [list0, list0+n)),
+// forward or reverse, until all batches are transformed or no pixel warp is
+// alive. Returns false on a timeout (status raised, abort set).
+__device__ __forceinline__ bool pipe_produce(Pipe &P, const uint32_t *__restrict__ vals, int64_t list0, int n,
+                                             bool reverse, const float4 *__restrict__ records, int tile_x0,
+                                             int tile_y0, DevStatus *st, int site)
+{
+    const int lane = threadIdx.x & 31;
+    const int nb = (n + kPB - 1) / kPB;
+    int issued = 0, done = 0; // batches issued / transformed
+    unsigned long long t_idle = 0;
+    bool ok = true;
+    while (done < nb) {
+        if (vload(P.alive) == 0 || vload(P.abort)) break;
+        bool progressed = false;
+        // transform the oldest issued batch once its copies have landed
+        if (done < issued) {
+            const int s = done % kPS;
+            const bool landed = __shfl_sync(0xffffffffu, lane == 0 ? mbar_try_wait(&P.full[s], (done / kPS) & 1) : false, 0);
+            if (landed) {
+                int cnt;
+                batch_range(done, n, reverse, cnt);
+                for (int j = lane; j < cnt; j += 32) transform_record(P.rec[s][j], tile_x0, tile_y0);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&P.ready[s]);
+                ++done;
+                progressed = true;
+            }
+        }
+        // issue the next batch into a stage every pixel warp has released
+        if (issued < nb && issued < done + kPS) {
+            const int s = issued % kPS;
+            const bool free_ = issued < kPS ||
+                               __shfl_sync(0xffffffffu, lane == 0 ? mbar_try_wait(&P.empty[s], ((issued / kPS) - 1) & 1) : false, 0);
+            if (free_) {
+                int cnt;
+                const int lo = batch_range(issued, n, reverse, cnt);
+                for (int j = lane; j < cnt; j += 32) P.val[s][j] = vals[list0 + lo + j];
+                __syncwarp();
+                if (lane == 0) mbar_arrive_expect_tx(&P.full[s], static_cast<uint32_t>(cnt) * (16u * kRecF4));
+                __syncwarp();
+                for (int j = lane; j < cnt; j += 32)
+                    bulk_g2s(&P.rec[s][j][0], records + kRecF4 * static_cast<size_t>(P.val[s][j]), 16u * kRecF4, &P.full[s]);
+                ++issued;
+                progressed = true;
+            }
+        }
+        if (progressed) {
+            t_idle = 0;
+        } else {
+            const unsigned long long now = global_ns();
+            if (t_idle == 0) {
+                t_idle = now;
+            } else if (now - t_idle > kWaitLimitNs) {
+                if (lane == 0 && st) {
+                    atomicCAS(&st->wait_site, 0, site);
+                    raise_status(st, PSI_ERR_TIMEOUT);
+                    atomicExch(&P.abort, 1);
+                }
+                ok = false;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    // copies still in flight must land before the stages are reused or freed
+    for (int b = done; b < issued; ++b) {
+        if (lane == 0) mbar_wait(&P.full[b % kPS], (b / kPS) & 1, st, kSiteDrain);
+        __syncwarp();
+    }
+    return ok;
+}
+
+// Pixel warp: wait until batch b is ready. Returns false if the walk is over
+// for everyone (no pixel warp alive, or an abort).
+__device__ __forceinline__ bool pipe_wait_ready(Pipe &P, int b, DevStatus *st, int site)
+{
+    const int s = b % kPS;
+    const uint32_t par = (b / kPS) & 1;
+    if (mbar_try_wait(&P.ready[s], par)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(&P.ready[s], par)) return true;
+        if (vload(P.abort) || vload(P.alive) == 0) return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            if (st) {
+                atomicCAS(&st->wait_site, 0, site);
+                raise_status(st, PSI_ERR_TIMEOUT);
+            }
+            atomicExch(&P.abort, 1);
+            return false;
+        }
+    }
+}
+
+// Pixel warp: done with batch b (one arrival per warp).
+__device__ __forceinline__ void pipe_release(Pipe &P, int b)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&P.empty[b % kPS]);
+}
+
+__device__ __forceinline__ bool pipe_hits(const Pipe &P, int s, int j, int w)
+{
+    return (__float_as_uint(P.rec[s][j][4].z) >> w) & 1u;
+}
+
+// Bitmap of the records of stage s (cnt of them) that touch warp w's block:
+// bit (j & 31) of word j >> 5. Identical in every lane.
+__device__ __forceinline__ void pipe_hit_words(const Pipe &P, int s, int cnt, int w, uint32_t hw[kPB / 32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < kPB / 32; ++q) {
+        const int j = q * 32 + lane;
+        hw[q] = __ballot_sync(0xffffffffu, j < cnt && pipe_hits(P, s, j, w));
+    }
 }
 
 // ------------------------------------------------------------ features

@@ -38,37 +38,34 @@ struct FwdArgs {
 };
 
 template <int KMAX, int DT, int CH>
-__global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 4 : 1)
+__global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
 {
-    __shared__ __align__(128) Stage S;
-    const int tid = threadIdx.x, wid = tid >> 5;
+    __shared__ __align__(128) Pipe P;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const uint32_t tile = a.ranges[2 * fp.n_tiles_total + blockIdx.x]; // longest lists first
     const int v = view_of_tile(fp, tile);
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);
     const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
+    const int64_t list0 = a.ranges[2 * tile];
+    const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    const int nb = (n + kPB - 1) / kPB;
+
+    if (tid == 0) pipe_init(P, kPixelWarps);
+    __syncthreads();
+    if (wid == kPixelWarps) {
+        pipe_produce(P, a.vals, list0, n, false, a.records, tx * kTile, ty * kTile, a.status, kSiteRenderFwd);
+        return;
+    }
+
     int lxi, lyi;
     pixel_of_thread(tid, lxi, lyi);
     const int px = tx * kTile + lxi, py = ty * kTile + lyi;
     const bool inside = px < cam.W && py < cam.H;
     const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
-    const int64_t list0 = a.ranges[2 * tile];
-    const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
-    const int nb = (n + kBatch - 1) / kBatch;
     const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
     const int K = KMAX > 0 ? fp.top_k : 0;
-
-    if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (wid == 0) {
-        for (int b = 0; b < 2 && b < nb; ++b)
-            issue_batch(S, b, a.vals, list0, b * kBatch, min(kBatch, n - b * kBatch), a.records);
-    }
 
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     int last = 0;
@@ -79,59 +76,61 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 4 : 1)
 #pragma unroll
     for (int c = 0; c < (KMAX == 0 ? CH : 1); ++c) facc[c] = 0.0f;
 
-    int issued = min(nb, 2), consumed = 0;
-    bool ok = true;
+    bool wdone = __all_sync(0xffffffffu, done);
+    if (wdone && lane == 0) atomicSub(&P.alive, 1);
     for (int b = 0; b < nb; ++b) {
-        const int buf = b & 1;
-        ok = mbar_wait(&S.bar[buf], (b >> 1) & 1, a.status, kSiteRenderFwd);
-        consumed = b + 1;
-        const int cnt = min(kBatch, n - b * kBatch);
-        if (ok) {
-            transform_batch(S, buf, cnt, tx * kTile, ty * kTile);
-            fence_proxy_async_smem();
-        }
-        if (__syncthreads_or(!ok)) break;
-        for (int j = 0; j < cnt; ++j) {
-            if (__all_sync(0xffffffffu, done)) break;
-            if (!warp_hits(S, buf, j, wid)) continue; // record misses this warp's pixel block
-            const Rec r = load_rec(S.rec[buf][j]);
-            Eval e;
-            const bool hit = !done && eval_alpha(r, lx, ly, e);
-            const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
-            const int pos = b * kBatch + j;
-            if (hit) {
-                const float4 col = S.rec[buf][j][3];
-                cr = __fmaf_rn(w, col.y, cr);
-                cg = __fmaf_rn(w, col.z, cg);
-                cb = __fmaf_rn(w, col.w, cb);
-                if constexpr (KMAX == 0) {
-                    if (a.feat) {
-                        float f[CH];
-                        load_feat<DT, CH>(a.feat, static_cast<int64_t>(S.val[buf][j]) - surf0, a.D, a.c0, f);
+        if (!pipe_wait_ready(P, b, a.status, kSiteRenderFwd)) break;
+        const int st = b % kPS;
+        int cnt;
+        const int lo = batch_range(b, n, false, cnt);
+        if (!wdone) {
+            // only the records that touch this warp's pixel block, in list order
+            uint32_t hw[kPB / 32];
+            pipe_hit_words(P, st, cnt, wid, hw);
+            bool all_done = false;
+#pragma unroll 1
+            for (int q = 0; q < kPB / 32 && !all_done; ++q)
+#pragma unroll 1
+            for (uint32_t bits = q == 0 ? hw[0] : q == 1 ? hw[1] : q == 2 ? hw[2] : hw[3]; bits; bits &= bits - 1) {
+                if (__all_sync(0xffffffffu, done)) {
+                    all_done = true;
+                    break;
+                }
+                const int j = q * 32 + __ffs(bits) - 1;
+                const Rec r = load_rec(P.rec[st][j]);
+                Eval e;
+                const bool hit = !done && eval_alpha(r, lx, ly, e);
+                const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
+                const int pos = lo + j;
+                if (hit) {
+                    const float4 col = P.rec[st][j][3];
+                    cr = __fmaf_rn(w, col.y, cr);
+                    cg = __fmaf_rn(w, col.z, cg);
+                    cb = __fmaf_rn(w, col.w, cb);
+                    if constexpr (KMAX == 0) {
+                        if (a.feat) {
+                            float f[CH];
+                            load_feat<DT, CH>(a.feat, static_cast<int64_t>(P.val[st][j]) - surf0, a.D, a.c0, f);
 #pragma unroll
-                        for (int c = 0; c < CH; ++c) facc[c] = __fmaf_rn(w, f[c], facc[c]);
+                            for (int c = 0; c < CH; ++c) facc[c] = __fmaf_rn(w, f[c], facc[c]);
+                        }
                     }
                 }
-            }
-            if constexpr (KMAX > 0) top.offer(hit, w, pos);
-            if (hit) {
-                T = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
-                last = pos + 1;
-                if (T < fp.t_eps) done = true;
+                if constexpr (KMAX > 0) top.offer(hit, w, pos);
+                if (hit) {
+                    T = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
+                    last = pos + 1;
+                    if (T < fp.t_eps) done = true;
+                }
             }
         }
-        const int alive = __syncthreads_count(!done);
-        if (alive == 0) break;
-        if (b + 2 < nb) {
-            // every thread counts the batch (uniform phase bookkeeping); warp 0 issues it
-            if (wid == 0)
-                issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
-            ++issued;
+        pipe_release(P, b);
+        if (!wdone && __all_sync(0xffffffffu, done)) {
+            wdone = true;
+            if (lane == 0) atomicSub(&P.alive, 1);
         }
     }
-    // drain copies still in flight before the CTA's shared memory is released
-    for (int b = consumed; b < issued; ++b) mbar_wait(&S.bar[b & 1], (b >> 1) & 1, a.status, kSiteDrain);
-    if (!ok) return;
+    if (vload(P.abort)) return;
     if (!inside) return;
 
     const int64_t pix = cam.pix_base + static_cast<int64_t>(py) * cam.W + px;
@@ -184,9 +183,9 @@ cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const FwdArgs &a
 {
     const unsigned grid = fp.n_tiles_total;
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
-    default: render_fwd_kernel<KMAX, PSI_F32, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    default: render_fwd_kernel<KMAX, PSI_F32, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
 }
