@@ -11,8 +11,6 @@ namespace raster {
 
 constexpr int kTile = 16;    // 16x16 pixels per CTA, one thread per pixel
 constexpr int kRecF4 = 5;    // render record: 80 bytes = 5 float4
-constexpr int kThreads = 256;
-constexpr int kBatch = 256;  // records staged per batch
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kNegHalfLog2e = -0.72134752044448170f; // -log2(e)/2: exp(-d2/2) = 2^(d2 * k)
@@ -148,67 +146,6 @@ struct TopK {
     __device__ __forceinline__ bool valid(int s, int K) const { return s < K && p[s] != 0x7fffffff; }
 };
 
-// ------------------------------------------------------------ staging
-struct Stage {
-    float4 rec[2][kBatch][kRecF4];
-    uint32_t val[2][kBatch];
-    uint64_t bar[2];
-};
-
-// Issued by warp 0: bulk-copy the records of list entries [b0, b0+cnt) into
-// buffer `buf` (one 64-byte TMA bulk copy per record), completion on bar[buf].
-__device__ __forceinline__ void issue_batch(Stage &S, int buf, const uint32_t *__restrict__ vals, int64_t list0,
-                                            int b0, int cnt, const float4 *__restrict__ records)
-{
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], static_cast<uint32_t>(cnt) * (16u * kRecF4));
-    __syncwarp();
-    for (int j = lane; j < cnt; j += 32) {
-        const uint32_t rid = vals[list0 + b0 + j];
-        S.val[buf][j] = rid;
-        bulk_g2s(&S.rec[buf][j][0], records + kRecF4 * static_cast<size_t>(rid), 16u * kRecF4, &S.bar[buf]);
-    }
-}
-
-// Per-tile transform of the staged records: fold the tile origin into the
-// third column so that q = A (lx, ly, 1) with small, exact pixel offsets, and
-// replace the covered-pixel rectangle by the mask of the 8x4 warp blocks it
-// meets (bit w = warp w), so a warp skips a record with one shared load.
-__device__ __forceinline__ void transform_batch(Stage &S, int buf, int cnt, int tile_x0, int tile_y0)
-{
-    const int j = threadIdx.x;
-    if (j < cnt) {
-        float4 *r = S.rec[buf][j];
-        const float4 q = r[4];
-        const uint32_t bx = __float_as_uint(q.x), by = __float_as_uint(q.y);
-        const int x0 = static_cast<int>(bx & 0xFFFFu) - tile_x0, x1 = static_cast<int>(bx >> 16) - tile_x0;
-        const int y0 = static_cast<int>(by & 0xFFFFu) - tile_y0, y1 = static_cast<int>(by >> 16) - tile_y0;
-        uint32_t mask = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            const int cx = (w & 1) * 8, cy = (w >> 1) * 4;
-            if (x0 <= cx + 7 && x1 >= cx && y0 <= cy + 3 && y1 >= cy) mask |= 1u << w;
-        }
-        r[4] = make_float4(q.x, q.y, __uint_as_float(mask), 0.0f);
-        float4 x = r[0], y = r[1], z = r[2];
-        // record: a00 a01 a02 a10 | a11 a12 a20 a21 | a22 p0x p0y o | r2 r g b
-        const float ox = (static_cast<float>(tile_x0) + 0.5f) - z.y;
-        const float oy = (static_cast<float>(tile_y0) + 0.5f) - z.z;
-        x.z = __fmaf_rn(x.x, ox, __fmaf_rn(x.y, oy, x.z));
-        y.y = __fmaf_rn(x.w, ox, __fmaf_rn(y.x, oy, y.y));
-        z.x = __fmaf_rn(y.z, ox, __fmaf_rn(y.w, oy, z.x));
-        r[0] = x;
-        r[1] = y;
-        r[2] = z;
-    }
-}
-
-// does record j of buffer buf touch warp w's pixel block?
-__device__ __forceinline__ bool warp_hits(const Stage &S, int buf, int j, int w)
-{
-    return (__float_as_uint(S.rec[buf][j][4].z) >> w) & 1u;
-}
-
 // ------------------------------------------------------------ decoupled pipeline
 // A tile's list is streamed through kPS shared-memory stages of kPB records. A
 // dedicated producer warp (warp 8) fills a stage with one TMA bulk copy per
@@ -256,7 +193,10 @@ __device__ __forceinline__ int batch_range(int b, int n, bool reverse, int &cnt)
     return bi * kPB;
 }
 
-// transform one staged record for the tile (see transform_batch)
+// Per-tile transform of one staged record: fold the tile origin into the
+// third column so that q = A (lx, ly, 1) with small, exact pixel offsets, and
+// replace the covered-pixel rectangle by the mask of the 8x4 warp blocks it
+// meets (bit w = warp w), so a warp skips a record with one shared load.
 __device__ __forceinline__ void transform_record(float4 *r, int tile_x0, int tile_y0)
 {
     const float4 q = r[4];

@@ -16,6 +16,11 @@
 // Per-surfel sums are reduced across the warp (a transposing butterfly: 16
 // values in 16 shuffles) and added with one atomic per value per warp; the
 // feature gradient is accumulated warp-cooperatively across channels.
+// Both passes stream the list through the same producer-warp pipeline as the
+// forward kernel (raster.cuh): pass A front to back until every pixel is
+// saturated, pass B back to front from the largest last-composited position
+// of the tile; a warp visits only the records that meet its 8x4 block, and in
+// pass B only those before the last surfel of one of its pixels.
 // A second kernel turns the per-record moments into gradients of mu, t_u,
 // t_v, s_u, s_v through the camera.
 #include "raster.cuh"
@@ -79,97 +84,85 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
 }
 
 template <int KMAX, int DT, int CH>
-__global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
+__global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
 {
-    __shared__ __align__(128) Stage S;
+    __shared__ __align__(128) Pipe P;
     __shared__ int s_maxlast;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const bool producer = wid == kPixelWarps;
     const uint32_t tile = a.ranges[2 * fp.n_tiles_total + blockIdx.x]; // longest lists first
     const int v = view_of_tile(fp, tile);
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);
     const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-    int lxi, lyi;
-    pixel_of_thread(tid, lxi, lyi);
-    const int px = tx * kTile + lxi, py = ty * kTile + lyi;
-    const bool inside = px < cam.W && py < cam.H;
-    const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
     const int64_t list0 = a.ranges[2 * tile];
     const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
-    const int nb = (n + kBatch - 1) / kBatch;
     const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
     const int K = KMAX > 0 ? fp.top_k : 0;
-    const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
     const int tileX = tx * kTile, tileY = ty * kTile;
+    int lxi = 0, lyi = 0;
+    if (!producer) pixel_of_thread(tid, lxi, lyi);
+    const int px = tileX + lxi, py = tileY + lyi;
+    const bool inside = !producer && px < cam.W && py < cam.H;
+    const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
+    const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
 
     if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        fence_mbar_init();
+        pipe_init(P, kPixelWarps);
         s_maxlast = 0;
     }
     __syncthreads();
-    int uses0 = 0, uses1 = 0; // completed phases per buffer (uniform over the CTA)
-    auto parity = [&](int buf) { return static_cast<uint32_t>((buf ? uses1 : uses0) & 1); };
-    auto used = [&](int buf) {
-        if (buf)
-            ++uses1;
-        else
-            ++uses0;
-    };
 
-    // ---------------- pass A: forward recompute
-    if (wid == 0)
-        for (int b = 0; b < 2 && b < nb; ++b)
-            issue_batch(S, b, a.vals, list0, b * kBatch, min(kBatch, n - b * kBatch), a.records);
+    // ---------------- pass A: forward recompute (Top-K set, T_final, last)
     float T = 1.0f;
     int last = 0;
     bool done = !inside;
     TopK<(KMAX > 0 ? KMAX : 1)> top;
     top.init(K);
-    int issued = min(nb, 2), consumed = 0;
-    bool ok = true;
-    for (int b = 0; b < nb; ++b) {
-        const int buf = b & 1;
-        ok = mbar_wait(&S.bar[buf], parity(buf), a.status, kSiteRenderBwdA);
-        used(buf);
-        consumed = b + 1;
-        const int cnt = min(kBatch, n - b * kBatch);
-        if (ok) {
-            transform_batch(S, buf, cnt, tileX, tileY);
-            fence_proxy_async_smem();
-        }
-        if (__syncthreads_or(!ok)) break;
-        for (int j = 0; j < cnt; ++j) {
-            if (__all_sync(0xffffffffu, done)) break;
-            if (!warp_hits(S, buf, j, wid)) continue; // record misses this warp's pixel block
-            const Rec r = load_rec(S.rec[buf][j]);
-            Eval e;
-            const bool hit = !done && eval_alpha(r, lx, ly, e);
-            const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
-            const int pos = b * kBatch + j;
-            if constexpr (KMAX > 0) top.offer(hit, w, pos);
-            if (hit) {
-                T = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
-                last = pos + 1;
-                if (T < fp.t_eps) done = true;
+    if (producer) {
+        pipe_produce(P, a.vals, list0, n, false, a.records, tileX, tileY, a.status, kSiteRenderBwdA);
+    } else {
+        const int nb = (n + kPB - 1) / kPB;
+        bool wdone = __all_sync(0xffffffffu, done);
+        if (wdone && lane == 0) atomicSub(&P.alive, 1);
+        for (int b = 0; b < nb; ++b) {
+            if (!pipe_wait_ready(P, b, a.status, kSiteRenderBwdA)) break;
+            const int st = b % kPS;
+            int cnt;
+            const int lo = batch_range(b, n, false, cnt);
+            if (!wdone) {
+                uint32_t hw[kPB / 32];
+                pipe_hit_words(P, st, cnt, wid, hw);
+                bool all_done = false;
+#pragma unroll 1
+                for (int q = 0; q < kPB / 32 && !all_done; ++q)
+#pragma unroll 1
+                for (uint32_t bits = q == 0 ? hw[0] : q == 1 ? hw[1] : q == 2 ? hw[2] : hw[3]; bits; bits &= bits - 1) {
+                    if (__all_sync(0xffffffffu, done)) {
+                        all_done = true;
+                        break;
+                    }
+                    const int j = q * 32 + __ffs(bits) - 1;
+                    const Rec r = load_rec(P.rec[st][j]);
+                    Eval e;
+                    const bool hit = !done && eval_alpha(r, lx, ly, e);
+                    const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
+                    if constexpr (KMAX > 0) top.offer(hit, w, lo + j);
+                    if (hit) {
+                        T = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
+                        last = lo + j + 1;
+                        if (T < fp.t_eps) done = true;
+                    }
+                }
+            }
+            pipe_release(P, b);
+            if (!wdone && __all_sync(0xffffffffu, done)) {
+                wdone = true;
+                if (lane == 0) atomicSub(&P.alive, 1);
             }
         }
-        const int alive = __syncthreads_count(!done);
-        if (alive == 0) break;
-        if (b + 2 < nb) {
-            // every thread counts the batch (uniform phase bookkeeping); warp 0 issues it
-            if (wid == 0)
-                issue_batch(S, buf, a.vals, list0, (b + 2) * kBatch, min(kBatch, n - (b + 2) * kBatch), a.records);
-            ++issued;
-        }
     }
-    for (int b = consumed; b < issued; ++b) {
-        mbar_wait(&S.bar[b & 1], parity(b & 1), a.status, kSiteDrain);
-        used(b & 1);
-    }
-    if (__syncthreads_or(!ok)) return;
 
     // selected set and <gF, f_j> for each selected surfel
     float kd[KMAX > 0 ? KMAX : 1];
@@ -211,8 +204,23 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
         }
     }
     if (inside && last > 0) atomicMax(&s_maxlast, last);
+    __syncthreads(); // pass A is over for every warp and the producer drained its copies
+    if (vload(P.abort)) return;
+    if (tid == 0) {
+        // fresh barriers for the reverse walk
+        for (int s = 0; s < kPS; ++s) {
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.full[s])) : "memory");
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.ready[s])) : "memory");
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.empty[s])) : "memory");
+        }
+        pipe_init(P, kPixelWarps);
+    }
     __syncthreads();
     const int maxlast = s_maxlast;
+    if (producer) {
+        pipe_produce(P, a.vals, list0, maxlast, true, a.records, tileX, tileY, a.status, kSiteRenderBwdB);
+        return;
+    }
     // entries at or beyond every lane's last composited surfel are skipped by the warp
     int warp_last = last;
 #pragma unroll
@@ -223,178 +231,169 @@ __global__ void __launch_bounds__(kThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     const float gg = inside ? a.g_rgb[fp.n_pix_total + pix] : 0.0f;
     const float gb = inside ? a.g_rgb[2 * fp.n_pix_total + pix] : 0.0f;
     const float gt = (inside && a.g_T) ? a.g_T[pix] : 0.0f;
-    float Tc = T;                  // T after the current surfel, walking back
+    float Tc = T;                    // T after the current surfel, walking back
     float suffix = __fmul_rn(T, gt); // sum_{k>j} omega_k s_k + T_final gT
-    const int nbB = (maxlast + kBatch - 1) / kBatch;
+    const int nbB = (maxlast + kPB - 1) / kPB;
     const bool want_feat = a.g_F && a.g_feat;
-    if (wid == 0)
-        for (int k = 0; k < 2 && k < nbB; ++k) {
-            const int bi = nbB - 1 - k;
-            issue_batch(S, k, a.vals, list0, bi * kBatch, min(kBatch, maxlast - bi * kBatch), a.records);
-        }
-    issued = min(nbB, 2);
-    consumed = 0;
-    for (int k = 0; k < nbB; ++k) {
-        const int buf = k & 1;
-        const int bi = nbB - 1 - k;
-        ok = mbar_wait(&S.bar[buf], parity(buf), a.status, kSiteRenderBwdB);
-        used(buf);
-        consumed = k + 1;
-        const int cnt = min(kBatch, maxlast - bi * kBatch);
-        if (ok) {
-            transform_batch(S, buf, cnt, tileX, tileY);
-            fence_proxy_async_smem();
-        }
-        if (__syncthreads_or(!ok)) break;
-        for (int j = min(cnt, warp_last - bi * kBatch) - 1; j >= 0; --j) {
-            if (!warp_hits(S, buf, j, wid)) continue; // record misses this warp's pixel block
-            const int pos = bi * kBatch + j;
-            const Rec r = load_rec(S.rec[buf][j]);
-            Eval e;
-            const bool act = inside && pos < last && eval_alpha(r, lx, ly, e);
-            const uint32_t amask = __ballot_sync(0xffffffffu, act);
-            if (!amask) continue;
-            const uint32_t rid = S.val[buf][j];
-            const int64_t sid = static_cast<int64_t>(rid) - surf0;
-            float vals[16];
+    for (int b = 0; b < nbB; ++b) {
+        if (!pipe_wait_ready(P, b, a.status, kSiteRenderBwdB)) break;
+        const int st = b % kPS;
+        int cnt;
+        const int lo = batch_range(b, maxlast, true, cnt);
+        const int limit = min(cnt, warp_last - lo); // entries [0, limit) of the batch can matter
+        if (limit > 0) {
+            uint32_t hw[kPB / 32];
+            pipe_hit_words(P, st, cnt, wid, hw);
+#pragma unroll 1
+            for (int q = kPB / 32 - 1; q >= 0; --q) {
+                uint32_t bits = q == 0 ? hw[0] : q == 1 ? hw[1] : q == 2 ? hw[2] : hw[3];
+                const int room = limit - q * 32;
+                if (room <= 0) continue;
+                if (room < 32) bits &= (1u << room) - 1u;
+#pragma unroll 1
+                for (; bits; ) {
+                    const int jj = 31 - __clz(bits);
+                    bits &= ~(1u << jj);
+                    const int j = q * 32 + jj;
+                    const int pos = lo + j;
+                    const Rec r = load_rec(P.rec[st][j]);
+                    Eval e;
+                    const bool act = inside && pos < last && eval_alpha(r, lx, ly, e);
+                    const uint32_t amask = __ballot_sync(0xffffffffu, act);
+                    if (!amask) continue;
+                    const uint32_t rid = P.val[st][j];
+                    const int64_t sid = static_cast<int64_t>(rid) - surf0;
+                    float vals[16];
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) vals[k2] = 0.0f;
-            float w = 0.0f;
-            bool sel = false;
-            if (act) {
-                const float one_m = __fsub_rn(1.0f, e.alpha);
-                const float inv = rcp_approx(one_m); // one_m >= 0.01
-                const float Tj = Tc * inv;
-                w = e.alpha * Tj;
-                float dot = 0.0f;
-                if constexpr (KMAX > 0) {
+                    for (int k2 = 0; k2 < 16; ++k2) vals[k2] = 0.0f;
+                    float w = 0.0f;
+                    bool sel = false;
+                    if (act) {
+                        const float one_m = __fsub_rn(1.0f, e.alpha);
+                        const float inv = rcp_approx(one_m); // one_m >= 0.01
+                        const float Tj = Tc * inv;
+                        w = e.alpha * Tj;
+                        float dot = 0.0f;
+                        if constexpr (KMAX > 0) {
 #pragma unroll
-                    for (int s = 0; s < KMAX; ++s)
-                        if (kpos[s] == pos) {
+                            for (int s = 0; s < KMAX; ++s)
+                                if (kpos[s] == pos) {
+                                    sel = true;
+                                    dot = kd[s];
+                                }
+                        } else if (a.g_F && a.feat) {
+                            // dense features: every composited surfel is selected
                             sel = true;
-                            dot = kd[s];
-                        }
-                } else if (a.g_F && a.feat) {
-                    // dense features: every composited surfel is selected
-                    sel = true;
-                    for (int c0 = 0; c0 < a.D; c0 += CH) {
-                        float f[CH];
-                        load_feat<DT, CH>(a.feat, sid, a.D, c0, f);
+                            for (int c0 = 0; c0 < a.D; c0 += CH) {
+                                float f[CH];
+                                load_feat<DT, CH>(a.feat, sid, a.D, c0, f);
 #pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            const float sc = a.fscale ? __ldg(a.fscale + c0 + c) : 1.0f;
-                            dot = fmaf(__ldg(a.g_F + pix * a.D + c0 + c) * sc, f[c], dot);
-                        }
-                    }
-                }
-                const float4 col = S.rec[buf][j][3];
-                const float sj = gr * col.y + gg * col.z + gb * col.w + dot;
-                const float dLda = Tj * sj - suffix * inv;
-                suffix = fmaf(w, sj, suffix);
-                Tc = Tj;
-                vals[0] = w * gr;
-                vals[1] = w * gg;
-                vals[2] = w * gb;
-                if (!e.clamped) {
-                    const float rq = rcp_approx(e.q2);
-                    const float u = e.q0 * rq, vv = e.q1 * rq;
-                    const float d2 = u * u + vv * vv;
-                    const float aa = dLda * e.alpha;
-                    vals[3] = dLda * e.G;
-                    vals[4] = aa * u * u;
-                    vals[5] = aa * u * vv;
-                    vals[6] = aa * vv * vv;
-                    vals[7] = aa * u;
-                    vals[8] = aa * vv;
-                    vals[9] = aa * d2 * u;
-                    vals[10] = aa * d2 * vv;
-                }
-            }
-            if (__popc(amask) == 1) {
-                // a single contributing lane adds its values directly
-                if (act) {
-#pragma unroll
-                    for (int k2 = 0; k2 < 11; ++k2) {
-                        if (vals[k2] == 0.0f) continue;
-                        if (k2 < 3) {
-                            if (a.g_col) atomicAdd(a.g_col + 3 * sid + k2, vals[k2]);
-                        } else {
-                            atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (k2 - 3), vals[k2]);
-                        }
-                    }
-                }
-            } else {
-                const float tot = warp_transpose_sum16(vals, lane);
-                const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-                if ((lane & 1) == 0 && idx < 11 && tot != 0.0f) {
-                    if (idx < 3) {
-                        if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
-                    } else {
-                        atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (idx - 3), tot);
-                    }
-                }
-            }
-            if (want_feat) {
-                uint32_t selmask = __ballot_sync(0xffffffffu, act && sel);
-                if (selmask) {
-                    // lane l owns channels [4l, 4l+4) (+128 for D=256) of the surfel's
-                    // feature gradient; up to four selecting pixels per round so
-                    // their g_F loads are in flight together
-                    const int nv = a.D >> 2; // float4 chunks per row
-                    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-                    while (selmask) {
-                        int Ls[4];
-                        int nL = 0;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            Ls[q] = selmask ? __ffs(selmask) - 1 : -1;
-                            if (selmask) {
-                                selmask &= selmask - 1;
-                                ++nL;
+                                for (int c = 0; c < CH; ++c) {
+                                    const float sc = a.fscale ? __ldg(a.fscale + c0 + c) : 1.0f;
+                                    dot = fmaf(__ldg(a.g_F + pix * a.D + c0 + c) * sc, f[c], dot);
+                                }
                             }
                         }
-                        float wq[4];
-                        float4 g0[4], g1[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int L = Ls[q] < 0 ? 0 : Ls[q];
-                            wq[q] = __shfl_sync(0xffffffffu, w, L);
-                            const int pL = __shfl_sync(0xffffffffu, static_cast<int>(pix), L);
-                            const float4 *grow = reinterpret_cast<const float4 *>(a.g_F + static_cast<int64_t>(pL) * a.D);
-                            const bool on = q < nL;
-                            g0[q] = (on && lane < nv) ? __ldg(grow + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
-                            g1[q] = (on && lane + 32 < nv) ? __ldg(grow + lane + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (!on) wq[q] = 0.0f;
-                        }
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            acc0.x = fmaf(wq[q], g0[q].x, acc0.x);
-                            acc0.y = fmaf(wq[q], g0[q].y, acc0.y);
-                            acc0.z = fmaf(wq[q], g0[q].z, acc0.z);
-                            acc0.w = fmaf(wq[q], g0[q].w, acc0.w);
-                            acc1.x = fmaf(wq[q], g1[q].x, acc1.x);
-                            acc1.y = fmaf(wq[q], g1[q].y, acc1.y);
-                            acc1.z = fmaf(wq[q], g1[q].z, acc1.z);
-                            acc1.w = fmaf(wq[q], g1[q].w, acc1.w);
+                        const float4 col = P.rec[st][j][3];
+                        const float sj = gr * col.y + gg * col.z + gb * col.w + dot;
+                        const float dLda = Tj * sj - suffix * inv;
+                        suffix = fmaf(w, sj, suffix);
+                        Tc = Tj;
+                        vals[0] = w * gr;
+                        vals[1] = w * gg;
+                        vals[2] = w * gb;
+                        if (!e.clamped) {
+                            const float rq = rcp_approx(e.q2);
+                            const float u = e.q0 * rq, vv = e.q1 * rq;
+                            const float d2 = u * u + vv * vv;
+                            const float aa = dLda * e.alpha;
+                            vals[3] = dLda * e.G;
+                            vals[4] = aa * u * u;
+                            vals[5] = aa * u * vv;
+                            vals[6] = aa * vv * vv;
+                            vals[7] = aa * u;
+                            vals[8] = aa * vv;
+                            vals[9] = aa * d2 * u;
+                            vals[10] = aa * d2 * vv;
                         }
                     }
-                    float4 *dst = reinterpret_cast<float4 *>(a.g_feat + sid * a.D);
-                    if (lane < nv) atomicAdd(dst + lane, acc0);
-                    if (lane + 32 < nv) atomicAdd(dst + lane + 32, acc1);
+                    if (__popc(amask) == 1) {
+                        // a single contributing lane adds its values directly
+                        if (act) {
+#pragma unroll
+                            for (int k2 = 0; k2 < 11; ++k2) {
+                                if (vals[k2] == 0.0f) continue;
+                                if (k2 < 3) {
+                                    if (a.g_col) atomicAdd(a.g_col + 3 * sid + k2, vals[k2]);
+                                } else {
+                                    atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (k2 - 3), vals[k2]);
+                                }
+                            }
+                        }
+                    } else {
+                        const float tot = warp_transpose_sum16(vals, lane);
+                        const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                        if ((lane & 1) == 0 && idx < 11 && tot != 0.0f) {
+                            if (idx < 3) {
+                                if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
+                            } else {
+                                atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (idx - 3), tot);
+                            }
+                        }
+                    }
+                    if (want_feat) {
+                        uint32_t selmask = __ballot_sync(0xffffffffu, act && sel);
+                        if (selmask) {
+                            // lane l owns channels [4l, 4l+4) (+128 for D=256) of the surfel's
+                            // feature gradient; up to four selecting pixels per round so
+                            // their g_F loads are in flight together
+                            const int nv = a.D >> 2; // float4 chunks per row
+                            float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+                            while (selmask) {
+                                int Ls[4];
+                                int nL = 0;
+#pragma unroll
+                                for (int qq = 0; qq < 4; ++qq) {
+                                    Ls[qq] = selmask ? __ffs(selmask) - 1 : -1;
+                                    if (selmask) {
+                                        selmask &= selmask - 1;
+                                        ++nL;
+                                    }
+                                }
+                                float wq[4];
+                                float4 g0[4], g1[4];
+#pragma unroll
+                                for (int qq = 0; qq < 4; ++qq) {
+                                    const int L = Ls[qq] < 0 ? 0 : Ls[qq];
+                                    wq[qq] = __shfl_sync(0xffffffffu, w, L);
+                                    const int pL = __shfl_sync(0xffffffffu, static_cast<int>(pix), L);
+                                    const float4 *grow = reinterpret_cast<const float4 *>(a.g_F + static_cast<int64_t>(pL) * a.D);
+                                    const bool on = qq < nL;
+                                    g0[qq] = (on && lane < nv) ? __ldg(grow + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                    g1[qq] = (on && lane + 32 < nv) ? __ldg(grow + lane + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                    if (!on) wq[qq] = 0.0f;
+                                }
+#pragma unroll
+                                for (int qq = 0; qq < 4; ++qq) {
+                                    acc0.x = fmaf(wq[qq], g0[qq].x, acc0.x);
+                                    acc0.y = fmaf(wq[qq], g0[qq].y, acc0.y);
+                                    acc0.z = fmaf(wq[qq], g0[qq].z, acc0.z);
+                                    acc0.w = fmaf(wq[qq], g0[qq].w, acc0.w);
+                                    acc1.x = fmaf(wq[qq], g1[qq].x, acc1.x);
+                                    acc1.y = fmaf(wq[qq], g1[qq].y, acc1.y);
+                                    acc1.z = fmaf(wq[qq], g1[qq].z, acc1.z);
+                                    acc1.w = fmaf(wq[qq], g1[qq].w, acc1.w);
+                                }
+                            }
+                            float4 *dst = reinterpret_cast<float4 *>(a.g_feat + sid * a.D);
+                            if (lane < nv) atomicAdd(dst + lane, acc0);
+                            if (lane + 32 < nv) atomicAdd(dst + lane + 32, acc1);
+                        }
+                    }
                 }
             }
         }
-        __syncthreads();
-        if (k + 2 < nbB) {
-            const int bi2 = nbB - 1 - (k + 2);
-            if (wid == 0)
-                issue_batch(S, buf, a.vals, list0, bi2 * kBatch, min(kBatch, maxlast - bi2 * kBatch), a.records);
-            ++issued;
-        }
-    }
-    for (int k = consumed; k < issued; ++k) {
-        mbar_wait(&S.bar[k & 1], parity(k & 1), a.status, kSiteDrain);
-        used(k & 1);
+        pipe_release(P, b);
     }
 }
 
@@ -494,9 +493,9 @@ cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const BwdArgs &a
 {
     const unsigned grid = fp.n_tiles_total;
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
-    default: render_bwd_kernel<KMAX, PSI_F32, CH><<<grid, kThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    default: render_bwd_kernel<KMAX, PSI_F32, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
 }
