@@ -43,7 +43,7 @@ PAPER_CONTEXT = ("Table 3 of the paper: Full Method 22 ms / 45 FPS, Baseline 46 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=256)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="psi", choices=["psi", "reference"])
     ap.add_argument("--surfels", type=int, default=3_000_000)
@@ -142,7 +142,8 @@ def job_throughput(steps_per_rank: int, world: int, max_ms: float) -> float:
 
 def roofline_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel (else None)."""
+    on the current sources of that kernel (its .cu file and the headers it
+    includes, hashed together in the listed order; else None)."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         d = json.load(open(path))
@@ -151,12 +152,13 @@ def roofline_traffic(kernel: str):
     e = d.get(kernel)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_2604_10982_gb300", "csrc", e["source"])
+    h = hashlib.sha256()
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
+        for name in e["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2604_10982_gb300", "csrc", name), "rb").read())
+    except (OSError, KeyError):
         return None
-    return e["bytes_per_launch"] if h == e.get("sha256_16") else None
+    return e["bytes_per_launch"] if h.hexdigest()[:16] == e.get("sha256_16") else None
 
 
 def measured_peaks():

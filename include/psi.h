@@ -237,18 +237,25 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
                    const psi_render_opts *o, const psi_fwd_out *out, psi_stream stream);
 
 /* ---- a5: adjoint of a4 ----------------------------------------------------
- * Recomputes the front-to-back pass (and hence the same Top-K sets), then walks
- * back to front with suffix sums: dL/dalpha_j = T_j s_j - (sum_{k>j} omega_k
- * s_k + T_final g_T)/(1 - alpha_j), s_j = <gC, c_j> + [j in K]<gF, f_j>, and
- * chains through alpha = o G, (u,v) of the homogeneous ray-splat map, to mu,
- * t_u, t_v, s, o; also dL/dc, dL/df. g_F and g_T may be NULL.
+ * Takes each pixel's final transmittance, last composited list position and
+ * Top-K set from the forward (or recomputes the front-to-back pass, which gives
+ * the same values), then walks back to front with suffix sums: dL/dalpha_j =
+ * T_j s_j - (sum_{k>j} omega_k s_k + T_final g_T)/(1 - alpha_j), s_j = <gC,
+ * c_j> + [j in K]<gF, f_j>, and chains through alpha = o G, (u,v) of the
+ * homogeneous ray-splat map, to mu, t_u, t_v, s, o; also dL/dc, dL/df. g_F
+ * and g_T may be NULL.
  *  g_rgb: [3][P_total] planar; g_F: [P_total, D] float32, 16-byte aligned
  *  (as grads->feat); g_T: [P_total]
+ *  saved: NULL (recompute), or psi_render_fwd's outputs for the same records,
+ *  vals, tile_ranges, cams and opts: T and n_last, and topk_ids when top_k > 0
+ *  (other members ignored; missing ones are PSI_ERR_INVALID_ARG). Outputs that
+ *  do not belong to this frame give wrong gradients; nothing checks that.
  *  workspace: psi_render_bwd_workspace_size(n_views*N) bytes. */
 int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
                    const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
                    const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
-                   const psi_grads *grads, void *workspace, size_t workspace_bytes, psi_stream stream);
+                   const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
+                   psi_stream stream);
 
 /* ---- a6: query decode (Sec. 4.1, Eq. 4 without the monotone sigmoid) -----
  * logits[p,q] = sum_c F[p,c] Q[q,c] on the tensor cores (BF16 in, FP32

@@ -327,7 +327,8 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
 int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
                    const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
                    const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
-                   const psi_grads *grads, void *workspace, size_t workspace_bytes, psi_stream stream)
+                   const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
+                   psi_stream stream)
 {
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc;
@@ -339,6 +340,8 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
     if (g_F && !fv.data) return fail(ctx, PSI_ERR_INVALID_ARG, "g_F given without features");
     if (!aligned(g_F, 16) || !aligned(grads->feat, 16))
         return fail(ctx, PSI_ERR_INVALID_ARG, "g_F and grads->feat must be 16-byte aligned");
+    if (saved && (!saved->T || !saved->n_last || (o->top_k > 0 && !saved->topk_ids)))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "saved forward state needs T, n_last and (top_k > 0) topk_ids");
     const size_t need = psi::render_bwd_workspace_bytes(s->n * n_views);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
         return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
@@ -346,7 +349,7 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
     psi::FrameParams fp;
     psi::fill_frame_params(fp, cams, n_views, o, s->n);
     cudaError_t e = psi::launch_render_bwd(fp, *s, fv, static_cast<const float4 *>(records), vals, tile_ranges, g_rgb,
-                                           g_F, g_T, *grads, workspace, ctx->status,
+                                           g_F, g_T, saved, *grads, workspace, ctx->status,
                                            reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_render_bwd", e);
 }

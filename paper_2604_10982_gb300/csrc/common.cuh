@@ -193,7 +193,8 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
 size_t render_bwd_workspace_bytes(int64_t n_records);
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
-                              const float *g_T, const psi_grads &g, void *ws, DevStatus *status, cudaStream_t st);
+                              const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
+                              DevStatus *status, cudaStream_t st);
 
 cudaError_t launch_decode(const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T, int32_t *ids,
                           void *logits, DevStatus *status, cudaStream_t st, const char **why);

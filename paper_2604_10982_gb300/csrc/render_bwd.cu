@@ -46,6 +46,10 @@ struct BwdArgs {
     float *g_feat;      // [N,D] or NULL
     float *moments;     // [R, 8]
     DevStatus *status;
+    // forward state of the same frame (all NULL: recompute it in pass A)
+    const float *saved_T;      // [P_total]
+    const int32_t *saved_last; // [P_total]
+    const int32_t *saved_topk; // [P_total, K] surfel ids in list order, -1 padded
 };
 
 // Sum 16 per-lane values over the warp: afterwards lane l (and l^1) holds the
@@ -83,7 +87,9 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
     return v[0];
 }
 
-template <int KMAX, int DT, int CH>
+// SAVED: T_final, last and the Top-K ids come from the forward's outputs;
+// otherwise pass A recomputes them. CH (channel chunk) matters only for K = 0.
+template <int KMAX, int DT, int CH, bool SAVED>
 __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
 {
@@ -114,13 +120,20 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     }
     __syncthreads();
 
-    // ---------------- pass A: forward recompute (Top-K set, T_final, last)
+    // ---------------- pass A: forward recompute (Top-K set, T_final, last),
+    // unless the forward's own outputs for this frame are given
+    constexpr bool recompute = !SAVED;
     float T = 1.0f;
     int last = 0;
     bool done = !inside;
     TopK<(KMAX > 0 ? KMAX : 1)> top;
     top.init(K);
-    if (producer) {
+    if constexpr (SAVED) {
+        if (inside) {
+            T = a.saved_T[pix];
+            last = a.saved_last[pix];
+        }
+    } else if (producer) {
         pipe_produce(P, a.vals, list0, n, false, a.records, tileX, tileY, a.status, kSiteRenderBwdA);
     } else {
         const int nb = (n + kPB - 1) / kPB;
@@ -164,16 +177,24 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
         }
     }
 
-    // selected set and <gF, f_j> for each selected surfel
+    // selected set (surfel ids; a surfel occurs at most once in a tile's list)
+    // and <gF, f_j> for each selected surfel
     float kd[KMAX > 0 ? KMAX : 1];
-    int kpos[KMAX > 0 ? KMAX : 1];
+    int kid[KMAX > 0 ? KMAX : 1];
     if constexpr (KMAX > 0) {
-        top.sort_by_pos();
+        if constexpr (recompute) {
+            top.sort_by_pos();
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            kpos[s] = (inside && top.valid(s, K)) ? top.p[s] : -1;
-            kd[s] = 0.0f;
+            for (int s = 0; s < KMAX; ++s)
+                kid[s] = (inside && top.valid(s, K))
+                             ? static_cast<int>(static_cast<int64_t>(a.vals[list0 + top.p[s]]) - surf0)
+                             : -1;
+        } else {
+#pragma unroll
+            for (int s = 0; s < KMAX; ++s) kid[s] = (inside && s < K) ? a.saved_topk[pix * K + s] : -1;
         }
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) kd[s] = 0.0f;
         if (a.g_F && a.feat && inside) {
             for (int c0 = 0; c0 < a.D; c0 += 16) {
                 float g[16];
@@ -191,10 +212,9 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                 }
 #pragma unroll
                 for (int s = 0; s < KMAX; ++s) {
-                    if (kpos[s] < 0) continue;
-                    const int64_t sid = static_cast<int64_t>(a.vals[list0 + kpos[s]]) - surf0;
+                    if (kid[s] < 0) continue;
                     float f[16];
-                    load_feat<DT, 16>(a.feat, sid, a.D, c0, f);
+                    load_feat<DT, 16>(a.feat, kid[s], a.D, c0, f);
                     float acc = kd[s];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) acc = __fmaf_rn(g[c], f[c], acc);
@@ -205,17 +225,19 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     }
     if (inside && last > 0) atomicMax(&s_maxlast, last);
     __syncthreads(); // pass A is over for every warp and the producer drained its copies
-    if (vload(P.abort)) return;
-    if (tid == 0) {
-        // fresh barriers for the reverse walk
-        for (int s = 0; s < kPS; ++s) {
-            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.full[s])) : "memory");
-            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.ready[s])) : "memory");
-            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.empty[s])) : "memory");
+    if constexpr (recompute) {
+        if (vload(P.abort)) return;
+        if (tid == 0) {
+            // fresh barriers for the reverse walk
+            for (int s = 0; s < kPS; ++s) {
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.full[s])) : "memory");
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.ready[s])) : "memory");
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.empty[s])) : "memory");
+            }
+            pipe_init(P, kPixelWarps);
         }
-        pipe_init(P, kPixelWarps);
+        __syncthreads();
     }
-    __syncthreads();
     const int maxlast = s_maxlast;
     if (producer) {
         pipe_produce(P, a.vals, list0, maxlast, true, a.records, tileX, tileY, a.status, kSiteRenderBwdB);
@@ -277,7 +299,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                         if constexpr (KMAX > 0) {
 #pragma unroll
                             for (int s = 0; s < KMAX; ++s)
-                                if (kpos[s] == pos) {
+                                if (kid[s] == static_cast<int>(sid)) {
                                     sel = true;
                                     dot = kd[s];
                                 }
@@ -488,22 +510,32 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     }
 }
 
-template <int KMAX, int CH>
-cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+template <int KMAX, int CH, bool SAVED>
+cudaError_t launch_kcs(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
 {
     const unsigned grid = fp.n_tiles_total;
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    default: render_bwd_kernel<KMAX, PSI_F32, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH, SAVED><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    default: render_bwd_kernel<KMAX, PSI_F32, CH, SAVED><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
+}
+
+template <int KMAX, int CH>
+cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+{
+    return a.saved_T ? launch_kcs<KMAX, CH, true>(fp, f, a, st) : launch_kcs<KMAX, CH, false>(fp, f, a, st);
 }
 
 template <int KMAX>
 cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const BwdArgs &a, int ch, cudaStream_t st)
 {
-    return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
+    // the channel chunk only shapes the dense (K = 0) feature dot product
+    if constexpr (KMAX > 0)
+        return launch_kc<KMAX, 16>(fp, f, a, st);
+    else
+        return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
 }
 
 } // namespace
@@ -515,7 +547,8 @@ size_t render_bwd_workspace_bytes(int64_t n_records)
 
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
-                              const float *g_T, const psi_grads &g, void *ws, DevStatus *status, cudaStream_t st)
+                              const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
+                              DevStatus *status, cudaStream_t st)
 {
     const int64_t R = fp.n * fp.n_views;
     cudaError_t e = cudaMemsetAsync(ws, 0, render_bwd_workspace_bytes(R), st);
@@ -534,6 +567,11 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
     a.g_feat = f.data ? g.feat : nullptr;
     a.moments = static_cast<float *>(ws);
     a.status = status;
+    if (saved) {
+        a.saved_T = saved->T;
+        a.saved_last = saved->n_last;
+        a.saved_topk = saved->topk_ids;
+    }
     const int ch = (f.dim % 32 == 0) ? 32 : 16;
     const int K = fp.top_k;
     if (K == 0)

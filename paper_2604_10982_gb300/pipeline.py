@@ -83,7 +83,7 @@ class Renderer:
     """Holds the per-frame device buffers for a fixed (N, cameras, opts)."""
 
     def __init__(self, ctx: psi.Context, n_surfels: int, cams, opts: psi.PsiRenderOpts, capacity: int,
-                 D: int = 0, F_dtype: int = psi.F32, want_topk_ids: bool = False, device="cuda"):
+                 D: int = 0, F_dtype: int = psi.F32, want_topk_ids: bool = True, device="cuda"):
         self.ctx = ctx
         self.dev = torch.device(device)
         self.cams_py = list(cams)
@@ -170,10 +170,19 @@ class Renderer:
         psi.psi_render_fwd(self.ctx, feats, self.records, self.vals, self.ranges, self.cams, self.V, self.n, self.opts,
                            out, stream)
 
+    def saved_state(self):
+        """The forward outputs the adjoint reuses (None if the Top-K ids are not kept)."""
+        if int(self.opts.top_k) > 0 and self.topk_ids is None:
+            return None
+        return psi.PsiFwdOut(psi._ptr(self.rgb), psi._ptr(self.T), psi._ptr(self.n_last), None, int(self.F_dtype),
+                             psi._ptr(self.topk_ids))
+
     # a5
-    def backward(self, scene: DeviceScene, g_rgb, g_F=None, g_T=None, grads=None, stream=None):
+    def backward(self, scene: DeviceScene, g_rgb, g_F=None, g_T=None, grads=None, stream=None, recompute=False):
         """Gradients (float32, [N, ...]) of L = <g_rgb, rgb> + <g_F, F> + <g_T, T>
-        for the frame last rendered by this renderer."""
+        for the frame last rendered by this renderer. The adjoint reuses that
+        frame's T, n_last and Top-K ids unless ``recompute`` is set (or the ids
+        were not kept), in which case it recomputes them from the lists."""
         dev = self.dev
         n, D = self.n, scene.D
         if grads is None:
@@ -187,7 +196,7 @@ class Renderer:
         psi.psi_render_bwd(self.ctx, scene.surfels_struct(), scene.features_struct(), self.records, self.vals,
                            self.ranges, self.cams, self.V, self.opts, g_rgb.contiguous(),
                            None if g_F is None else g_F.contiguous(), None if g_T is None else g_T.contiguous(),
-                           gs, self.ws_bwd, stream)
+                           None if recompute else self.saved_state(), gs, self.ws_bwd, stream)
         return grads
 
     def frame(self, scene: DeviceScene, want_F: bool = True, stream=None):
@@ -211,7 +220,7 @@ class Renderer:
         return t[a:b].reshape(c.height, c.width, *t.shape[1:])
 
 
-def make_renderer(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, want_topk_ids=False, headroom=1.25,
+def make_renderer(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, want_topk_ids=True, headroom=1.25,
                   min_capacity=1024):
     """Renderer whose key buffer fits this scene and these cameras."""
     r = Renderer(ctx, scene.n, cams, opts, min_capacity, D=D, F_dtype=F_dtype, want_topk_ids=want_topk_ids,
@@ -224,8 +233,9 @@ def make_renderer(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, wan
 class PsiRender(torch.autograd.Function):
     """Differentiable frame: (mu, tu, tv, scale, opacity, rgb, feat) -> (rgb image
     [3, P], feature map [P, D], transmittance [P]). The backward pass is the
-    library's hand-written adjoint (psi_render_bwd), which recomputes the Top-K
-    sets instead of storing per-pixel lists. The tensors must be the ones held
+    library's hand-written adjoint (psi_render_bwd), which reuses the frame's
+    per-pixel T, last position and Top-K ids (no per-pixel lists are stored).
+    The tensors must be the ones held
     by ``scene``; one frame per renderer may be in flight between forward and
     backward (the renderer's buffers hold it)."""
 

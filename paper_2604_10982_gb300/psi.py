@@ -91,7 +91,7 @@ def lib():
                                      ctypes.c_int, _i64, ctypes.POINTER(PsiRenderOpts), ctypes.POINTER(PsiFwdOut), _P]
         L.psi_render_bwd.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures), _P, _P, _P,
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
-                                     ctypes.POINTER(PsiGrads), _P, sz, _P]
+                                     ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_decode_queries.argtypes = [_P, _P, _i64, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]
         _lib = L
     return _lib
@@ -250,10 +250,13 @@ def psi_render_fwd(ctx, feats, records, vals, tile_ranges, cams_arr, n_views, n_
 
 
 def psi_render_bwd(ctx, s, feats, records, vals, tile_ranges, cams_arr, n_views, opts, g_rgb, g_F, g_T,
-                   grads: PsiGrads, workspace, stream=None):
+                   saved, grads: PsiGrads, workspace, stream=None):
+    """saved: a PsiFwdOut holding the forward's T, n_last (and topk_ids when
+    top_k > 0) of this frame, or None to recompute them."""
     ctx.check(lib().psi_render_bwd(ctx.handle, ctypes.byref(s), ctypes.byref(feats), _ptr(records), _ptr(vals),
                                    _ptr(tile_ranges), cams_arr, n_views, ctypes.byref(opts), _ptr(g_rgb), _ptr(g_F),
-                                   _ptr(g_T), ctypes.byref(grads), _ptr(workspace),
+                                   _ptr(g_T), None if saved is None else ctypes.byref(saved), ctypes.byref(grads),
+                                   _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), _stream(stream)), "psi_render_bwd")
 
 

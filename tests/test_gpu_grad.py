@@ -62,7 +62,10 @@ def _grad_compare(ctx, w, cams, o, D, tol=1e-3, sample_pixels=None):
     tgC = torch.from_numpy(np.ascontiguousarray(gC)).cuda()
     tgF = torch.from_numpy(np.ascontiguousarray(gF)).cuda() if D else None
     tgT = torch.from_numpy(gT).cuda()
+    # both adjoint forms: the forward's saved T / last / Top-K ids, and the
+    # recomputing walk; each against the oracle, and against each other
     g = r.backward(scene, tgC, tgF, tgT)
+    g_re = r.backward(scene, tgC, tgF, tgT, recompute=True)
     torch.cuda.synchronize()
     st, _ = ctx.status_fetch()
     assert st == 0
@@ -80,12 +83,16 @@ def _grad_compare(ctx, w, cams, o, D, tol=1e-3, sample_pixels=None):
     for k in KEYS:
         if k == "feat" and not D:
             continue
-        gk = g[k].cpu().numpy().astype(np.float64).reshape(ref[k].shape)
         den = np.linalg.norm(ref[k])
-        rel = np.linalg.norm(gk - ref[k]) / max(den, 1e-30)
-        report[k] = rel
         assert den > 0, k
-        assert rel < tol, (k, rel)
+        for form, gg in (("saved", g), ("recompute", g_re)):
+            gk = gg[k].cpu().numpy().astype(np.float64).reshape(ref[k].shape)
+            rel = np.linalg.norm(gk - ref[k]) / max(den, 1e-30)
+            report[(k, form)] = rel
+            assert rel < tol, (k, form, rel)
+        # same arithmetic; only the order of the float32 atomic additions differs
+        a, b = g[k].double(), g_re[k].double()
+        assert torch.linalg.norm(a - b).item() <= 1e-5 * max(torch.linalg.norm(a).item(), 1e-30), k
     return report
 
 
@@ -150,3 +157,27 @@ def test_grad_long_lists_early_exit(ctx):
     w = sg.dense_box(n=20000, d=16, width=64, height=48, scale_median=0.25)
     o = orc.Opts(mode=orc.AABB, top_k=8)
     _grad_compare(ctx, w, w.cameras, o, 16)
+
+
+def test_saved_state_needs_topk_ids(ctx):
+    """Saved forward state without Top-K ids (K > 0) is refused."""
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    w = sg.crop_scene(n=200, d=16, size=32)
+    o = orc.Opts(mode=orc.EXACT, top_k=8)
+    scene = pl.DeviceScene(w.surfels, w.features)
+    r = pl.make_renderer(ctx, scene, w.cameras, opts_of(o), D=16, want_topk_ids=False)
+    r.frame(scene)
+    assert r.saved_state() is None
+    saved = psi.PsiFwdOut(psi._ptr(r.rgb), psi._ptr(r.T), psi._ptr(r.n_last), None, psi.F32, None)
+    gC = torch.zeros(3, r.n_pix, device="cuda")
+    grads = {k: torch.zeros(r.n, 3, device="cuda") for k in ("mu", "tu", "tv", "rgb")}
+    gs = psi.PsiGrads(*(psi._ptr(grads.get(k)) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
+    ws = torch.empty(psi.render_bwd_workspace_size(r.n), dtype=torch.uint8, device="cuda")
+    with pytest.raises(psi.PsiError) as e:
+        psi.psi_render_bwd(ctx, scene.surfels_struct(), scene.features_struct(), r.records, r.vals, r.ranges,
+                           r.cams, r.V, r.opts, gC, None, None, saved, gs, ws)
+    assert e.value.code == psi.PSI_ERR_INVALID_ARG
+    # the recomputing form still runs on the same renderer
+    g = r.backward(scene, gC)
+    torch.cuda.synchronize()
+    assert ctx.status_fetch()[0] == 0
