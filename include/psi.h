@@ -113,7 +113,8 @@ typedef struct {
  *  T:        [P_total] final transmittance; required
  *  n_last:   [P_total] int32, 1 + list position of the last surfel composited (0: none)
  *  F:        [P_total, D] feature map in F_dtype (PSI_F32 or PSI_BF16)
- *  topk_ids: [P_total, K] int32 surfel ids of the selected set in list order, -1 padded */
+ *  topk_ids: [P_total, K] int32 surfel ids of the selected set in list order, -1 padded
+ *  topk_w:   [P_total, K] float32 weights omega_j = alpha_j T_j of those surfels, 0 padded */
 typedef struct {
     float *rgb;
     float *T;
@@ -121,6 +122,7 @@ typedef struct {
     void *F;
     int32_t F_dtype;
     int32_t *topk_ids;
+    float *topk_w;
 } psi_fwd_out;
 
 /* Gradients (device, float32, ACCUMULATED into: the caller zeroes them). Any
@@ -160,7 +162,9 @@ int psi_view_layout(const psi_camera *cams, int n_views, const psi_render_opts *
 /* ---- workspace sizes (bytes of caller-allocated scratch, 256-B aligned) -- */
 int psi_intersect_workspace_size(int64_t n_records, size_t *bytes);
 int psi_sort_workspace_size(int64_t capacity, size_t *bytes);
-int psi_render_bwd_workspace_size(int64_t n_records, size_t *bytes);
+/* Adjoint scratch: per-record moments (n_records = n_views * N) and, for
+ * top_k > 0, one float per (pixel, selected slot) (n_pix = P_total). */
+int psi_render_bwd_workspace_size(int64_t n_records, int64_t n_pix, int top_k, size_t *bytes);
 
 /* ---- a1: projection and ray-splat setup --------------------------------
  * Per (view, surfel): camera transform, the pixel-homogeneous 3x3 map M of the
@@ -247,10 +251,13 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
  *  g_rgb: [3][P_total] planar; g_F: [P_total, D] float32, 16-byte aligned
  *  (as grads->feat); g_T: [P_total]
  *  saved: NULL (recompute), or psi_render_fwd's outputs for the same records,
- *  vals, tile_ranges, cams and opts: T and n_last, and topk_ids when top_k > 0
- *  (other members ignored; missing ones are PSI_ERR_INVALID_ARG). Outputs that
- *  do not belong to this frame give wrong gradients; nothing checks that.
- *  workspace: psi_render_bwd_workspace_size(n_views*N) bytes. */
+ *  vals, tile_ranges, cams and opts: T and n_last, and topk_ids and topk_w
+ *  when top_k > 0 (other members ignored; missing ones are
+ *  PSI_ERR_INVALID_ARG). With them the feature part of the adjoint (<gF, f_j>
+ *  and dL/df) runs per pixel from the saved selection, outside the list walk.
+ *  Outputs that do not belong to this frame give wrong gradients; nothing
+ *  checks that.
+ *  workspace: psi_render_bwd_workspace_size(n_views*N, P_total, top_k) bytes. */
 int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
                    const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
                    const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,

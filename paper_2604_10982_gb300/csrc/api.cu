@@ -209,10 +209,10 @@ int psi_sort_workspace_size(int64_t capacity, size_t *bytes)
     return PSI_OK;
 }
 
-int psi_render_bwd_workspace_size(int64_t n_records, size_t *bytes)
+int psi_render_bwd_workspace_size(int64_t n_records, int64_t n_pix, int top_k, size_t *bytes)
 {
-    if (!bytes || n_records < 0) return PSI_ERR_INVALID_ARG;
-    *bytes = psi::render_bwd_workspace_bytes(n_records);
+    if (!bytes || n_records < 0 || n_pix < 0 || top_k < 0 || top_k > PSI_MAX_TOPK) return PSI_ERR_INVALID_ARG;
+    *bytes = psi::render_bwd_workspace_bytes(n_records, n_pix, top_k);
     return PSI_OK;
 }
 
@@ -340,9 +340,15 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
     if (g_F && !fv.data) return fail(ctx, PSI_ERR_INVALID_ARG, "g_F given without features");
     if (!aligned(g_F, 16) || !aligned(grads->feat, 16))
         return fail(ctx, PSI_ERR_INVALID_ARG, "g_F and grads->feat must be 16-byte aligned");
-    if (saved && (!saved->T || !saved->n_last || (o->top_k > 0 && !saved->topk_ids)))
-        return fail(ctx, PSI_ERR_INVALID_ARG, "saved forward state needs T, n_last and (top_k > 0) topk_ids");
-    const size_t need = psi::render_bwd_workspace_bytes(s->n * n_views);
+    if (saved && (!saved->T || !saved->n_last || (o->top_k > 0 && (!saved->topk_ids || !saved->topk_w))))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "saved forward state needs T, n_last and (top_k > 0) topk_ids, topk_w");
+    int64_t n_pix_total = 0;
+    {
+        int64_t tb[PSI_MAX_VIEWS + 1], pb[PSI_MAX_VIEWS + 1];
+        if ((rc = psi_view_layout(cams, n_views, o, tb, pb))) return fail(ctx, rc, "camera layout");
+        n_pix_total = pb[n_views];
+    }
+    const size_t need = psi::render_bwd_workspace_bytes(s->n * n_views, n_pix_total, o->top_k);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
         return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
     DeviceGuard g(ctx->device);

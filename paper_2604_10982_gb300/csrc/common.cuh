@@ -190,7 +190,9 @@ struct FeatView {
 cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const float4 *records, const uint32_t *vals,
                               const uint32_t *ranges, const psi_fwd_out &out, DevStatus *status, cudaStream_t st);
 
-size_t render_bwd_workspace_bytes(int64_t n_records);
+size_t render_bwd_workspace_bytes(int64_t n_records, int64_t n_pix, int top_k);
+cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int32_t *topk_ids, const float *topk_w,
+                            const float *g_F, float *kd, float *g_feat, cudaStream_t st);
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,

@@ -50,6 +50,7 @@ struct BwdArgs {
     const float *saved_T;      // [P_total]
     const int32_t *saved_last; // [P_total]
     const int32_t *saved_topk; // [P_total, K] surfel ids in list order, -1 padded
+    const float *kd_saved;     // [P_total, K] <gF, f_j> of the saved set (feat_bwd.cu), or NULL
 };
 
 // Sum 16 per-lane values over the warp: afterwards lane l (and l^1) holds the
@@ -88,7 +89,9 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
 }
 
 // SAVED: T_final, last and the Top-K ids come from the forward's outputs;
-// otherwise pass A recomputes them. CH (channel chunk) matters only for K = 0.
+// otherwise pass A recomputes them. With SAVED and K > 0 the feature terms
+// (<gF, f_j> and dL/df) come from the per-pixel feature kernel instead of this
+// walk. CH (channel chunk) matters only for K = 0.
 template <int KMAX, int DT, int CH, bool SAVED>
 __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     // ---------------- pass A: forward recompute (Top-K set, T_final, last),
     // unless the forward's own outputs for this frame are given
     constexpr bool recompute = !SAVED;
+    constexpr bool ext_feat = SAVED && KMAX > 0; // feature terms computed outside the walk
     float T = 1.0f;
     int last = 0;
     bool done = !inside;
@@ -195,7 +199,13 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
         }
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) kd[s] = 0.0f;
-        if (a.g_F && a.feat && inside) {
+        if (ext_feat) {
+            if (a.kd_saved && inside) {
+#pragma unroll
+                for (int s = 0; s < KMAX; ++s)
+                    if (s < K) kd[s] = a.kd_saved[pix * K + s];
+            }
+        } else if (a.g_F && a.feat && inside) {
             for (int c0 = 0; c0 < a.D; c0 += 16) {
                 float g[16];
 #pragma unroll
@@ -256,7 +266,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     float Tc = T;                    // T after the current surfel, walking back
     float suffix = __fmul_rn(T, gt); // sum_{k>j} omega_k s_k + T_final gT
     const int nbB = (maxlast + kPB - 1) / kPB;
-    const bool want_feat = a.g_F && a.g_feat;
+    const bool want_feat = !ext_feat && a.g_F && a.g_feat;
     for (int b = 0; b < nbB; ++b) {
         if (!pipe_wait_ready(P, b, a.status, kSiteRenderBwdB)) break;
         const int st = b % kPS;
@@ -540,9 +550,17 @@ cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const BwdArgs &a,
 
 } // namespace
 
-size_t render_bwd_workspace_bytes(int64_t n_records)
+namespace {
+size_t moments_bytes(int64_t n_records)
 {
     return align_up(static_cast<size_t>(std::max<int64_t>(n_records, 1)) * kMoments * sizeof(float), 256);
+}
+} // namespace
+
+size_t render_bwd_workspace_bytes(int64_t n_records, int64_t n_pix, int top_k)
+{
+    const size_t kd = top_k > 0 ? align_up(static_cast<size_t>(n_pix) * top_k * sizeof(float), 256) : 0;
+    return moments_bytes(n_records) + kd;
 }
 
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
@@ -551,7 +569,7 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
                               DevStatus *status, cudaStream_t st)
 {
     const int64_t R = fp.n * fp.n_views;
-    cudaError_t e = cudaMemsetAsync(ws, 0, render_bwd_workspace_bytes(R), st);
+    cudaError_t e = cudaMemsetAsync(ws, 0, moments_bytes(R), st);
     if (e != cudaSuccess || R == 0 || fp.n_tiles_total == 0) return e;
     BwdArgs a{};
     a.records = records;
@@ -571,6 +589,13 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
         a.saved_T = saved->T;
         a.saved_last = saved->n_last;
         a.saved_topk = saved->topk_ids;
+        if (fp.top_k > 0 && a.g_F) {
+            // feature terms from the saved selection: kd for the walk, dL/df
+            float *kd = reinterpret_cast<float *>(static_cast<char *>(ws) + moments_bytes(R));
+            e = launch_feat_bwd(fp, f, saved->topk_ids, saved->topk_w, a.g_F, kd, a.g_feat, st);
+            if (e != cudaSuccess) return e;
+            a.kd_saved = kd;
+        }
     }
     const int ch = (f.dim % 32 == 0) ? 32 : 16;
     const int K = fp.top_k;

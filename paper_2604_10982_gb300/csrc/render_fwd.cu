@@ -34,6 +34,7 @@ struct FwdArgs {
     void *F;
     int F_bf16;
     int32_t *topk_ids;
+    float *topk_w;
     DevStatus *status;
 };
 
@@ -156,6 +157,12 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
             for (int s = 0; s < KMAX; ++s)
                 if (s < K) dst[s] = sid[s];
         }
+        if (a.topk_w) {
+            float *dst = a.topk_w + pix * K;
+#pragma unroll
+            for (int s = 0; s < KMAX; ++s)
+                if (s < K) dst[s] = sid[s] >= 0 ? top.w[s] : 0.0f;
+        }
         if (a.F && a.feat) {
             // 16 channels per chunk keeps the gather's registers low (one
             // 32-byte BF16 row slice = two 16-byte loads per selected surfel)
@@ -217,6 +224,7 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
     a.F = out.F;
     a.F_bf16 = out.F_dtype == PSI_BF16;
     a.topk_ids = out.topk_ids;
+    a.topk_w = out.topk_w;
     a.status = status;
     const int K = fp.top_k;
     const int ch = (f.dim % 32 == 0) ? 32 : 16;

@@ -114,6 +114,7 @@ class Renderer:
         self.F = torch.empty(self.n_pix, D, dtype=fdt, device=self.dev) if D else None
         K = int(opts.top_k)
         self.topk_ids = torch.empty(self.n_pix, K, dtype=torch.int32, device=self.dev) if (want_topk_ids and K) else None
+        self.topk_w = torch.empty(self.n_pix, K, dtype=torch.float32, device=self.dev) if (want_topk_ids and K) else None
 
     def set_cameras(self, cams):
         """Switch to other cameras with the same view count and image sizes."""
@@ -166,23 +167,24 @@ class Renderer:
         feats = scene.features_struct()
         out = psi.PsiFwdOut(psi._ptr(self.rgb), psi._ptr(self.T), psi._ptr(self.n_last),
                             psi._ptr(self.F) if (want_F and self.F is not None) else None, int(self.F_dtype),
-                            psi._ptr(self.topk_ids))
+                            psi._ptr(self.topk_ids), psi._ptr(self.topk_w))
         psi.psi_render_fwd(self.ctx, feats, self.records, self.vals, self.ranges, self.cams, self.V, self.n, self.opts,
                            out, stream)
 
     def saved_state(self):
-        """The forward outputs the adjoint reuses (None if the Top-K ids are not kept)."""
+        """The forward outputs the adjoint reuses (None if the Top-K set is not kept)."""
         if int(self.opts.top_k) > 0 and self.topk_ids is None:
             return None
         return psi.PsiFwdOut(psi._ptr(self.rgb), psi._ptr(self.T), psi._ptr(self.n_last), None, int(self.F_dtype),
-                             psi._ptr(self.topk_ids))
+                             psi._ptr(self.topk_ids), psi._ptr(self.topk_w))
 
     # a5
     def backward(self, scene: DeviceScene, g_rgb, g_F=None, g_T=None, grads=None, stream=None, recompute=False):
         """Gradients (float32, [N, ...]) of L = <g_rgb, rgb> + <g_F, F> + <g_T, T>
         for the frame last rendered by this renderer. The adjoint reuses that
-        frame's T, n_last and Top-K ids unless ``recompute`` is set (or the ids
-        were not kept), in which case it recomputes them from the lists."""
+        frame's T, n_last and Top-K ids and weights unless ``recompute`` is set
+        (or the set was not kept), in which case it recomputes them from the
+        lists."""
         dev = self.dev
         n, D = self.n, scene.D
         if grads is None:
@@ -191,7 +193,8 @@ class Renderer:
                          opacity=torch.zeros(n, device=dev), rgb=torch.zeros(n, 3, device=dev),
                          feat=torch.zeros(n, D, device=dev) if D else None)
         if not hasattr(self, "ws_bwd"):
-            self.ws_bwd = torch.empty(psi.render_bwd_workspace_size(self.V * self.n), dtype=torch.uint8, device=dev)
+            self.ws_bwd = torch.empty(psi.render_bwd_workspace_size(self.V * self.n, self.n_pix, int(self.opts.top_k)),
+                                      dtype=torch.uint8, device=dev)
         gs = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
         psi.psi_render_bwd(self.ctx, scene.surfels_struct(), scene.features_struct(), self.records, self.vals,
                            self.ranges, self.cams, self.V, self.opts, g_rgb.contiguous(),

@@ -47,7 +47,8 @@ class PsiRenderOpts(ctypes.Structure):
 
 
 class PsiFwdOut(ctypes.Structure):
-    _fields_ = [("rgb", _P), ("T", _P), ("n_last", _P), ("F", _P), ("F_dtype", _i32), ("topk_ids", _P)]
+    _fields_ = [("rgb", _P), ("T", _P), ("n_last", _P), ("F", _P), ("F_dtype", _i32), ("topk_ids", _P),
+                ("topk_w", _P)]
 
 
 class PsiGrads(ctypes.Structure):
@@ -79,8 +80,9 @@ def lib():
         L.psi_default_opts.argtypes = [ctypes.POINTER(PsiRenderOpts)]
         L.psi_default_opts.restype = None
         L.psi_view_layout.argtypes = [ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P]
-        for f in ("psi_intersect_workspace_size", "psi_sort_workspace_size", "psi_render_bwd_workspace_size"):
+        for f in ("psi_intersect_workspace_size", "psi_sort_workspace_size"):
             getattr(L, f).argtypes = [_i64, ctypes.POINTER(sz)]
+        L.psi_render_bwd_workspace_size.argtypes = [_i64, _i64, ctypes.c_int, ctypes.POINTER(sz)]
         L.psi_project_surfels.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiCamera), ctypes.c_int,
                                           ctypes.POINTER(PsiRenderOpts), _P, _P, _P, _P]
         L.psi_intersect_tiles.argtypes = [_P, ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts),
@@ -198,8 +200,12 @@ def sort_workspace_size(capacity):
     return _ws("psi_sort_workspace_size", capacity)
 
 
-def render_bwd_workspace_size(n_records):
-    return _ws("psi_render_bwd_workspace_size", n_records)
+def render_bwd_workspace_size(n_records, n_pix=0, top_k=0):
+    b = ctypes.c_size_t(0)
+    rc = lib().psi_render_bwd_workspace_size(int(n_records), int(n_pix), int(top_k), ctypes.byref(b))
+    if rc != PSI_OK:
+        raise PsiError(rc, "psi_render_bwd_workspace_size")
+    return int(b.value)
 
 
 def surfels_struct(mu, tu, tv, scale, opacity, rgb) -> PsiSurfels:
@@ -251,8 +257,8 @@ def psi_render_fwd(ctx, feats, records, vals, tile_ranges, cams_arr, n_views, n_
 
 def psi_render_bwd(ctx, s, feats, records, vals, tile_ranges, cams_arr, n_views, opts, g_rgb, g_F, g_T,
                    saved, grads: PsiGrads, workspace, stream=None):
-    """saved: a PsiFwdOut holding the forward's T, n_last (and topk_ids when
-    top_k > 0) of this frame, or None to recompute them."""
+    """saved: a PsiFwdOut holding the forward's T, n_last (and topk_ids,
+    topk_w when top_k > 0) of this frame, or None to recompute them."""
     ctx.check(lib().psi_render_bwd(ctx.handle, ctypes.byref(s), ctypes.byref(feats), _ptr(records), _ptr(vals),
                                    _ptr(tile_ranges), cams_arr, n_views, ctypes.byref(opts), _ptr(g_rgb), _ptr(g_F),
                                    _ptr(g_T), None if saved is None else ctypes.byref(saved), ctypes.byref(grads),

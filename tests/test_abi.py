@@ -35,6 +35,8 @@ def test_workspace_sizes(lib):
     assert psi.intersect_workspace_size(0) > 0
     assert psi.sort_workspace_size(10_000) >= 10_000 * 12
     assert psi.render_bwd_workspace_size(1000) >= 1000 * 4
+    assert psi.render_bwd_workspace_size(1000, 5000, 8) >= psi.render_bwd_workspace_size(1000) + 5000 * 8 * 4
+    assert lib.psi_render_bwd_workspace_size(10, -1, 8, ctypes.byref(ctypes.c_size_t(0))) == psi.PSI_ERR_INVALID_ARG
     b = ctypes.c_size_t(0)
     assert lib.psi_sort_workspace_size(-1, ctypes.byref(b)) == psi.PSI_ERR_INVALID_ARG
 

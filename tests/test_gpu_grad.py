@@ -160,7 +160,7 @@ def test_grad_long_lists_early_exit(ctx):
 
 
 def test_saved_state_needs_topk_ids(ctx):
-    """Saved forward state without Top-K ids (K > 0) is refused."""
+    """Saved forward state without the Top-K ids and weights (K > 0) is refused."""
     from paper_2604_10982_gb300 import pipeline as pl, psi
     w = sg.crop_scene(n=200, d=16, size=32)
     o = orc.Opts(mode=orc.EXACT, top_k=8)
@@ -168,11 +168,11 @@ def test_saved_state_needs_topk_ids(ctx):
     r = pl.make_renderer(ctx, scene, w.cameras, opts_of(o), D=16, want_topk_ids=False)
     r.frame(scene)
     assert r.saved_state() is None
-    saved = psi.PsiFwdOut(psi._ptr(r.rgb), psi._ptr(r.T), psi._ptr(r.n_last), None, psi.F32, None)
+    saved = psi.PsiFwdOut(psi._ptr(r.rgb), psi._ptr(r.T), psi._ptr(r.n_last), None, psi.F32, None, None)
     gC = torch.zeros(3, r.n_pix, device="cuda")
     grads = {k: torch.zeros(r.n, 3, device="cuda") for k in ("mu", "tu", "tv", "rgb")}
     gs = psi.PsiGrads(*(psi._ptr(grads.get(k)) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
-    ws = torch.empty(psi.render_bwd_workspace_size(r.n), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(psi.render_bwd_workspace_size(r.n, r.n_pix, 8), dtype=torch.uint8, device="cuda")
     with pytest.raises(psi.PsiError) as e:
         psi.psi_render_bwd(ctx, scene.surfels_struct(), scene.features_struct(), r.records, r.vals, r.ranges,
                            r.cams, r.V, r.opts, gC, None, None, saved, gs, ws)
