@@ -309,15 +309,21 @@ def run_psi(args):
         def dec():
             psi.psi_decode_queries(ctx, r.F, r.n_pix, D, Qd, nq, r.T, ids)
 
-        def bwd():
+        def zero():
             for g in grads.values():
                 g.zero_()
+
+        def bwd():
             r.set_cameras([cams[f]])
             r.backward(scene, gC, gF, gT, grads=grads)
 
-        return [proj, isect, srt, rend, dec, bwd]
+        return [proj, isect, srt, rend, dec, zero, bwd]
 
-    names = ["project", "intersect", "sort", "render_fwd", "decode", "render_bwd"]
+    names = ["project", "intersect", "sort", "render_fwd", "decode", "zero_grads", "render_bwd"]
+    # the adjoint call launches three kernels (features, list walk, chain); it
+    # runs eagerly so that the library can bracket its kernels with the
+    # per-step timing events below (a graph replay cannot record them)
+    EAGER = {"render_bwd"}
     # warm every code path once (lazy buffers, function attributes), then capture
     for fn in stage_fns(0):
         fn()
@@ -329,7 +335,10 @@ def run_psi(args):
         graphs = []
         for f in range(len(cams)):
             gs = []
-            for fn in stage_fns(f):
+            for name, fn in zip(names, stage_fns(f)):
+                if name in EAGER:
+                    gs.append(None)
+                    continue
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=cap_stream, capture_error_mode="relaxed"):
                     fn()
@@ -337,10 +346,16 @@ def run_psi(args):
             graphs.append(gs)
         torch.cuda.synchronize()
 
-    def run_frame(f, evs=None):
-        stages = graphs[f] if use_graph else stage_fns(f)
-        for i, st in enumerate(stages):
-            st.replay() if use_graph else st()
+    def run_frame(f, evs=None, kev=None):
+        fns = stage_fns(f)
+        for i in range(len(names)):
+            if kev is not None and names[i] == "render_bwd":
+                psi.psi_ctx_time_kernel(ctx, psi.KERNEL_BWD_FEAT, kev[0], kev[1])
+                psi.psi_ctx_time_kernel(ctx, psi.KERNEL_BWD_WALK, kev[2], kev[3])
+            if use_graph and graphs[f][i] is not None:
+                graphs[f][i].replay()
+            else:
+                fns[i]()
             if evs is not None:
                 evs[i + 1].record()
 
@@ -356,6 +371,11 @@ def run_psi(args):
 
     # ---- timed region
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    # per-step events around the adjoint's feature kernel and list walk
+    kevs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for kv in kevs:
+        for e in kv:
+            e.record()  # creates the CUDA event the library records into
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -366,7 +386,7 @@ def run_psi(args):
     t_start.record()
     for k in range(args.steps):
         evs[k][0].record()
-        run_frame(fidx(k), evs[k])
+        run_frame(fidx(k), evs[k], kevs[k])
     t_end.record()
     torch.cuda.synchronize()
     if world > 1:
@@ -377,55 +397,58 @@ def run_psi(args):
     st, req = ctx.status_fetch()
     assert st == 0, f"device status {st}"
     total_ms = max_over_ranks(total_ms, world, dev)
+    kern = np.array([[kevs[k][0].elapsed_time(kevs[k][1]), kevs[k][2].elapsed_time(kevs[k][3])]
+                     for k in range(args.steps)])
     frame_ms = stage.sum(1)
     fwd_ms = stage[:, :5].sum(1)
     value = job_throughput(args.steps, world, total_ms)
 
     # ---- per-frame statistics (outside the timed region)
-    pairs, nlast_sum, nonempty = [], [], []
+    pairs, nlast_sum, nonempty, uniq_sel = [], [], [], []
     for f in sorted(set(fidx(k) for k in range(args.steps))):
         run_frame(f)
         torch.cuda.synchronize()
         pairs.append(int(r.num_pairs.item()))
         nlast_sum.append(float(r.n_last.to(torch.float64).sum().item()))
         nonempty.append(int(((1.0 - r.T) >= 1e-4).sum().item()))
+        ids_sel = r.topk_ids.reshape(-1)
+        uniq_sel.append(int(torch.unique(ids_sel[ids_sel >= 0]).numel()))
     n_tiles = r.n_tiles
 
     # ---- roofline of the dominant kernel
     mean_stage = stage.mean(0)
-    dom = int(np.argmax(mean_stage))
+    kernel_ms = {"render_fwd_kernel": float(mean_stage[names.index("render_fwd")]),
+                 "decode_kernel": float(mean_stage[names.index("decode")]),
+                 "feat_bwd_kernel": float(kern[:, 0].mean()),
+                 "render_bwd_kernel": float(kern[:, 1].mean())}
+    dom = max(kernel_ms, key=kernel_ms.get)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
-    launch_s = mean_stage[dom] / 1000.0
-    kname = names[dom]
-    if kname == "render_fwd":
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    launch_s = kernel_ms[dom] / 1000.0
+    if dom == "render_fwd_kernel":
         flop = 20.0 * np.mean(nlast_sum) + 2.0 * K * D * np.mean(nonempty)
-        roof = {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": flop / launch_s / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s",
+        roof = {"bound": "alu", "achieved": flop / launch_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                 "work": "20 FP32 flop per (pixel, list entry up to its last composited surfel) + 2KD per pixel"}
-    elif kname == "render_bwd":
-        flop = 90.0 * np.mean(nlast_sum) + 4.0 * K * D * np.mean(nonempty)
-        roof = {"kernel": "render_bwd_kernel", "bound": "alu", "achieved": flop / launch_s / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s",
-                "work": "90 FP32 flop per (pixel, list entry up to its last composited surfel) + 4KD per pixel"}
-    elif kname == "sort":
-        key_bits = r.key_bits
-        passes = max(2, (key_bits + 7) // 8)
-        passes += passes & 1
-        byts = passes * np.mean(pairs) * 32.0
-        roof = {"kernel": "radix sort passes", "bound": "hbm", "achieved": byts / launch_s / 1e9,
-                "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
-                "work": "32 B per pair per pass (key+value read twice, written once)"}
+    elif dom == "render_bwd_kernel":
+        flop = 90.0 * np.mean(nlast_sum)
+        roof = {"bound": "alu", "achieved": flop / launch_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "work": "90 FP32 flop per (pixel, list entry up to its last composited surfel)"}
+    elif dom == "feat_bwd_kernel":
+        byts = r.n_pix * (4.0 * D + 12.0 * K) + np.mean(uniq_sel) * (2.0 * D + 8.0 * D)
+        roof = {"bound": "hbm", "achieved": byts / launch_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "work": "per pixel gF row + K ids, weights, dots; per selected surfel its BF16 row and dL/df row read+write"}
     else:
-        byts = 64.0 * args.surfels
-        roof = {"kernel": kname, "bound": "hbm", "achieved": byts / launch_s / 1e9,
-                "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "work": "64 B per surfel"}
+        byts = r.n_pix * (2.0 * D + 8.0)
+        roof = {"bound": "hbm", "achieved": byts / launch_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "work": "per pixel its BF16 feature row, T and id"}
+    roof = {"kernel": dom, **roof}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["peak_source"] = ("measured HBM (MEASURED_PEAKS.json)" if roof["bound"] == "hbm" else
+    roof["peak_source"] = ("measured HBM copy bandwidth (MEASURED_PEAKS.json)" if roof["bound"] == "hbm" else
                            f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz")
-    roof["traffic"] = roofline_traffic(roof["kernel"])
-    roof["launch_ms"] = float(mean_stage[dom])
+    roof["traffic"] = roofline_traffic(dom)
+    roof["launch_ms"] = kernel_ms[dom]
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -509,7 +532,7 @@ def run_psi(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, use_graph),
         "fwd_frames_per_s": float(1000.0 / fwd_ms.mean()), "fwd_bwd_ms": float(frame_ms.mean()),
         "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
-        "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)},
+        "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)}, "kernel_ms": kernel_ms,
         "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
         "plain_fp32": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),

@@ -152,6 +152,20 @@ const char *psi_last_error(const psi_ctx *ctx);
  * that gave up (1 render, 2/3 adjoint passes, 4-6 decode, 7 drain); then
  * clears the word. */
 int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *detail);
+
+/* Kernels psi_ctx_time_kernel can bracket: those that share an entry point
+ * with other kernels (psi_render_bwd launches the feature kernel, the list
+ * walk and the chain kernel). */
+enum psi_kernel_id { PSI_KERNEL_BWD_FEAT = 1, PSI_KERNEL_BWD_WALK = 2 };
+/* Kernel timing, a tracing aid with no counterpart in the paper: arm a
+ * one-shot pair of CUDA events (cudaEvent_t created with timing enabled,
+ * passed as void*) that the next launch of `kernel` through this context
+ * records on the call's stream, ev_begin right before the launch and ev_end
+ * right after it; the pair is then disarmed (NULL, NULL disarms it early). The
+ * caller reads cudaEventElapsedTime once the stream has run. Meant for eager
+ * launches: inside a stream capture a plain event record adds no graph node.
+ * PSI_ERR_INVALID_ARG for an unknown kernel or only one event. */
+int psi_ctx_time_kernel(psi_ctx *ctx, int kernel, void *ev_begin, void *ev_end);
 /* Fill *o with the defaults: EXACT, K=0, chi2=9, z_near=0.2, no opacity
  * radius, 16x16 tiles, t_eps=1e-4. */
 void psi_default_opts(psi_render_opts *o);

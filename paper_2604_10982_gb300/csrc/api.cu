@@ -10,6 +10,8 @@ struct psi_ctx {
     int device;
     psi::DevStatus *status;
     char err[512];
+    // armed kernel-timing events per psi_kernel_id: [id][0] begin, [id][1] end
+    cudaEvent_t time_ev[3][2];
 };
 
 namespace {
@@ -116,7 +118,7 @@ int psi_ctx_create(psi_ctx **out, int device)
     *out = nullptr;
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return PSI_ERR_INVALID_ARG;
-    psi_ctx *c = new (std::nothrow) psi_ctx;
+    psi_ctx *c = new (std::nothrow) psi_ctx(); // value-initialised: no timing events armed
     if (!c) return PSI_ERR_CUDA;
     c->device = device;
     c->status = nullptr;
@@ -143,6 +145,18 @@ void psi_ctx_destroy(psi_ctx *ctx)
 }
 
 const char *psi_last_error(const psi_ctx *ctx) { return ctx ? ctx->err : "NULL context"; }
+
+int psi_ctx_time_kernel(psi_ctx *ctx, int kernel, void *ev_begin, void *ev_end)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (kernel != PSI_KERNEL_BWD_FEAT && kernel != PSI_KERNEL_BWD_WALK)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "unknown kernel id %d", kernel);
+    if ((ev_begin == nullptr) != (ev_end == nullptr))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "give both events or neither");
+    ctx->time_ev[kernel][0] = static_cast<cudaEvent_t>(ev_begin);
+    ctx->time_ev[kernel][1] = static_cast<cudaEvent_t>(ev_end);
+    return PSI_OK;
+}
 
 int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *detail)
 {
@@ -356,7 +370,8 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
     psi::fill_frame_params(fp, cams, n_views, o, s->n);
     cudaError_t e = psi::launch_render_bwd(fp, *s, fv, static_cast<const float4 *>(records), vals, tile_ranges, g_rgb,
                                            g_F, g_T, saved, *grads, workspace, ctx->status,
-                                           reinterpret_cast<cudaStream_t>(stream));
+                                           reinterpret_cast<cudaStream_t>(stream), ctx->time_ev);
+    for (int k = PSI_KERNEL_BWD_FEAT; k <= PSI_KERNEL_BWD_WALK; ++k) ctx->time_ev[k][0] = ctx->time_ev[k][1] = nullptr;
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_render_bwd", e);
 }
 

@@ -196,7 +196,7 @@ cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int3
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
-                              DevStatus *status, cudaStream_t st);
+                              DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2]);
 
 cudaError_t launch_decode(const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T, int32_t *ids,
                           void *logits, DevStatus *status, cudaStream_t st, const char **why);

@@ -566,8 +566,12 @@ size_t render_bwd_workspace_bytes(int64_t n_records, int64_t n_pix, int top_k)
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
-                              DevStatus *status, cudaStream_t st)
+                              DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2])
 {
+    // optional timing events around one kernel (see psi_ctx_time_kernel)
+    auto mark = [&](int kernel, int which) {
+        if (time_ev && time_ev[kernel][which]) cudaEventRecord(time_ev[kernel][which], st);
+    };
     const int64_t R = fp.n * fp.n_views;
     cudaError_t e = cudaMemsetAsync(ws, 0, moments_bytes(R), st);
     if (e != cudaSuccess || R == 0 || fp.n_tiles_total == 0) return e;
@@ -592,13 +596,16 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
         if (fp.top_k > 0 && a.g_F) {
             // feature terms from the saved selection: kd for the walk, dL/df
             float *kd = reinterpret_cast<float *>(static_cast<char *>(ws) + moments_bytes(R));
+            mark(PSI_KERNEL_BWD_FEAT, 0);
             e = launch_feat_bwd(fp, f, saved->topk_ids, saved->topk_w, a.g_F, kd, a.g_feat, st);
             if (e != cudaSuccess) return e;
+            mark(PSI_KERNEL_BWD_FEAT, 1);
             a.kd_saved = kd;
         }
     }
     const int ch = (f.dim % 32 == 0) ? 32 : 16;
     const int K = fp.top_k;
+    mark(PSI_KERNEL_BWD_WALK, 0);
     if (K == 0)
         e = launch_k<0>(fp, f, a, ch, st);
     else if (K <= 8)
@@ -608,6 +615,7 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
     else
         e = launch_k<32>(fp, f, a, ch, st);
     if (e != cudaSuccess) return e;
+    mark(PSI_KERNEL_BWD_WALK, 1);
     chain_kernel<<<static_cast<unsigned>((R + 255) / 256), 256, 0, st>>>(fp, s, static_cast<const float4 *>(ws), g);
     return cudaGetLastError();
 }

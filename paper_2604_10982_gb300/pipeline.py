@@ -138,7 +138,9 @@ class Renderer:
         ch = 32 if D % 32 == 0 else 16
         n += 1 if (K or not D) else max(1, D // ch)        # render (dense: one pass per channel chunk)
         n += 1 if with_decode else 0
-        n += 2 if with_bwd else 0                          # adjoint + chain
+        if with_bwd:
+            n += 2                                         # list walk + chain
+            n += 1 if (K and D and self.topk_ids is not None) else 0  # feature terms from the saved set
         return n
 
     def set_capacity(self, capacity: int):

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libpsi.so")
 PSI_OK, PSI_ERR_INVALID_ARG, PSI_ERR_CUDA, PSI_ERR_CAPACITY, PSI_ERR_TIMEOUT, PSI_ERR_UNSUPPORTED = range(6)
 SPHERE, AABB, EXACT = 0, 1, 2
 F32, BF16, FP8_E4M3 = 0, 1, 2
+KERNEL_BWD_FEAT, KERNEL_BWD_WALK = 1, 2  # enum psi_kernel_id
 MAX_VIEWS = 64
 RECORD_BYTES = 80
 BIN_RECORD_BYTES = 32
@@ -94,6 +95,7 @@ def lib():
         L.psi_render_bwd.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures), _P, _P, _P,
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
+        L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
         L.psi_decode_queries.argtypes = [_P, _P, _i64, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]
         _lib = L
     return _lib
@@ -264,6 +266,15 @@ def psi_render_bwd(ctx, s, feats, records, vals, tile_ranges, cams_arr, n_views,
                                    _ptr(g_T), None if saved is None else ctypes.byref(saved), ctypes.byref(grads),
                                    _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), _stream(stream)), "psi_render_bwd")
+
+
+def psi_ctx_time_kernel(ctx, kernel, ev_begin, ev_end):
+    """Arm a one-shot pair of timing events (torch.cuda.Event(enable_timing=True),
+    already recorded once so that the CUDA event exists) around the next
+    eager launch of `kernel` (KERNEL_BWD_FEAT / KERNEL_BWD_WALK)."""
+    b = None if ev_begin is None else ctypes.c_void_p(ev_begin.cuda_event)
+    e = None if ev_end is None else ctypes.c_void_p(ev_end.cuda_event)
+    ctx.check(lib().psi_ctx_time_kernel(ctx.handle, int(kernel), b, e), "psi_ctx_time_kernel")
 
 
 def psi_decode_queries(ctx, F, n_pix, D, Q, n_q, T, ids, logits=None, stream=None):

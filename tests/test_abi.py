@@ -54,3 +54,8 @@ def test_ctx_create_without_device_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.psi_ctx_create(ctypes.byref(h), 0) == psi.PSI_ERR_INVALID_ARG
     assert not h.value
+
+
+def test_time_kernel_rejects_bad_arguments(lib):
+    # no context: refused before anything touches a device
+    assert lib.psi_ctx_time_kernel(None, psi.KERNEL_BWD_WALK, None, None) == psi.PSI_ERR_INVALID_ARG

@@ -181,3 +181,34 @@ def test_saved_state_needs_topk_ids(ctx):
     g = r.backward(scene, gC)
     torch.cuda.synchronize()
     assert ctx.status_fetch()[0] == 0
+
+
+def test_kernel_timing_events(ctx):
+    """psi_ctx_time_kernel brackets the adjoint's feature kernel and list walk
+    of the next eager call, once."""
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    w = sg.crop_scene(n=300, d=16, size=48)
+    o = orc.Opts(mode=orc.EXACT, top_k=8)
+    scene = pl.DeviceScene(w.surfels, w.features)
+    r = pl.make_renderer(ctx, scene, w.cameras, opts_of(o), D=16)
+    r.frame(scene)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev:
+        e.record()
+    torch.cuda.synchronize()
+    psi.psi_ctx_time_kernel(ctx, psi.KERNEL_BWD_FEAT, ev[0], ev[1])
+    psi.psi_ctx_time_kernel(ctx, psi.KERNEL_BWD_WALK, ev[2], ev[3])
+    gC = torch.ones(3, r.n_pix, device="cuda")
+    gF = torch.ones(r.n_pix, 16, device="cuda")
+    r.backward(scene, gC, gF)
+    torch.cuda.synchronize()
+    t_feat, t_walk = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    assert t_feat > 0 and t_walk > 0
+    # disarmed after one call: the events keep their timestamps
+    r.backward(scene, gC, gF)
+    torch.cuda.synchronize()
+    assert ev[2].elapsed_time(ev[3]) == t_walk
+    with pytest.raises(psi.PsiError):
+        psi.psi_ctx_time_kernel(ctx, 7, ev[0], ev[1])
+    with pytest.raises(psi.PsiError):
+        psi.psi_ctx_time_kernel(ctx, psi.KERNEL_BWD_WALK, ev[0], None)
