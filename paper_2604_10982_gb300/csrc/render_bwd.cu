@@ -13,8 +13,8 @@
 // clamped): dL/do = dL/dalpha G, and (u, v) enter via a = dL/dalpha * alpha:
 // with (u, v, 1) ~ M^-1 p the gradient of M is M^-T W, W = sum a (u, v,
 // -d^2)(u, v, 1)^T, so each (pixel, record) adds 7 moments of (u, v).
-// Per-surfel sums are reduced across the warp (a transposing butterfly: 16
-// values in 16 shuffles) and added with one atomic per value per warp; the
+// Per-surfel sums are reduced across the warp (a transposing butterfly: 11
+// values in 13 shuffles) and added with one atomic per value per warp; the
 // feature gradient is accumulated warp-cooperatively across channels.
 // Both passes stream the list through the same producer-warp pipeline as the
 // forward kernel (raster.cuh): pass A front to back until every pixel is
@@ -53,33 +53,36 @@ struct BwdArgs {
     const float *kd_saved;     // [P_total, K] <gF, f_j> of the saved set (feat_bwd.cu), or NULL
 };
 
-// Sum 16 per-lane values over the warp: afterwards lane l (and l^1) holds the
-// total of value index 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l).
-__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
+// Sum 12 per-lane values over the warp (a transposing butterfly, 13
+// shuffles): afterwards lane l (and l ^ 1) holds the total of value index
+// 6 b4 + 3 b3 + g with g = 2 b2 + b1 (b_k = bit k of l); lanes with g = 3 hold
+// a padding slot.
+__device__ __forceinline__ float warp_transpose_sum12(float v[12], int lane)
 {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 6; ++k) { // 12 -> 6: halves [0, 6) / [6, 12)
         const bool hi = lane & 16;
-        const float send = hi ? v[k] : v[k + 8];
-        const float keep = hi ? v[k + 8] : v[k];
+        const float send = hi ? v[k] : v[k + 6];
+        const float keep = hi ? v[k + 6] : v[k];
         v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) { // 6 -> 3
         const bool hi = lane & 8;
-        const float send = hi ? v[k] : v[k + 4];
-        const float keep = hi ? v[k + 4] : v[k];
+        const float send = hi ? v[k] : v[k + 3];
+        const float keep = hi ? v[k + 3] : v[k];
         v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
+    v[3] = 0.0f; // 3 -> 4 slots (one padding)
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2; ++k) { // 4 -> 2
         const bool hi = lane & 4;
         const float send = hi ? v[k] : v[k + 2];
         const float keep = hi ? v[k + 2] : v[k];
         v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
     {
-        const bool hi = lane & 2;
+        const bool hi = lane & 2; // 2 -> 1
         const float send = hi ? v[0] : v[1];
         const float keep = hi ? v[1] : v[0];
         v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
@@ -87,6 +90,10 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
     return v[0];
 }
+
+// Up to this many contributing lanes add their values with their own atomics
+// instead of reducing over the warp first.
+constexpr int kDirectLanes = 1;
 
 // SAVED: T_final, last and the Top-K ids come from the forward's outputs;
 // otherwise pass A recomputes them. With SAVED and K > 0 the feature terms
@@ -295,9 +302,9 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                     if (!amask) continue;
                     const uint32_t rid = P.val[st][j];
                     const int64_t sid = static_cast<int64_t>(rid) - surf0;
-                    float vals[16];
+                    float vals[12];
 #pragma unroll
-                    for (int k2 = 0; k2 < 16; ++k2) vals[k2] = 0.0f;
+                    for (int k2 = 0; k2 < 12; ++k2) vals[k2] = 0.0f;
                     float w = 0.0f;
                     bool sel = false;
                     if (act) {
@@ -349,8 +356,8 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                             vals[10] = aa * d2 * vv;
                         }
                     }
-                    if (__popc(amask) == 1) {
-                        // a single contributing lane adds its values directly
+                    if (__popc(amask) <= kDirectLanes) {
+                        // few contributing lanes add their values directly
                         if (act) {
 #pragma unroll
                             for (int k2 = 0; k2 < 11; ++k2) {
@@ -363,9 +370,10 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                             }
                         }
                     } else {
-                        const float tot = warp_transpose_sum16(vals, lane);
-                        const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-                        if ((lane & 1) == 0 && idx < 11 && tot != 0.0f) {
+                        const float tot = warp_transpose_sum12(vals, lane);
+                        const int g = ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                        const int idx = ((lane >> 4) & 1) * 6 + ((lane >> 3) & 1) * 3 + g;
+                        if ((lane & 1) == 0 && g < 3 && tot != 0.0f) {
                             if (idx < 3) {
                                 if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
                             } else {
