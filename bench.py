@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--ablation-frames", type=int, default=6, help="frames per Table-3 row (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -510,6 +511,41 @@ def run_psi(args):
                  "form": "SPHERE tiles, dense FP32 features (no Top-K), single view per launch, no graph, no decode"}
         del scene32, rp
 
+    # ---- the paper's Table 3 rows on this GPU: tile test x feature selection,
+    # same BF16 features, forward of one frame (project, intersect, sort,
+    # render), eager launches, median over frames
+    ablation = None
+    if args.ablation_frames > 0:
+        rows = [("baseline", psi.SPHERE, 0), ("precise_tile_aabb", psi.AABB, 0), ("precise_tile_exact", psi.EXACT, 0),
+                ("topk", psi.SPHERE, K), ("full_aabb", psi.AABB, K), ("full_exact", psi.EXACT, K)]
+        ablation = {}
+        for name, mode, kk in rows:
+            ao = psi.default_opts(mode=mode, top_k=kk, opacity_radius=1 if mode == psi.EXACT else 0)
+            ra = pl.Renderer(ctx, scene.n, [cams[0]], ao, 1024, D=D, F_dtype=psi.BF16, device=dev)
+            nf = min(args.ablation_frames, len(cams))
+            need = 0
+            for k in range(nf):
+                ra.set_cameras([cams[fidx(k)]])
+                need = max(need, ra.required_pairs(scene))
+            ra.set_capacity(int(need * 1.15) + 1024)
+            ts, prs = [], []
+            for k in range(nf + 1):
+                ra.set_cameras([cams[fidx(k)]])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ra.frame(scene)
+                e1.record()
+                torch.cuda.synchronize()
+                if k > 0:
+                    ts.append(e0.elapsed_time(e1))
+                    prs.append(int(ra.num_pairs.item()))
+            ablation[name] = {"fwd_ms": float(np.median(ts)), "pairs_per_frame": float(np.mean(prs)),
+                              "pairs_per_tile": float(np.mean(prs)) / ra.n_tiles,
+                              "tiles": {0: "sphere", 1: "aabb", 2: "exact+opacity-radius"}[mode], "top_k": kk}
+            del ra
+        ablation["form"] = ("forward (project+intersect+sort+render) of one 1920x1080 frame, BF16 features, "
+                            "K=0 dense / K=8 Top-K, median over %d frames" % min(args.ablation_frames, len(cams)))
+
     # ---- CPU oracle on a bounded sample (rank 0)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -534,7 +570,7 @@ def run_psi(args):
         "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)}, "kernel_ms": kernel_ms,
         "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
-        "plain_fp32": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "plain_fp32": plain, "ablation": ablation, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),
         "clocks": clk, "paper_context": PAPER_CONTEXT, "setup_s": setup_s,
     }

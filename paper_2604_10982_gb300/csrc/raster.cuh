@@ -295,26 +295,37 @@ __device__ __forceinline__ bool pipe_produce(Pipe &P, const uint32_t *__restrict
     return ok;
 }
 
-// Pixel warp: wait until batch b is ready. Returns false if the walk is over
-// for everyone (no pixel warp alive, or an abort).
+// Pixel warp (all 32 lanes): wait until batch b is ready. Returns false if
+// the walk is over for everyone (no pixel warp alive, or an abort). The
+// answer is the same in every lane of the warp: once one lane has seen the
+// batch ready it stays ready (the stage cannot be refilled before this warp
+// releases it), so the others wait for it too.
 __device__ __forceinline__ bool pipe_wait_ready(Pipe &P, int b, DevStatus *st, int site)
 {
     const int s = b % kPS;
     const uint32_t par = (b / kPS) & 1;
-    if (mbar_try_wait(&P.ready[s], par)) return true;
-    const unsigned long long t0 = global_ns();
-    while (true) {
-        if (mbar_try_wait(&P.ready[s], par)) return true;
-        if (vload(P.abort) || vload(P.alive) == 0) return false;
-        if (global_ns() - t0 > kWaitLimitNs) {
-            if (st) {
-                atomicCAS(&st->wait_site, 0, site);
-                raise_status(st, PSI_ERR_TIMEOUT);
+    bool ready = mbar_try_wait(&P.ready[s], par);
+    if (!ready) {
+        const unsigned long long t0 = global_ns();
+        while (true) {
+            if (mbar_try_wait(&P.ready[s], par)) {
+                ready = true;
+                break;
             }
-            atomicExch(&P.abort, 1);
-            return false;
+            if (vload(P.abort) || vload(P.alive) == 0) break;
+            if (global_ns() - t0 > kWaitLimitNs) {
+                if (st) {
+                    atomicCAS(&st->wait_site, 0, site);
+                    raise_status(st, PSI_ERR_TIMEOUT);
+                }
+                atomicExch(&P.abort, 1);
+                break;
+            }
         }
     }
+    if (!__any_sync(0xffffffffu, ready)) return false;
+    if (!ready) mbar_wait(&P.ready[s], par, st, site); // complete already: returns at once
+    return true;
 }
 
 // Pixel warp: done with batch b (one arrival per warp).

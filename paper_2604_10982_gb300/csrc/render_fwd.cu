@@ -201,7 +201,11 @@ template <int KMAX>
 cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FwdArgs &a, int ch, cudaStream_t st)
 {
     if (fp.n_tiles_total == 0) return cudaSuccess;
-    return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
+    // the channel chunk only shapes the dense (K = 0) accumulation
+    if constexpr (KMAX > 0)
+        return launch_kc<KMAX, 16>(fp, f, a, st);
+    else
+        return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
 }
 
 } // namespace
