@@ -23,6 +23,7 @@ struct FeatBwdArgs {
     const void *feat;
     const float *fscale;
     int D;
+    bool wide; // feature rows read 32 bytes at a time
     const int32_t *topk_ids; // [P_total, K]
     const float *topk_w;     // [P_total, K]
     const float *g_F;        // [P_total, D]
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
             for (int s = 0; s < KMAX; ++s) {
                 if (id[s] < 0) continue;
                 float f[16];
-                load_feat<DT, 16>(a.feat, id[s], a.D, c0, f);
+                load_feat<DT, 16>(a.feat, id[s], a.D, c0, f, a.wide);
                 float acc = kd[s];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) acc = __fmaf_rn(g[c], f[c], acc);
@@ -173,6 +174,7 @@ cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int3
     if (fp.n_tiles_total == 0 || fp.top_k <= 0 || !f.data || !g_F) return cudaSuccess;
     FeatBwdArgs a{};
     a.feat = f.data;
+    a.wide = feat_rows_wide(f.data, f.dim, f.dtype);
     a.fscale = f.scale;
     a.D = f.dim;
     a.topk_ids = topk_ids;

@@ -353,11 +353,54 @@ __device__ __forceinline__ void pipe_hit_words(const Pipe &P, int s, int cnt, in
 }
 
 // ------------------------------------------------------------ features
-// CH (16 or 32) channels [c0, c0+CH) of feature row i as float32, before the
-// per-channel scale. Rows are read with 16-byte vector loads.
-template <int DT, int CH>
-__device__ __forceinline__ void load_feat(const void *__restrict__ base, int64_t i, int D, int c0, float *f)
+// 32 bytes of read-only global memory (address 32-byte aligned).
+__device__ __forceinline__ void ldg32(const void *p, uint32_t w[8])
 {
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+        : "l"(p));
+}
+
+// Whether feature rows can be read 32 bytes at a time: the table starts on a
+// 32-byte boundary and every row is a whole number of 32-byte units.
+inline bool feat_rows_wide(const void *base, int D, int dtype)
+{
+    const int esize = dtype == PSI_F32 ? 4 : (dtype == PSI_BF16 ? 2 : 1);
+    return (reinterpret_cast<uintptr_t>(base) % 32 == 0) && ((D * esize) % 32 == 0);
+}
+
+// CH (16 or 32) channels [c0, c0+CH) of feature row i as float32, before the
+// per-channel scale. Rows are read with 16-byte vector loads, or 32-byte ones
+// when `wide` (see feat_rows_wide; c0 is a multiple of 16): a lane then
+// touches one whole 32-byte sector per load when the rows of a warp differ.
+template <int DT, int CH>
+__device__ __forceinline__ void load_feat(const void *__restrict__ base, int64_t i, int D, int c0, float *f,
+                                          bool wide = false)
+{
+    if (wide && DT != PSI_FP8_E4M3) {
+        const unsigned char *row = static_cast<const unsigned char *>(base) + (i * D + c0) * (DT == PSI_F32 ? 4 : 2);
+        if constexpr (DT == PSI_F32) {
+#pragma unroll
+            for (int k = 0; k < CH / 8; ++k) {
+                uint32_t w[8];
+                ldg32(row + 32 * k, w);
+#pragma unroll
+                for (int h = 0; h < 8; ++h) f[8 * k + h] = __uint_as_float(w[h]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < CH / 16; ++k) {
+                uint32_t w[8];
+                ldg32(row + 32 * k, w);
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    f[16 * k + 2 * h] = __uint_as_float(w[h] << 16);
+                    f[16 * k + 2 * h + 1] = __uint_as_float(w[h] & 0xFFFF0000u);
+                }
+            }
+        }
+        return;
+    }
     if constexpr (DT == PSI_F32) {
         const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(base) + i * D + c0);
 #pragma unroll

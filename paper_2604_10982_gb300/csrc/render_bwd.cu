@@ -39,6 +39,7 @@ struct BwdArgs {
     const void *feat;
     const float *fscale;
     int D;
+    bool wide; // feature rows read 32 bytes at a time
     const float *g_rgb; // [3][P_total]
     const float *g_F;   // [P_total, D] or NULL
     const float *g_T;   // [P_total] or NULL
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                 for (int s = 0; s < KMAX; ++s) {
                     if (kid[s] < 0) continue;
                     float f[16];
-                    load_feat<DT, 16>(a.feat, kid[s], a.D, c0, f);
+                    load_feat<DT, 16>(a.feat, kid[s], a.D, c0, f, a.wide);
                     float acc = kd[s];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) acc = __fmaf_rn(g[c], f[c], acc);
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                             sel = true;
                             for (int c0 = 0; c0 < a.D; c0 += CH) {
                                 float f[CH];
-                                load_feat<DT, CH>(a.feat, sid, a.D, c0, f);
+                                load_feat<DT, CH>(a.feat, sid, a.D, c0, f, a.wide);
 #pragma unroll
                                 for (int c = 0; c < CH; ++c) {
                                     const float sc = a.fscale ? __ldg(a.fscale + c0 + c) : 1.0f;
@@ -588,6 +589,7 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
     a.vals = vals;
     a.ranges = ranges;
     a.feat = f.data;
+    a.wide = f.data && feat_rows_wide(f.data, f.dim, f.dtype);
     a.fscale = f.scale;
     a.D = f.dim;
     a.g_rgb = g_rgb;

@@ -26,6 +26,7 @@ struct FwdArgs {
     const void *feat;
     const float *fscale;
     int D;
+    bool wide; // feature rows read 32 bytes at a time
     int c0;          // dense mode: first channel of this pass
     int write_rgb;   // dense mode: only the first pass writes rgb / T / ids
     float *rgb;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                     if constexpr (KMAX == 0) {
                         if (a.feat) {
                             float f[CH];
-                            load_feat<DT, CH>(a.feat, static_cast<int64_t>(P.val[st][j]) - surf0, a.D, a.c0, f);
+                            load_feat<DT, CH>(a.feat, static_cast<int64_t>(P.val[st][j]) - surf0, a.D, a.c0, f, a.wide);
 #pragma unroll
                             for (int c = 0; c < CH; ++c) facc[c] = __fmaf_rn(w, f[c], facc[c]);
                         }
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                 for (int s = 0; s < KMAX; ++s) {
                     if (sid[s] < 0) continue;
                     float f[CB];
-                    load_feat<DT, CB>(a.feat, sid[s], a.D, c0, f);
+                    load_feat<DT, CB>(a.feat, sid[s], a.D, c0, f, a.wide);
 #pragma unroll
                     for (int c = 0; c < CB; ++c) acc[c] = __fmaf_rn(top.w[s], f[c], acc[c]);
                 }
@@ -218,6 +219,7 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
     a.vals = vals;
     a.ranges = ranges;
     a.feat = f.data;
+    a.wide = f.data && feat_rows_wide(f.data, f.dim, f.dtype);
     a.fscale = f.scale;
     a.D = f.dim;
     a.c0 = 0;
