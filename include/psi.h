@@ -284,7 +284,7 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
  * 1e-4 (nothing rendered).
  *  F: [n_pix, D] BF16, 16-byte aligned rows; Q: [n_q, D] BF16; D in {64,128};
  *  1 <= n_q <= 128; T: [n_pix] float; ids: [n_pix] int32; logits: [n_pix, n_q]
- *  BF16 or NULL. */
+ *  BF16 or NULL, 2-byte aligned (4-byte when n_q is even). */
 int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
                        int32_t *ids, void *logits, psi_stream stream);
 

@@ -384,8 +384,8 @@ int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const 
     if (n_q < 1 || n_q > 128) return fail(ctx, PSI_ERR_INVALID_ARG, "n_q must be in [1,128]");
     if (n_pix > 0 && (!F || !Q || !T || !ids)) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
     if (!aligned(F, 16) || !aligned(Q, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "F and Q must be 16-byte aligned");
-    if (logits && (!aligned(logits, 4) || (n_q % 2) != 0))
-        return fail(ctx, PSI_ERR_INVALID_ARG, "logits need an even n_q and 4-byte alignment");
+    if (logits && ((!aligned(logits, 4) && (n_q % 2) == 0) || !aligned(logits, 2)))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "logits must be 2-byte aligned (4-byte for an even n_q)");
     if (n_pix == 0) return PSI_OK;
     DeviceGuard g(ctx->device);
     const char *why = nullptr;

@@ -84,18 +84,18 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+// 16 consecutive TMEM columns of this thread's lane; the values are valid
+// only after tmem_wait_ld (several loads can be in flight before one wait).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t *r)
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kThreads, 1) decode_kernel(const __grid_constant__ CUtensorMap map_f,
                                                             const __grid_constant__ CUtensorMap map_q,
@@ -202,32 +202,42 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(const __grid_consta
             issue_tile(i + kStages);
             t_issued = i + kStages + 1;
         }
-        // epilogue: one pixel (TMEM lane) per thread
+        // epilogue: one pixel (TMEM lane) per thread; all of the row's
+        // columns are requested before a single wait
         const int64_t pix = tile_of(i) * kM + wid * 32 + lane;
+        const float Tp = pix < p.n_pix ? __ldg(p.T + pix) : 1.0f;
         const uint32_t tacc = tmem + (i & 1) * kAccStride + (static_cast<uint32_t>(wid * 32) << 16);
+        uint32_t r[kAccStride];
+#pragma unroll
+        for (int c0 = 0; c0 < static_cast<int>(kAccStride); c0 += 16)
+            if (c0 < p.n_pad) tmem_ld16_async(tacc + c0, r + c0);
+        tmem_wait_ld();
         float best = -__int_as_float(0x7f800000);
         int arg = 0;
-        for (int c0 = 0; c0 < p.n_pad; c0 += 16) {
-            float v[16];
-            tmem_ld16(tacc + c0, v);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int q = c0 + k;
-                if (q < p.n_q && v[k] > best) {
-                    best = v[k];
-                    arg = q;
-                }
-            }
-            if (p.logits && pix < p.n_pix) {
-                __nv_bfloat16 *row = p.logits + pix * p.n_q;
-#pragma unroll
-                for (int k = 0; k < 16; k += 2) {
-                    const int q = c0 + k;
-                    if (q < p.n_q) *reinterpret_cast<__nv_bfloat162 *>(row + q) = __floats2bfloat162_rn(v[k], v[k + 1]);
-                }
+        for (int q = 0; q < static_cast<int>(kAccStride); ++q) {
+            const float v = __uint_as_float(r[q]);
+            if (q < p.n_q && v > best) {
+                best = v;
+                arg = q;
             }
         }
-        if (pix < p.n_pix && !fail) p.ids[pix] = (1.0f - p.T[pix] < 1e-4f) ? -1 : arg;
+        if (p.logits && pix < p.n_pix) {
+            __nv_bfloat16 *row = p.logits + pix * p.n_q;
+            if ((p.n_q & 1) == 0) {
+                // even row length: 4-byte aligned pairs, never past the row
+#pragma unroll
+                for (int q = 0; q < static_cast<int>(kAccStride); q += 2)
+                    if (q < p.n_q)
+                        *reinterpret_cast<__nv_bfloat162 *>(row + q) =
+                            __floats2bfloat162_rn(__uint_as_float(r[q]), __uint_as_float(r[q + 1]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < static_cast<int>(kAccStride); ++q)
+                    if (q < p.n_q) row[q] = __float2bfloat16_rn(__uint_as_float(r[q]));
+            }
+        }
+        if (pix < p.n_pix && !fail) p.ids[pix] = (1.0f - Tp < 1e-4f) ? -1 : arg;
         tc_fence_before();
         stop = __syncthreads_or(fail) != 0;
     }

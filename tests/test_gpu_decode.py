@@ -38,7 +38,7 @@ def _check(F_bf16, Q_bf16, T, ids, logits, n_q):
 
 
 @pytest.mark.parametrize("D", [64, 128])
-@pytest.mark.parametrize("n_q", [1, 16, 100, 128])
+@pytest.mark.parametrize("n_q", [1, 16, 37, 100, 128])
 def test_decode_random(ctx, D, n_q):
     from paper_2604_10982_gb300 import psi
     n_pix = 1000 + 77  # 8 full tiles of 128 and a ragged tail
@@ -48,7 +48,7 @@ def test_decode_random(ctx, D, n_q):
     T = torch.rand(n_pix, generator=g).cuda()
     T[::7] = 1.0  # nothing rendered there
     ids = torch.full((n_pix,), -7, dtype=torch.int32, device="cuda")
-    logits = torch.empty(n_pix, n_q, dtype=torch.bfloat16, device="cuda") if n_q % 2 == 0 else None
+    logits = torch.empty(n_pix, n_q, dtype=torch.bfloat16, device="cuda")  # odd n_q: unaligned rows
     psi.psi_decode_queries(ctx, F, n_pix, D, Q, n_q, T, ids, logits)
     torch.cuda.synchronize()
     assert (ids.cpu().numpy()[::7] == -1).all()
