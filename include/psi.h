@@ -87,7 +87,7 @@ typedef struct {
 
 /* Per-surfel features f_i (Sec. 4.1): [N, dim] row-major in `dtype`.
  * Value of channel c is q[i,c] * scale[c] (scale may be NULL for F32/BF16,
- * meaning 1). dim must be a multiple of 8 and at most 256; rows must start on
+ * meaning 1). dim must be a multiple of 16 in [16, 256]; rows must start on
  * 16-byte boundaries. */
 typedef struct {
     const void *data;

@@ -4,6 +4,8 @@ Upstream gradients are zeroed on pixels the forward comparison excuses
 (threshold straddles, near ties, ill-conditioned), on both sides, so the
 comparison is exact apart from float32 rounding: the gradient is linear in
 the upstream gradient."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -40,9 +42,13 @@ def _upstream(cams, D, seed, pixel_mask=None):
     return gC, gF, gT
 
 
-def _grad_compare(ctx, w, cams, o, D, tol=1e-3, sample_pixels=None):
-    from paper_2604_10982_gb300 import pipeline as pl
-    scene = pl.DeviceScene(w.surfels, w.features if D else None)
+def _grad_compare(ctx, w, cams, o, D, tol=1e-3, sample_pixels=None, feat_dtype=None):
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    fdt = psi.F32 if feat_dtype is None else feat_dtype
+    scene = pl.DeviceScene(w.surfels, w.features if D else None, feat_dtype=fdt)
+    if D and fdt != psi.F32:
+        # the oracle sees the stored (dequantised) feature values
+        w = dataclasses.replace(w, features=pl.dequantize(scene.q, scene.qscale, fdt))
     r = pl.make_renderer(ctx, scene, cams, opts_of(o), D=D)
     r.frame(scene)
     # excusal mask from the oracle's forward diagnostics, evaluated only on the
@@ -114,6 +120,16 @@ def test_grad_box_multiview(ctx, K):
     w = sg.dense_box(n=4000, d=16)
     o = orc.Opts(mode=orc.EXACT, top_k=K, opacity_radius=True)
     _grad_compare(ctx, w, multi_cams(), o, 16)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_grad_quantised_features_d128(ctx, dtype):
+    """The bench's feature form: D=128 stored in BF16 (32-byte row loads) or
+    FP8-E4M3 with per-channel scales, K=8, EXACT + opacity radius."""
+    from paper_2604_10982_gb300 import psi
+    w = sg.dense_box(n=3000, d=128)
+    o = orc.Opts(mode=orc.EXACT, top_k=8, opacity_radius=True)
+    _grad_compare(ctx, w, multi_cams()[:2], o, 128, feat_dtype=psi.BF16 if dtype == "bf16" else psi.FP8_E4M3)
 
 
 def test_grad_rgb_only(ctx):
