@@ -275,3 +275,46 @@ def decode(F, Q, T, empty_eps: float = 1e-4):
     empty = (1.0 - np.asarray(T, np.float64)) < empty_eps
     ids[empty] = -1
     return ids, L, gap
+
+
+def surfel_labels(feat, queries, q_mu, q_cov, centres, plant: int = 0):
+    """Per-surfel instance label distribution (Sec. 4.1, Eqs. 4-7), FP64.
+
+    feat [N, D] (the stored feature values), queries [Q, D] (query features
+    f_q), q_mu [Q, 3] and q_cov [Q, 3, 3] (each query's spatial Gaussian),
+    centres [N, 3] (surfel centres p_g). For every query q and surfel g:
+      S(f_q, f_g) = sigmoid(f_q^T f_g)                        (Eq. 4)
+      D(p_q, p_g) = phi_q(p_g) / phi_q(p_q), with phi_q the density of
+                    N(mu_q, Sigma_q) and p_q = mu_q its centre   (Eq. 5)
+      A(q, g)     = S D                                       (Eq. 6)
+      l_ins(g)    = softmax over the Q queries of A(., g)     (Eq. 7)
+    The ratio of densities leaves exp(-(p_g - mu_q)^T Sigma_q^-1 (p_g - mu_q) / 2).
+    Returns [N, Q] float64. `plant` > 0 builds a deliberately wrong variant
+    (only the test that checks the pins uses it)."""
+    f = np.asarray(feat, np.float64)
+    qf = np.asarray(queries, np.float64)
+    mu = np.asarray(q_mu, np.float64)
+    cov = np.asarray(q_cov, np.float64)
+    p = np.asarray(centres, np.float64)
+    z = f @ qf.T
+    S = z if plant == 4 else 1.0 / (1.0 + np.exp(-z))
+    prec = cov if plant == 3 else np.linalg.inv(cov)
+    d = p[:, None, :] - mu[None, :, :]
+    m2 = np.einsum("nqi,qij,nqj->nq", d, prec, d)
+    D = np.exp(-m2) if plant == 1 else np.exp(-0.5 * m2)
+    A = S * D
+    axis = 0 if plant == 2 else 1
+    e = np.exp(A - A.max(axis=axis, keepdims=True))
+    return e / e.sum(axis=axis, keepdims=True)
+
+
+def label_ids(I, T, empty_eps: float = 1e-4):
+    """Pixel instance identity from the rendered label mixture I [P, Q]
+    (Eq. 8): argmax over queries, lowest index on ties, -1 where nothing was
+    rendered. Returns (ids [P] int32, gap [P] top-2 margin)."""
+    I = np.asarray(I, np.float64)
+    ids = np.argmax(I, axis=1).astype(np.int32)
+    part = -np.sort(-I, axis=1)
+    gap = part[:, 0] - part[:, 1] if I.shape[1] > 1 else np.full(I.shape[0], np.inf)
+    ids[(1.0 - np.asarray(T, np.float64)) < empty_eps] = -1
+    return ids, gap

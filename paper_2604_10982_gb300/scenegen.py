@@ -184,6 +184,28 @@ def make_queries(q: int, d: int, seed: int) -> np.ndarray:
     return (normal(seed, _S_QUERY, q * d).reshape(q, d) / math.sqrt(d)).astype(np.float32)
 
 
+def make_query_gaussians(q: int, seed: int, lo, hi, sigma_range=(0.5, 3.0)):
+    """Spatial Gaussians of Q instance queries (Sec. 4.1): centres uniform in
+    the box [lo, hi], covariances R diag(s^2) R^T with per-axis s uniform in
+    sigma_range and R a rotation about a uniformly random axis by a uniform
+    angle. Returns (mu [Q,3], cov [Q,3,3]) float32."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    u = uniform(seed, _S_QUERY + 1, q * 10).reshape(q, 10)
+    mu = lo + u[:, 0:3] * (hi - lo)
+    s = sigma_range[0] + u[:, 3:6] * (sigma_range[1] - sigma_range[0])
+    cov = np.zeros((q, 3, 3))
+    for k in range(q):
+        z = 2.0 * u[k, 6] - 1.0
+        ph = 2.0 * math.pi * u[k, 7]
+        axis = np.array([math.sqrt(1 - z * z) * math.cos(ph), math.sqrt(1 - z * z) * math.sin(ph), z])
+        ang = 2.0 * math.pi * u[k, 8]
+        K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+        R = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * (K @ K)
+        cov[k] = R @ np.diag(s[k] ** 2) @ R.T
+    return mu.astype(np.float32), cov.astype(np.float32)
+
+
 def make_upstream(n: int, seed: int, stream: int = 0) -> np.ndarray:
     """n float32 N(0,1) values used as an upstream loss gradient."""
     return normal(seed, _S_GRAD + stream, n).astype(np.float32)

@@ -88,3 +88,58 @@ def test_planted_mistake_is_caught(plant, check):
             fn()
     finally:
         orc.use_variant(0)
+
+
+# ---------------------------------------------------------------- instance labels (Sec. 4.1, Eqs. 4-8)
+def _label_case(seed=5, n=40, q=7, d=16):
+    f = sg.make_features(n, d, seed).astype(np.float64)
+    qf = sg.make_queries(q, d, seed).astype(np.float64) * 3.0
+    mu, cov = sg.make_query_gaussians(q, seed, (-2, -2, 0), (2, 2, 3))
+    p = np.stack([sg.uniform(seed, 20 + k, n) * 4 - 2 for k in range(3)], axis=1)
+    return f, qf, mu.astype(np.float64), cov.astype(np.float64), p
+
+
+def _labels_pinned(plant=0):
+    """The label oracle against library routines that are not the oracle's:
+    scipy's multivariate normal density (the geometric factor is a ratio of
+    two of its values), its logistic function and its softmax."""
+    from scipy.special import expit, softmax
+    from scipy.stats import multivariate_normal
+    f, qf, mu, cov, p = _label_case()
+    L = orc.surfel_labels(f, qf, mu, cov, p, plant=plant)
+    S = expit(f @ qf.T)
+    D = np.stack([multivariate_normal(mu[k], cov[k]).pdf(p) / multivariate_normal(mu[k], cov[k]).pdf(mu[k])
+                  for k in range(len(mu))], axis=1)
+    ref = softmax(S * D, axis=1)
+    return np.abs(L - ref).max()
+
+
+def test_labels_against_library_densities():
+    assert _labels_pinned() < 1e-12
+
+
+def test_labels_special_cases():
+    f, qf, mu, cov, p = _label_case()
+    L = orc.surfel_labels(f, qf, mu, cov, p)
+    # a distribution over the queries for every surfel
+    assert np.all(L > 0) and np.allclose(L.sum(1), 1.0, atol=1e-14)
+    # a surfel at a query's centre: geometric factor exactly 1 for that query
+    p0 = np.repeat(mu[:1], 3, axis=0)
+    L0 = orc.surfel_labels(f[:3], qf[:1], mu[:1], cov[:1], p0)
+    assert np.array_equal(L0, np.ones((3, 1)))
+    # identical queries: the uniform distribution
+    Lu = orc.surfel_labels(f, np.repeat(qf[:1], 5, 0), np.repeat(mu[:1], 5, 0), np.repeat(cov[:1], 5, 0), p)
+    assert np.allclose(Lu, 0.2, atol=1e-15)
+
+
+def test_label_ids_rendered_mixture():
+    # Eq. 8 blends label vectors; the identity is the argmax (lowest on ties)
+    I = np.array([[0.1, 0.5, 0.4], [0.3, 0.3, 0.2], [0.0, 0.0, 0.0]])
+    ids, gap = orc.label_ids(I, np.array([0.5, 0.2, 1.0]))
+    assert list(ids) == [1, 0, -1] and np.isclose(gap[0], 0.1)
+
+
+@pytest.mark.parametrize("plant", [1, 2, 3, 4])
+def test_label_planted_mistake_is_caught(plant):
+    # dropped 1/2, softmax over surfels, covariance for precision, no sigmoid
+    assert _labels_pinned(plant) > 1e-6
