@@ -114,7 +114,11 @@ typedef struct {
  *  n_last:   [P_total] int32, 1 + list position of the last surfel composited (0: none)
  *  F:        [P_total, D] feature map in F_dtype (PSI_F32 or PSI_BF16)
  *  topk_ids: [P_total, K] int32 surfel ids of the selected set in list order, -1 padded
- *  topk_w:   [P_total, K] float32 weights omega_j = alpha_j T_j of those surfels, 0 padded */
+ *  topk_w:   [P_total, K] float32 weights omega_j = alpha_j T_j of those surfels, 0 padded
+ *  argmax:   [P_total] int32 channel of F's largest value (lowest channel on ties; FP32
+ *            before any BF16 rounding), -1 where 1 - T < 1e-4; top_k > 0 only. With F
+ *            NULL the feature mixture is formed in registers and never written: for a
+ *            label table from psi_surfel_labels this is the instance identity of Eq. 8 */
 typedef struct {
     float *rgb;
     float *T;
@@ -123,6 +127,7 @@ typedef struct {
     int32_t F_dtype;
     int32_t *topk_ids;
     float *topk_w;
+    int32_t *argmax;
 } psi_fwd_out;
 
 /* Gradients (device, float32, ACCUMULATED into: the caller zeroes them). Any
@@ -287,6 +292,30 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
  *  BF16 or NULL, 2-byte aligned (4-byte when n_q is even). */
 int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
                        int32_t *ids, void *logits, psi_stream stream);
+
+/* ---- per-surfel instance labels (Sec. 4.1, Eqs. 4-7) ---------------------
+ * For each surfel g and instance query q:
+ *   l[g, q] = softmax over q of sigmoid(f_q^T f_g) * D(q, g),
+ *   D(q, g) = exp(-(p_g - mu_q)^T Sigma_q^-1 (p_g - mu_q) / 2),
+ * the feature similarity (Eq. 4) times the ratio of the query Gaussian's
+ * densities at the surfel centre p_g and at its own centre mu_q (Eq. 5),
+ * normalised over the queries (Eqs. 6-7). f_q^T f_g runs on the tensor cores
+ * (BF16 in, FP32 accumulate), the rest in FP32. The table has ld columns,
+ * zero past n_q, so psi_render_fwd can render it as a feature table: F is
+ * then the alpha-blended label mixture I of Eq. 8 (Top-K selected), and
+ * psi_fwd_out.argmax its per-pixel instance identity.
+ *  f: the surfel feature table, BF16 without scale, dim 64 or 128
+ *  centres: [n, 3] float32 surfel centres (psi_surfels.mu); n < 2^31
+ *  Q: [n_q, D] BF16 query features, 1 <= n_q <= 128, 16-byte aligned
+ *  q_mu: [n_q, 3] float32 query centres; q_cov: [n_q, 6] float32 covariance
+ *  entries (xx, xy, xz, yy, yz, zz), positive definite
+ *  labels: [n, ld] in labels_dtype (PSI_F32 or PSI_BF16), 16-byte aligned;
+ *  ld a multiple of 16 in [n_q, 128].
+ * PSI_ERR_UNSUPPORTED for other feature types or dims. No counterpart call in
+ * the paper's tables; the equations are its Sec. 4.1. */
+int psi_surfel_labels(psi_ctx *ctx, const psi_features *f, const float *centres, int64_t n, const void *Q, int n_q,
+                      const float *q_mu, const float *q_cov, void *labels, int labels_dtype, int ld,
+                      psi_stream stream);
 
 #ifdef __cplusplus
 }

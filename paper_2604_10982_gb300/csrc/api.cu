@@ -327,6 +327,8 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
     if (out->F && out->F_dtype != PSI_F32 && out->F_dtype != PSI_BF16)
         return fail(ctx, PSI_ERR_INVALID_ARG, "F_dtype must be PSI_F32 or PSI_BF16");
     if (out->F && !aligned(out->F, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "out.F must be 16-byte aligned");
+    if (out->argmax && (o->top_k <= 0 || !fv.data))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "out.argmax needs top_k > 0 and features");
     if (!records || !vals || !tile_ranges) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
     if (!aligned(records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 16-byte aligned");
     if (n_surfels < 0) return fail(ctx, PSI_ERR_INVALID_ARG, "n_surfels < 0");
@@ -393,6 +395,30 @@ int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const 
                                        reinterpret_cast<cudaStream_t>(stream), &why);
     if (why) return fail(ctx, PSI_ERR_CUDA, "psi_decode_queries: %s", why);
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_decode_queries", e);
+}
+
+int psi_surfel_labels(psi_ctx *ctx, const psi_features *f, const float *centres, int64_t n, const void *Q, int n_q,
+                      const float *q_mu, const float *q_cov, void *labels, int labels_dtype, int ld, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "n out of range");
+    if (!f || !f->data) return fail(ctx, PSI_ERR_INVALID_ARG, "features are required");
+    if (f->dtype != PSI_BF16 || f->scale) return fail(ctx, PSI_ERR_UNSUPPORTED, "labels need BF16 features without scale");
+    if (f->dim != 64 && f->dim != 128) return fail(ctx, PSI_ERR_UNSUPPORTED, "D must be 64 or 128");
+    if (n_q < 1 || n_q > 128) return fail(ctx, PSI_ERR_INVALID_ARG, "n_q must be in [1,128]");
+    if (ld < n_q || ld > 128 || ld % 16 != 0) return fail(ctx, PSI_ERR_INVALID_ARG, "ld must be a multiple of 16 in [n_q, 128]");
+    if (labels_dtype != PSI_F32 && labels_dtype != PSI_BF16)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "labels_dtype must be PSI_F32 or PSI_BF16");
+    if (n > 0 && (!centres || !Q || !q_mu || !q_cov || !labels)) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned(f->data, 16) || !aligned(Q, 16) || !aligned(labels, 16))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "features, Q and labels must be 16-byte aligned");
+    if (n == 0) return PSI_OK;
+    DeviceGuard g(ctx->device);
+    const char *why = nullptr;
+    cudaError_t e = psi::launch_labels(f->data, n, f->dim, centres, Q, n_q, q_mu, q_cov, labels, ld,
+                                       labels_dtype == PSI_BF16, ctx->status, reinterpret_cast<cudaStream_t>(stream), &why);
+    if (why) return fail(ctx, PSI_ERR_CUDA, "psi_surfel_labels: %s", why);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_surfel_labels", e);
 }
 
 } // extern "C"

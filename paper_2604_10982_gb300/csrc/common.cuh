@@ -198,6 +198,9 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
                               DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2]);
 
+cudaError_t launch_labels(const void *F, int64_t n, int D, const float *centres, const void *Q, int n_q,
+                          const float *q_mu, const float *q_cov, void *labels, int ld, int out_bf16, DevStatus *status,
+                          cudaStream_t st, const char **why);
 cudaError_t launch_decode(const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T, int32_t *ids,
                           void *logits, DevStatus *status, cudaStream_t st, const char **why);
 

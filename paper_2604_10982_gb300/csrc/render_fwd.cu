@@ -36,6 +36,7 @@ struct FwdArgs {
     int F_bf16;
     int32_t *topk_ids;
     float *topk_w;
+    int32_t *argmax;
     DevStatus *status;
 };
 
@@ -164,10 +165,12 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
             for (int s = 0; s < KMAX; ++s)
                 if (s < K) dst[s] = sid[s] >= 0 ? top.w[s] : 0.0f;
         }
-        if (a.F && a.feat) {
+        if ((a.F || a.argmax) && a.feat) {
             // 16 channels per chunk keeps the gather's registers low (one
             // 32-byte BF16 row slice = two 16-byte loads per selected surfel)
             constexpr int CB = 16;
+            float best = -__int_as_float(0x7f800000);
+            int arg = 0;
             for (int c0 = 0; c0 < a.D; c0 += CB) {
                 float acc[CB];
 #pragma unroll
@@ -180,8 +183,19 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
 #pragma unroll
                     for (int c = 0; c < CB; ++c) acc[c] = __fmaf_rn(top.w[s], f[c], acc[c]);
                 }
-                store_feat<CB>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
+                if (a.F) store_feat<CB>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
+                if (a.argmax) {
+#pragma unroll
+                    for (int c = 0; c < CB; ++c) {
+                        const float val = a.fscale ? acc[c] * __ldg(a.fscale + c0 + c) : acc[c];
+                        if (val > best) {
+                            best = val;
+                            arg = c0 + c;
+                        }
+                    }
+                }
             }
+            if (a.argmax) a.argmax[pix] = (1.0f - T < 1e-4f) ? -1 : arg;
         }
     }
 }
@@ -231,6 +245,7 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
     a.F_bf16 = out.F_dtype == PSI_BF16;
     a.topk_ids = out.topk_ids;
     a.topk_w = out.topk_w;
+    a.argmax = out.argmax;
     a.status = status;
     const int K = fp.top_k;
     const int ch = (f.dim % 32 == 0) ? 32 : 16;

@@ -165,11 +165,15 @@ class Renderer:
                           end_bit or self.key_bits, self.ranges, self.n_tiles, self.ws_sort, stream)
 
     # a4
-    def render(self, scene: DeviceScene, want_F: bool = True, stream=None):
+    def render(self, scene: DeviceScene, want_F: bool = True, stream=None, argmax: bool = False):
+        """Composite the frame. argmax: also the per-pixel channel argmax of the
+        feature mixture (self.argmax; -1 on empty pixels), fused in the kernel."""
         feats = scene.features_struct()
+        if argmax and getattr(self, "argmax", None) is None:
+            self.argmax = torch.empty(self.n_pix, dtype=torch.int32, device=self.dev)
         out = psi.PsiFwdOut(psi._ptr(self.rgb), psi._ptr(self.T), psi._ptr(self.n_last),
                             psi._ptr(self.F) if (want_F and self.F is not None) else None, int(self.F_dtype),
-                            psi._ptr(self.topk_ids), psi._ptr(self.topk_w))
+                            psi._ptr(self.topk_ids), psi._ptr(self.topk_w), psi._ptr(self.argmax) if argmax else None)
         psi.psi_render_fwd(self.ctx, feats, self.records, self.vals, self.ranges, self.cams, self.V, self.n, self.opts,
                            out, stream)
 
@@ -223,6 +227,35 @@ class Renderer:
         if t.dim() == 2 and t.shape[0] == 3 and t.shape[1] == self.n_pix:
             return t[:, a:b].reshape(3, c.height, c.width)
         return t[a:b].reshape(c.height, c.width, *t.shape[1:])
+
+
+def surfel_labels(ctx, scene: DeviceScene, queries, q_mu, q_cov, ld: int | None = None, dtype: int = psi.BF16,
+                  stream=None) -> torch.Tensor:
+    """Per-surfel instance label table [N, ld] (Sec. 4.1, Eqs. 4-7) from the
+    scene's BF16 features. queries [Q, D] BF16, q_mu [Q, 3], q_cov [Q, 3, 3]
+    (device or host tensors)."""
+    dev = scene.mu.device
+    nq = int(queries.shape[0])
+    ld = ld or ((nq + 15) // 16) * 16
+    Q = torch.as_tensor(queries).to(dev).to(torch.bfloat16).contiguous()
+    mu = torch.as_tensor(q_mu, dtype=torch.float32).to(dev).contiguous()
+    cov = torch.as_tensor(q_cov, dtype=torch.float32).to(dev)
+    c6 = torch.stack([cov[:, 0, 0], cov[:, 0, 1], cov[:, 0, 2], cov[:, 1, 1], cov[:, 1, 2], cov[:, 2, 2]], 1).contiguous()
+    out = torch.empty(scene.n, ld, dtype=torch.bfloat16 if dtype == psi.BF16 else torch.float32, device=dev)
+    psi.psi_surfel_labels(ctx, scene.features_struct(), scene.mu, scene.n, Q, nq, mu, c6, out, dtype, ld, stream)
+    return out
+
+
+def label_scene(scene: DeviceScene, labels: torch.Tensor) -> DeviceScene:
+    """The same surfels with the label table as their feature table, so a
+    Renderer composites the label mixture of Eq. 8."""
+    ls = object.__new__(DeviceScene)
+    ls.__dict__.update(scene.__dict__)
+    ls.q = labels
+    ls.qscale = None
+    ls.feat_dtype = psi.BF16 if labels.dtype == torch.bfloat16 else psi.F32
+    ls.D = int(labels.shape[1])
+    return ls
 
 
 def make_renderer(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, want_topk_ids=True, headroom=1.25,

@@ -49,7 +49,7 @@ class PsiRenderOpts(ctypes.Structure):
 
 class PsiFwdOut(ctypes.Structure):
     _fields_ = [("rgb", _P), ("T", _P), ("n_last", _P), ("F", _P), ("F_dtype", _i32), ("topk_ids", _P),
-                ("topk_w", _P)]
+                ("topk_w", _P), ("argmax", _P)]
 
 
 class PsiGrads(ctypes.Structure):
@@ -96,6 +96,8 @@ def lib():
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.psi_surfel_labels.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _i64, _P, ctypes.c_int, _P, _P, _P,
+                                         ctypes.c_int, ctypes.c_int, _P]
         L.psi_decode_queries.argtypes = [_P, _P, _i64, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]
         _lib = L
     return _lib
@@ -275,6 +277,12 @@ def psi_ctx_time_kernel(ctx, kernel, ev_begin, ev_end):
     b = None if ev_begin is None else ctypes.c_void_p(ev_begin.cuda_event)
     e = None if ev_end is None else ctypes.c_void_p(ev_end.cuda_event)
     ctx.check(lib().psi_ctx_time_kernel(ctx.handle, int(kernel), b, e), "psi_ctx_time_kernel")
+
+
+def psi_surfel_labels(ctx, feats, centres, n, Q, n_q, q_mu, q_cov, labels, labels_dtype, ld, stream=None):
+    ctx.check(lib().psi_surfel_labels(ctx.handle, ctypes.byref(feats), _ptr(centres), int(n), _ptr(Q), int(n_q),
+                                      _ptr(q_mu), _ptr(q_cov), _ptr(labels), int(labels_dtype), int(ld),
+                                      _stream(stream)), "psi_surfel_labels")
 
 
 def psi_decode_queries(ctx, F, n_pix, D, Q, n_q, T, ids, logits=None, stream=None):
