@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--ablation-frames", type=int, default=6, help="frames per Table-3 row (0: skip)")
+    ap.add_argument("--label-frames", type=int, default=8, help="frames of the instance-label path (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -551,6 +552,46 @@ def run_psi(args):
                  "form": "SPHERE tiles, dense FP32 features (no Top-K), single view per launch, no graph, no decode"}
         del scene32, rp
 
+    # ---- panoptic identity path (Sec. 4.1, Eqs. 4-8): per-surfel instance
+    # labels once per map, then per frame the label table composited with
+    # Top-K and a fused per-pixel argmax (no feature map written)
+    labels = None
+    if args.label_frames > 0:
+        q_mu, q_cov = sg.make_query_gaussians(nq, 9, (-8, 0, 0), (8, 60, 12))
+        Qb = Qd
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for rep in range(2):  # the second call is timed
+            ev[0].record()
+            L = pl.surfel_labels(ctx, scene, Qb, q_mu, q_cov, dtype=psi.BF16)
+            ev[1].record()
+            torch.cuda.synchronize()
+        lab_ms = ev[0].elapsed_time(ev[1])
+        ls = pl.label_scene(scene, L)
+        rl = pl.Renderer(ctx, scene.n, [cams[0]], opts, r.capacity, D=ls.D, F_dtype=psi.BF16, device=dev)
+        lt = []
+        for k in range(args.label_frames + 1):
+            rl.set_cameras([cams[fidx(k)]])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rl.project(ls)
+            rl.intersect()
+            rl.sort()
+            rl.render(ls, want_F=False, argmax=True)
+            e1.record()
+            torch.cuda.synchronize()
+            if k > 0:
+                lt.append(e0.elapsed_time(e1))
+        st, _ = ctx.status_fetch()
+        assert st == 0, f"device status {st}"
+        lab_bytes = scene.n * (2.0 * D + 12.0 + 2.0 * ls.D)  # features + centres read, table written
+        labels = {"labels_ms": float(lab_ms), "queries": nq, "table": f"[{scene.n}, {ls.D}] BF16",
+                  "labels_hbm_frac": lab_bytes / (lab_ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+                  "frame_ms": float(np.median(lt)), "frames_per_s": float(1000.0 / np.median(lt)),
+                  "form": "per map: sigmoid(f_q^T f_g) x query-Gaussian density ratio, softmax over queries "
+                          "(tcgen05 + FP32 epilogue); per frame: project+intersect+sort+render of the label table "
+                          "(K=8, EXACT) with the fused per-pixel argmax"}
+        del rl, ls, L
+
     # ---- the paper's Table 3 rows on this GPU: tile test x feature selection,
     # same BF16 features, forward of one frame (project, intersect, sort,
     # render), eager launches, median over frames
@@ -610,7 +651,7 @@ def run_psi(args):
         "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)}, "kernel_ms": kernel_ms,
         "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
-        "plain_fp32": plain, "ablation": ablation, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "plain_fp32": plain, "ablation": ablation, "labels": labels, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),
         "clocks": clk, "paper_context": PAPER_CONTEXT, "setup_s": setup_s,
     }
