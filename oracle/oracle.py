@@ -318,3 +318,45 @@ def label_ids(I, T, empty_eps: float = 1e-4):
     gap = part[:, 0] - part[:, 1] if I.shape[1] > 1 else np.full(I.shape[0], np.inf)
     ids[(1.0 - np.asarray(T, np.float64)) < empty_eps] = -1
     return ids, gap
+
+
+def surfel_regularisers(s, node_of, node_mu, node_n, lambda_n: float, plant: int = 0):
+    """Geometric and anisotropy regularisers of the joint objective (Sec. 4.2), FP64.
+
+    For surfel i with an assigned planar prior k = node_of[i] (>= 0; -1: none),
+    prior centre m_k and unit normal nhat_k:
+      d_i   = |(mu_i - m_k) . nhat_k|                  point-to-plane distance
+      L_geo = sum_i d_i + lambda_n (1 - |n_i . nhat_k|),  n_i = t_u x t_v / |t_u x t_v|
+      L_iso = sum_i (s_i1 - s_i2)^2
+    Returns (L_geo, L_iso, grads) with grads the gradients of L_geo (keys
+    mu, tu, tv) and of L_iso (key scale), each [N, ...] float64, written by
+    hand from the chain rule. `plant` > 0 builds a deliberately wrong variant
+    (only the pin test uses it)."""
+    mu = np.asarray(s.mu, np.float64)
+    tu = np.asarray(s.tu, np.float64)
+    tv = np.asarray(s.tv, np.float64)
+    sc = np.asarray(s.scale, np.float64)
+    k = np.asarray(node_of, np.int64)
+    has = k >= 0
+    m = np.asarray(node_mu, np.float64)[np.where(has, k, 0)]
+    nh = np.asarray(node_n, np.float64)[np.where(has, k, 0)]
+    c = np.cross(tu, tv)
+    cn = np.linalg.norm(c, axis=1, keepdims=True)
+    n = c / cn
+    off = np.sum((mu - m) * nh, axis=1)
+    dot = np.sum(n * nh, axis=1)
+    term_n = (1.0 - dot) if plant == 2 else (1.0 - np.abs(dot))
+    L_geo = float(np.sum(np.where(has, np.abs(off) + lambda_n * term_n, 0.0)))
+    diff = sc[:, 0] - sc[:, 1]
+    L_iso = float(np.sum(diff * diff)) if plant != 3 else float(np.sum(np.abs(diff)))
+    g = {}
+    g["mu"] = np.where(has[:, None], np.sign(off)[:, None] * nh, 0.0)
+    gn = np.where(has[:, None], -lambda_n * (np.ones_like(dot) if plant == 2 else np.sign(dot))[:, None] * nh, 0.0)
+    # n = c/|c|: dL/dc = (I - n n^T) dL/dn / |c|; c = tu x tv: dL/dtu = tv x dL/dc, dL/dtv = dL/dc x tu
+    gc = (gn - np.sum(gn * n, axis=1, keepdims=True) * n) / cn
+    if plant == 1:
+        gc = gn / cn
+    g["tu"] = np.cross(tv, gc)
+    g["tv"] = np.cross(gc, tu)
+    g["scale"] = np.stack([2.0 * diff, -2.0 * diff], axis=1)
+    return L_geo, L_iso, g

@@ -143,3 +143,86 @@ def test_label_ids_rendered_mixture():
 def test_label_planted_mistake_is_caught(plant):
     # dropped 1/2, softmax over surfels, covariance for precision, no sigmoid
     assert _labels_pinned(plant) > 1e-6
+
+
+# ---------------------------------------------------------------- regularisers (Sec. 4.2)
+def _reg_case(n=60, seed=3):
+    s = sg.dense_box(n=n).surfels
+    rng = np.random.default_rng(seed)
+    M = 9
+    node_mu = rng.normal(size=(M, 3))
+    nn = rng.normal(size=(M, 3))
+    node_n = nn / np.linalg.norm(nn, axis=1, keepdims=True)
+    node_of = rng.integers(-1, M, n)
+    return s, node_of, node_mu, node_n
+
+
+def _reg_loss(s, node_of, node_mu, node_n, lam, mu, tu, tv, sc, plant=0):
+    t = sg.Surfels(mu=mu, tu=tu, tv=tv, scale=sc, opacity=s.opacity, rgb=s.rgb)
+    Lg, Li, _ = orc.surfel_regularisers(t, node_of, node_mu, node_n, lam, plant=plant)
+    return Lg + Li
+
+
+def _reg_fd_error(plant=0, lam=0.7):
+    """Hand-written gradients against central differences of the losses."""
+    s, node_of, node_mu, node_n = _reg_case()
+    base = dict(mu=np.asarray(s.mu, np.float64), tu=np.asarray(s.tu, np.float64), tv=np.asarray(s.tv, np.float64),
+                sc=np.asarray(s.scale, np.float64))
+    _, _, g = orc.surfel_regularisers(s, node_of, node_mu, node_n, lam, plant=plant)
+    gmap = {"mu": g["mu"], "tu": g["tu"], "tv": g["tv"], "sc": g["scale"]}
+    worst = 0.0
+    h = 1e-6
+    for key in ("mu", "tu", "tv", "sc"):
+        for i in range(0, 60, 7):
+            for c in range(base[key].shape[1]):
+                p = {k2: v.copy() for k2, v in base.items()}
+                m = {k2: v.copy() for k2, v in base.items()}
+                p[key][i, c] += h
+                m[key][i, c] -= h
+                fd = (_reg_loss(s, node_of, node_mu, node_n, lam, p["mu"], p["tu"], p["tv"], p["sc"], plant) -
+                      _reg_loss(s, node_of, node_mu, node_n, lam, m["mu"], m["tu"], m["tv"], m["sc"], plant)) / (2 * h)
+                worst = max(worst, abs(fd - gmap[key][i, c]) / max(1.0, abs(fd)))
+    return worst
+
+
+def test_regulariser_gradients_against_central_differences():
+    assert _reg_fd_error() < 1e-6
+
+
+def test_regulariser_closed_forms():
+    s, node_of, node_mu, node_n = _reg_case()
+    # a surfel lying in its prior plane, facing along the prior normal, with equal scales: zero loss
+    n0 = node_n[0]
+    a = np.cross(n0, [1.0, 0.0, 0.0])
+    a /= np.linalg.norm(a)
+    b = np.cross(n0, a)  # a x b = n0
+    t = sg.Surfels(mu=(node_mu[0] + 0.3 * a)[None], tu=a[None], tv=b[None], scale=np.array([[0.1, 0.1]]),
+                   opacity=np.array([0.5]), rgb=np.zeros((1, 3)))
+    Lg, Li, _ = orc.surfel_regularisers(t, np.array([0]), node_mu, node_n, 0.7)
+    assert abs(Lg) < 1e-15 and Li == 0.0
+    # moved 0.25 along the normal and flipped (|n . nhat| = 1 still): distance term only
+    t2 = sg.Surfels(mu=(node_mu[0] + 0.25 * n0)[None], tu=b[None], tv=a[None], scale=np.array([[0.3, 0.1]]),
+                    opacity=np.array([0.5]), rgb=np.zeros((1, 3)))
+    Lg2, Li2, _ = orc.surfel_regularisers(t2, np.array([0]), node_mu, node_n, 0.7)
+    assert abs(Lg2 - 0.25) < 1e-14 and abs(Li2 - 0.04) < 1e-15
+    # unassigned surfels carry no geometric loss
+    Lg3, _, g3 = orc.surfel_regularisers(t2, np.array([-1]), node_mu, node_n, 0.7)
+    assert Lg3 == 0.0 and not g3["mu"].any() and not g3["tu"].any()
+
+
+@pytest.mark.parametrize("plant", [1, 2, 3])
+def test_regulariser_planted_mistake_is_caught(plant):
+    # no tangent projection of the normal gradient; signed alignment; |.| for the anisotropy square
+    assert _reg_fd_error(plant) > 1e-4 or plant == 2 and _reg_plant2_closed_form_fails()
+
+
+def _reg_plant2_closed_form_fails():
+    s, node_of, node_mu, node_n = _reg_case()
+    n0 = node_n[0]
+    a = np.cross(n0, [1.0, 0.0, 0.0])
+    a /= np.linalg.norm(a)
+    b = np.cross(n0, a)
+    t = sg.Surfels(mu=node_mu[0][None], tu=b[None], tv=a[None], scale=np.array([[0.1, 0.1]]),
+                   opacity=np.array([0.5]), rgb=np.zeros((1, 3)))  # normal -nhat: |n . nhat| = 1
+    Lg, _, _ = orc.surfel_regularisers(t, np.array([0]), node_mu, node_n, 0.7, plant=2)
+    return abs(Lg) > 1e-6
