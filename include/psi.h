@@ -293,6 +293,22 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
 int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
                        int32_t *ids, void *logits, psi_stream stream);
 
+/* ---- geometric and anisotropy regularisers (Sec. 4.2) ---------------------
+ * For surfel i with an assigned planar prior k = node_of[i] (k < 0: none;
+ * k >= n_nodes raises PSI_ERR_INVALID_ARG in the status word):
+ *   L_geo = sum_i |(mu_i - m_k).nhat_k| + lambda_n (1 - |n_i.nhat_k|),
+ *           n_i = (t_u x t_v) / |t_u x t_v|   (point-to-plane distance and
+ *           normal alignment against the prior)
+ *   L_iso = sum_i (s_i1 - s_i2)^2            (anisotropy)
+ * losses[0] = L_geo, losses[1] = L_iso (device float64, overwritten); the
+ * gradients of w_geo L_geo + w_iso L_iso are ADDED to grads->mu, tu, tv,
+ * scale (any may be NULL; other members ignored). node_of may be NULL (no
+ * priors). node_mu, node_n: [n_nodes, 3] float32, node_n unit length. The
+ * planar priors themselves (the paper's SOGMM nodes) come from the caller. */
+int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *node_of, const float *node_mu,
+                            const float *node_n, int64_t n_nodes, float lambda_n, float w_geo, float w_iso,
+                            double *losses, const psi_grads *grads, psi_stream stream);
+
 /* ---- per-surfel instance labels (Sec. 4.1, Eqs. 4-7) ---------------------
  * For each surfel g and instance query q:
  *   l[g, q] = softmax over q of sigmoid(f_q^T f_g) * D(q, g),

@@ -397,6 +397,23 @@ int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const 
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_decode_queries", e);
 }
 
+int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *node_of, const float *node_mu,
+                            const float *node_n, int64_t n_nodes, float lambda_n, float w_geo, float w_iso,
+                            double *losses, const psi_grads *grads, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = check_surfels(ctx, s))) return rc;
+    if (!losses || !grads) return fail(ctx, PSI_ERR_INVALID_ARG, "losses and grads are required");
+    if (n_nodes < 0 || (n_nodes > 0 && (!node_mu || !node_n)))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "node arrays are required for n_nodes > 0");
+    if (!aligned(losses, 8)) return fail(ctx, PSI_ERR_INVALID_ARG, "losses must be 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_regularisers(*s, node_of, node_mu, node_n, n_nodes, lambda_n, w_geo, w_iso, losses,
+                                             *grads, ctx->status, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_surfel_regularisers", e);
+}
+
 int psi_surfel_labels(psi_ctx *ctx, const psi_features *f, const float *centres, int64_t n, const void *Q, int n_q,
                       const float *q_mu, const float *q_cov, void *labels, int labels_dtype, int ld, psi_stream stream)
 {

@@ -96,6 +96,8 @@ def lib():
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.psi_surfel_regularisers.argtypes = [_P, ctypes.POINTER(PsiSurfels), _P, _P, _P, _i64, ctypes.c_float,
+                                               ctypes.c_float, ctypes.c_float, _P, ctypes.POINTER(PsiGrads), _P]
         L.psi_surfel_labels.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _i64, _P, ctypes.c_int, _P, _P, _P,
                                          ctypes.c_int, ctypes.c_int, _P]
         L.psi_decode_queries.argtypes = [_P, _P, _i64, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]
@@ -277,6 +279,13 @@ def psi_ctx_time_kernel(ctx, kernel, ev_begin, ev_end):
     b = None if ev_begin is None else ctypes.c_void_p(ev_begin.cuda_event)
     e = None if ev_end is None else ctypes.c_void_p(ev_end.cuda_event)
     ctx.check(lib().psi_ctx_time_kernel(ctx.handle, int(kernel), b, e), "psi_ctx_time_kernel")
+
+
+def psi_surfel_regularisers(ctx, s, node_of, node_mu, node_n, n_nodes, lambda_n, w_geo, w_iso, losses,
+                            grads: PsiGrads, stream=None):
+    ctx.check(lib().psi_surfel_regularisers(ctx.handle, ctypes.byref(s), _ptr(node_of), _ptr(node_mu), _ptr(node_n),
+                                            int(n_nodes), float(lambda_n), float(w_geo), float(w_iso), _ptr(losses),
+                                            ctypes.byref(grads), _stream(stream)), "psi_surfel_regularisers")
 
 
 def psi_surfel_labels(ctx, feats, centres, n, Q, n_q, q_mu, q_cov, labels, labels_dtype, ld, stream=None):
