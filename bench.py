@@ -592,6 +592,29 @@ def run_psi(args):
                           "(K=8, EXACT) with the fused per-pixel argmax"}
         del rl, ls, L
 
+    # ---- geometric and anisotropy regularisers (Sec. 4.2) over all surfels,
+    # against 4096 synthetic planar priors (every surfel assigned)
+    regs = None
+    if args.label_frames > 0:
+        rng = np.random.default_rng(5)
+        n_nodes = 4096
+        nm = torch.from_numpy(rng.normal(size=(n_nodes, 3)).astype(np.float32) * 10).to(dev)
+        nn_ = torch.from_numpy(rng.normal(size=(n_nodes, 3)).astype(np.float32)).to(dev)
+        nn_ = (nn_ / nn_.norm(dim=1, keepdim=True)).contiguous()
+        node_of = torch.from_numpy(rng.integers(0, n_nodes, scene.n).astype(np.int32)).to(dev)
+        losses = torch.empty(2, dtype=torch.float64, device=dev)
+        gs = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale")), None, None, None)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for rep in range(3):
+            ev[0].record()
+            psi.psi_surfel_regularisers(ctx, scene.surfels_struct(), node_of, nm, nn_, n_nodes, 0.5, 1.0, 1.0, losses, gs)
+            ev[1].record()
+            torch.cuda.synchronize()
+        reg_ms = ev[0].elapsed_time(ev[1])
+        reg_bytes = scene.n * (4.0 * (3 + 3 + 3 + 2) + 4.0 + 2 * 4.0 * (3 + 3 + 3 + 2))  # read + gradient read/write
+        regs = {"ms": float(reg_ms), "surfels": scene.n, "priors": n_nodes,
+                "hbm_frac": reg_bytes / (reg_ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
+
     # ---- the paper's Table 3 rows on this GPU: tile test x feature selection,
     # same BF16 features, forward of one frame (project, intersect, sort,
     # render), eager launches, median over frames
@@ -651,7 +674,7 @@ def run_psi(args):
         "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)}, "kernel_ms": kernel_ms,
         "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
-        "plain_fp32": plain, "ablation": ablation, "labels": labels, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "plain_fp32": plain, "ablation": ablation, "labels": labels, "regularisers": regs, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),
         "clocks": clk, "paper_context": PAPER_CONTEXT, "setup_s": setup_s,
     }
