@@ -360,3 +360,39 @@ def surfel_regularisers(s, node_of, node_mu, node_n, lambda_n: float, plant: int
     g["tv"] = np.cross(gc, tu)
     g["scale"] = np.stack([2.0 * diff, -2.0 * diff], axis=1)
     return L_geo, L_iso, g
+
+
+def quat_frames(q, plant: int = 0):
+    """Tangent frame of a quaternion-parameterised surfel (the 2DGS form), FP64.
+
+    q [N, 4] = (w, x, y, z), not necessarily unit: R = R(q / |q|) and
+    t_u, t_v are its first two columns (the third is the surfel normal).
+    Returns (tu [N,3], tv [N,3])."""
+    q = np.asarray(q, np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    if plant == 1:
+        x = -x
+    tu = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)], axis=1)
+    tv = np.stack([2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)], axis=1)
+    return tu, tv
+
+
+def quat_frames_grad(q, g_tu, g_tv):
+    """dL/dq from dL/dt_u, dL/dt_v through quat_frames (normalisation
+    included), written from the partial derivatives of R's columns."""
+    q = np.asarray(q, np.float64)
+    nq = np.linalg.norm(q, axis=1, keepdims=True)
+    u = q / nq
+    w, x, y, z = u[:, 0], u[:, 1], u[:, 2], u[:, 3]
+    gu = np.asarray(g_tu, np.float64)
+    gv = np.asarray(g_tv, np.float64)
+    zero = np.zeros_like(w)
+    # d t_u / d(w, x, y, z) and d t_v / d(w, x, y, z), each [N, 3]
+    du = [np.stack(c, 1) for c in ((zero, 2 * z, -2 * y), (zero, 2 * y, 2 * z), (-4 * y, 2 * x, -2 * w),
+                                   (-4 * z, 2 * w, 2 * x))]
+    dv = [np.stack(c, 1) for c in ((-2 * z, zero, 2 * x), (2 * y, -4 * x, 2 * w), (2 * x, zero, 2 * z),
+                                   (-2 * w, -4 * z, 2 * y))]
+    gq_hat = np.stack([np.sum(gu * du[k], 1) + np.sum(gv * dv[k], 1) for k in range(4)], axis=1)
+    # through q / |q|
+    return (gq_hat - np.sum(gq_hat * u, axis=1, keepdims=True) * u) / nq

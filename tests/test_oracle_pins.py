@@ -226,3 +226,47 @@ def _reg_plant2_closed_form_fails():
                    opacity=np.array([0.5]), rgb=np.zeros((1, 3)))  # normal -nhat: |n . nhat| = 1
     Lg, _, _ = orc.surfel_regularisers(t, np.array([0]), node_mu, node_n, 0.7, plant=2)
     return abs(Lg) > 1e-6
+
+
+# ---------------------------------------------------------------- quaternion frames
+def _quats(n=50, seed=4):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(n, 4)) * rng.uniform(0.5, 2.0, size=(n, 1))
+
+
+def _frames_vs_scipy(plant=0):
+    from scipy.spatial.transform import Rotation
+    q = _quats()
+    tu, tv = orc.quat_frames(q, plant=plant)
+    R = Rotation.from_quat(q[:, [1, 2, 3, 0]]).as_matrix()  # scipy: scalar last, normalises
+    return max(np.abs(tu - R[:, :, 0]).max(), np.abs(tv - R[:, :, 1]).max())
+
+
+def test_quat_frames_against_scipy_rotation():
+    assert _frames_vs_scipy() < 1e-14
+
+
+def test_quat_frames_identity_and_orthonormal():
+    tu, tv = orc.quat_frames(np.array([[3.0, 0.0, 0.0, 0.0]]))
+    assert np.array_equal(tu, [[1.0, 0.0, 0.0]]) and np.array_equal(tv, [[0.0, 1.0, 0.0]])
+    tu, tv = orc.quat_frames(_quats())
+    assert np.allclose(np.sum(tu * tv, 1), 0.0, atol=1e-14) and np.allclose(np.linalg.norm(tu, axis=1), 1.0)
+
+
+def test_quat_frames_gradient_central_differences():
+    q = _quats()
+    rng = np.random.default_rng(9)
+    gu, gv = rng.normal(size=(50, 3)), rng.normal(size=(50, 3))
+    g = orc.quat_frames_grad(q, gu, gv)
+    h = 1e-6
+    for k in range(4):
+        p, m = q.copy(), q.copy()
+        p[:, k] += h
+        m[:, k] -= h
+        fp = np.sum(orc.quat_frames(p)[0] * gu, 1) + np.sum(orc.quat_frames(p)[1] * gv, 1)
+        fm = np.sum(orc.quat_frames(m)[0] * gu, 1) + np.sum(orc.quat_frames(m)[1] * gv, 1)
+        assert np.abs((fp - fm) / (2 * h) - g[:, k]).max() < 1e-7
+
+
+def test_quat_frames_planted_mistake_is_caught():
+    assert _frames_vs_scipy(plant=1) > 1e-3
