@@ -293,6 +293,17 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
 int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
                        int32_t *ids, void *logits, psi_stream stream);
 
+/* ---- quaternion-parameterised tangent frames (2DGS form) ------------------
+ * The paper's surfels follow 2DGS (Sec. 3.1), whose tangent frame is a
+ * rotation R(q / |q|) of a quaternion q = (w, x, y, z): t_u, t_v are R's first
+ * two columns. psi_quat_frames writes them ([n, 3] float32 each) for use as
+ * psi_surfels.tu / tv; psi_quat_frames_bwd ADDS dL/dq ([n, 4]) given dL/dt_u,
+ * dL/dt_v (either may be NULL), e.g. psi_grads.tu / tv from psi_render_bwd.
+ * q, g_q: [n, 4] float32, 16-byte aligned; q must not be zero. */
+int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream);
+int psi_quat_frames_bwd(psi_ctx *ctx, const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
+                        psi_stream stream);
+
 /* ---- geometric and anisotropy regularisers (Sec. 4.2) ---------------------
  * For surfel i with an assigned planar prior k = node_of[i] (k < 0: none;
  * k >= n_nodes raises PSI_ERR_INVALID_ARG in the status word):

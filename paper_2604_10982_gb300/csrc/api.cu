@@ -397,6 +397,27 @@ int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const 
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_decode_queries", e);
 }
 
+int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!q || !tu || !tv))) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument or n < 0");
+    if (!aligned(q, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "q must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_frames(q, n, tu, tv, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_quat_frames", e);
+}
+
+int psi_quat_frames_bwd(psi_ctx *ctx, const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
+                        psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!q || !g_q))) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument or n < 0");
+    if (!aligned(q, 16) || !aligned(g_q, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "q and g_q must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_frames_bwd(q, n, g_tu, g_tv, g_q, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_quat_frames_bwd", e);
+}
+
 int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *node_of, const float *node_mu,
                             const float *node_n, int64_t n_nodes, float lambda_n, float w_geo, float w_iso,
                             double *losses, const psi_grads *grads, psi_stream stream)

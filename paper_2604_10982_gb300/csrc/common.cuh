@@ -198,6 +198,9 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
                               DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2]);
 
+cudaError_t launch_frames(const float *q, int64_t n, float *tu, float *tv, cudaStream_t st);
+cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
+                              cudaStream_t st);
 cudaError_t launch_regularisers(const psi_surfels &s, const int32_t *node_of, const float *node_mu, const float *node_n,
                                 int64_t n_nodes, float lambda_n, float w_geo, float w_iso, double *losses,
                                 const psi_grads &g, DevStatus *status, cudaStream_t st);

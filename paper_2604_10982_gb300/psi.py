@@ -96,6 +96,8 @@ def lib():
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.psi_quat_frames.argtypes = [_P, _P, _i64, _P, _P, _P]
+        L.psi_quat_frames_bwd.argtypes = [_P, _P, _i64, _P, _P, _P, _P]
         L.psi_surfel_regularisers.argtypes = [_P, ctypes.POINTER(PsiSurfels), _P, _P, _P, _i64, ctypes.c_float,
                                                ctypes.c_float, ctypes.c_float, _P, ctypes.POINTER(PsiGrads), _P]
         L.psi_surfel_labels.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _i64, _P, ctypes.c_int, _P, _P, _P,
@@ -279,6 +281,16 @@ def psi_ctx_time_kernel(ctx, kernel, ev_begin, ev_end):
     b = None if ev_begin is None else ctypes.c_void_p(ev_begin.cuda_event)
     e = None if ev_end is None else ctypes.c_void_p(ev_end.cuda_event)
     ctx.check(lib().psi_ctx_time_kernel(ctx.handle, int(kernel), b, e), "psi_ctx_time_kernel")
+
+
+def psi_quat_frames(ctx, q, n, tu, tv, stream=None):
+    ctx.check(lib().psi_quat_frames(ctx.handle, _ptr(q), int(n), _ptr(tu), _ptr(tv), _stream(stream)),
+              "psi_quat_frames")
+
+
+def psi_quat_frames_bwd(ctx, q, n, g_tu, g_tv, g_q, stream=None):
+    ctx.check(lib().psi_quat_frames_bwd(ctx.handle, _ptr(q), int(n), _ptr(g_tu), _ptr(g_tv), _ptr(g_q),
+                                        _stream(stream)), "psi_quat_frames_bwd")
 
 
 def psi_surfel_regularisers(ctx, s, node_of, node_mu, node_n, n_nodes, lambda_n, w_geo, w_iso, losses,
