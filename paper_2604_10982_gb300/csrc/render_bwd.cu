@@ -101,7 +101,7 @@ constexpr int kDirectLanes = 1;
 // (<gF, f_j> and dL/df) come from the per-pixel feature kernel instead of this
 // walk. CH (channel chunk) matters only for K = 0.
 template <int KMAX, int DT, int CH, bool SAVED>
-__global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
+__global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED ? 4 : 3) : 1)
     render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
 {
     __shared__ __align__(128) Pipe P;
