@@ -591,45 +591,55 @@ def run_psi(args):
                  "form": "SPHERE tiles, dense FP32 features (no Top-K), single view per launch, no graph, no decode"}
         del scene32, rp
 
-    # ---- panoptic identity path (Sec. 4.1, Eqs. 4-8): per-surfel instance
-    # labels once per map, then per frame the label table composited with
-    # Top-K and a fused per-pixel argmax (no feature map written)
+    # ---- tables rendered like features (once per map, then per frame):
+    # instance labels (Sec. 4.1, Eqs. 4-8) and the plain query logits (the
+    # decode fused into compositing by linearity); per frame the table is
+    # composited with Top-K and the fused per-pixel argmax, no feature map
     labels = None
     if args.label_frames > 0:
         q_mu, q_cov = sg.make_query_gaussians(nq, 9, (-8, 0, 0), (8, 60, 12))
-        Qb = Qd
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        for rep in range(2):  # the second call is timed
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for rep in range(2):  # the second pass is timed
             ev[0].record()
-            L = pl.surfel_labels(ctx, scene, Qb, q_mu, q_cov, dtype=psi.BF16)
+            Lt = pl.surfel_labels(ctx, scene, Qd, q_mu, q_cov, dtype=psi.BF16)
             ev[1].record()
+            Gt = pl.surfel_logits(ctx, scene, Qd, dtype=psi.BF16)
+            ev[2].record()
             torch.cuda.synchronize()
-        lab_ms = ev[0].elapsed_time(ev[1])
-        ls = pl.label_scene(scene, L)
-        rl = pl.Renderer(ctx, scene.n, [cams[0]], opts, r.capacity, D=ls.D, F_dtype=psi.BF16, device=dev)
-        lt = []
-        for k in range(args.label_frames + 1):
-            rl.set_cameras([cams[fidx(k)]])
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            rl.project(ls)
-            rl.intersect()
-            rl.sort()
-            rl.render(ls, want_F=False, argmax=True)
-            e1.record()
-            torch.cuda.synchronize()
-            if k > 0:
-                lt.append(e0.elapsed_time(e1))
+        lab_ms, logit_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        out = {}
+        for name, table in (("labels", Lt), ("decode_fused", Gt)):
+            ts = pl.label_scene(scene, table)
+            rl = pl.Renderer(ctx, scene.n, [cams[0]], opts, r.capacity, D=ts.D, F_dtype=psi.BF16, device=dev)
+            rt, ft = [], []
+            for k in range(args.label_frames + 1):
+                rl.set_cameras([cams[fidx(k)]])
+                ev[0].record()
+                rl.project(ts)
+                rl.intersect()
+                rl.sort()
+                ev[1].record()
+                rl.render(ts, want_F=False, argmax=True)
+                ev[2].record()
+                torch.cuda.synchronize()
+                if k > 0:
+                    rt.append(ev[1].elapsed_time(ev[2]))
+                    ft.append(ev[0].elapsed_time(ev[2]))
+            out[name] = {"render_ms": float(np.median(rt)), "frame_ms": float(np.median(ft)),
+                         "table": f"[{scene.n}, {ts.D}] BF16"}
+            del rl, ts
         st, _ = ctx.status_fetch()
         assert st == 0, f"device status {st}"
-        lab_bytes = scene.n * (2.0 * D + 12.0 + 2.0 * ls.D)  # features + centres read, table written
-        labels = {"labels_ms": float(lab_ms), "queries": nq, "table": f"[{scene.n}, {ls.D}] BF16",
-                  "labels_hbm_frac": lab_bytes / (lab_ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
-                  "frame_ms": float(np.median(lt)), "frames_per_s": float(1000.0 / np.median(lt)),
-                  "form": "per map: sigmoid(f_q^T f_g) x query-Gaussian density ratio, softmax over queries "
-                          "(tcgen05 + FP32 epilogue); per frame: project+intersect+sort+render of the label table "
-                          "(K=8, EXACT) with the fused per-pixel argmax"}
-        del rl, ls, L
+        lab_bytes = scene.n * (2.0 * D + 12.0 + 2.0 * Lt.shape[1])  # features + centres read, table written
+        labels = {"labels_table_ms": float(lab_ms), "logits_table_ms": float(logit_ms), "queries": nq,
+                  "labels_table_hbm_frac": lab_bytes / (lab_ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+                  **out,
+                  "unfused_render_plus_decode_ms": float(mean_stage[names.index("render_fwd")] +
+                                                         mean_stage[names.index("decode")]),
+                  "form": "tables once per map on the tensor cores (labels: sigmoid x query-Gaussian density ratio, "
+                          "softmax; logits: f_q^T f_g); per frame: project+intersect+sort (eager) and the compositing "
+                          "of the table (K=8, EXACT) with the fused per-pixel argmax (render_ms)"}
+        del Lt, Gt
 
     # ---- geometric and anisotropy regularisers (Sec. 4.2) over all surfels,
     # against 4096 synthetic planar priors (every surfel assigned)

@@ -320,6 +320,19 @@ int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *n
                             const float *node_n, int64_t n_nodes, float lambda_n, float w_geo, float w_iso,
                             double *losses, const psi_grads *grads, psi_stream stream);
 
+/* ---- per-surfel query logits: the decode fused into compositing ----------
+ * table[g, q] = f_q^T f_g for every surfel (tensor cores, BF16 in, FP32
+ * accumulate), zero past n_q. Since sum_j omega_j <f_j, q> = <F, q>, the
+ * table rendered as a feature table by psi_render_fwd (Top-K selected) gives
+ * every pixel's decode logits, and psi_fwd_out.argmax the decoded id (a6),
+ * without the feature map F ever being written (F NULL). Computed once per
+ * map (features and queries fixed), then rendered per frame.
+ *  f: BF16 without scale, dim 64 or 128; Q: [n_q, D] BF16, 1 <= n_q <= 128;
+ *  table: [n, ld] in table_dtype (PSI_F32 or PSI_BF16), 16-byte aligned, ld
+ *  a multiple of 16 in [n_q, 128]. */
+int psi_surfel_logits(psi_ctx *ctx, const psi_features *f, int64_t n, const void *Q, int n_q, void *table,
+                      int table_dtype, int ld, psi_stream stream);
+
 /* ---- per-surfel instance labels (Sec. 4.1, Eqs. 4-7) ---------------------
  * For each surfel g and instance query q:
  *   l[g, q] = softmax over q of sigmoid(f_q^T f_g) * D(q, g),

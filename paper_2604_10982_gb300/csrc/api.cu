@@ -435,6 +435,30 @@ int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *n
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_surfel_regularisers", e);
 }
 
+int psi_surfel_logits(psi_ctx *ctx, const psi_features *f, int64_t n, const void *Q, int n_q, void *table,
+                      int table_dtype, int ld, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "n out of range");
+    if (!f || !f->data) return fail(ctx, PSI_ERR_INVALID_ARG, "features are required");
+    if (f->dtype != PSI_BF16 || f->scale) return fail(ctx, PSI_ERR_UNSUPPORTED, "logits need BF16 features without scale");
+    if (f->dim != 64 && f->dim != 128) return fail(ctx, PSI_ERR_UNSUPPORTED, "D must be 64 or 128");
+    if (n_q < 1 || n_q > 128) return fail(ctx, PSI_ERR_INVALID_ARG, "n_q must be in [1,128]");
+    if (ld < n_q || ld > 128 || ld % 16 != 0) return fail(ctx, PSI_ERR_INVALID_ARG, "ld must be a multiple of 16 in [n_q, 128]");
+    if (table_dtype != PSI_F32 && table_dtype != PSI_BF16)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "table_dtype must be PSI_F32 or PSI_BF16");
+    if (n > 0 && (!Q || !table)) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned(f->data, 16) || !aligned(Q, 16) || !aligned(table, 16))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "features, Q and table must be 16-byte aligned");
+    if (n == 0) return PSI_OK;
+    DeviceGuard g(ctx->device);
+    const char *why = nullptr;
+    cudaError_t e = psi::launch_logits(f->data, n, f->dim, Q, n_q, table, ld, table_dtype == PSI_BF16, ctx->status,
+                                       reinterpret_cast<cudaStream_t>(stream), &why);
+    if (why) return fail(ctx, PSI_ERR_CUDA, "psi_surfel_logits: %s", why);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_surfel_logits", e);
+}
+
 int psi_surfel_labels(psi_ctx *ctx, const psi_features *f, const float *centres, int64_t n, const void *Q, int n_q,
                       const float *q_mu, const float *q_cov, void *labels, int labels_dtype, int ld, psi_stream stream)
 {

@@ -204,6 +204,8 @@ cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, cons
 cudaError_t launch_regularisers(const psi_surfels &s, const int32_t *node_of, const float *node_mu, const float *node_n,
                                 int64_t n_nodes, float lambda_n, float w_geo, float w_iso, double *losses,
                                 const psi_grads &g, DevStatus *status, cudaStream_t st);
+cudaError_t launch_logits(const void *F, int64_t n, int D, const void *Q, int n_q, void *table, int ld, int out_bf16,
+                          DevStatus *status, cudaStream_t st, const char **why);
 cudaError_t launch_labels(const void *F, int64_t n, int D, const float *centres, const void *Q, int n_q,
                           const float *q_mu, const float *q_cov, void *labels, int ld, int out_bf16, DevStatus *status,
                           cudaStream_t st, const char **why);

@@ -114,7 +114,47 @@ struct LabelEpi {
     }
 };
 
+// The plain per-surfel query logits f_q^T f_g (no sigmoid, geometric factor
+// or softmax): composited with the Top-K weights they give, by linearity,
+// the decode's logits <F, q> of every pixel without forming F.
+struct LogitEpi {
+    int64_t n;
+    int n_q;
+    void *table; // [n, ld]
+    int ld;
+    int out_bf16;
+
+    struct Pre {};
+    __device__ __forceinline__ void prepare(unsigned char *, int) const {}
+    __device__ __forceinline__ Pre begin(int64_t) const { return Pre{}; }
+    __device__ __forceinline__ void end(int64_t g, uint32_t (&r)[kRowAccStride], Pre, bool fail, unsigned char *) const
+    {
+        if (g >= n || fail) return;
+        const float *A = reinterpret_cast<const float *>(r);
+        if (out_bf16) {
+            __nv_bfloat162 *row = reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(table) + g * ld);
+#pragma unroll
+            for (int q = 0; q < static_cast<int>(kRowAccStride); q += 2)
+                if (q < ld) row[q >> 1] = __floats2bfloat162_rn(q < n_q ? A[q] : 0.0f, q + 1 < n_q ? A[q + 1] : 0.0f);
+        } else {
+            float4 *row = reinterpret_cast<float4 *>(static_cast<float *>(table) + g * ld);
+#pragma unroll
+            for (int q = 0; q < static_cast<int>(kRowAccStride); q += 4)
+                if (q < ld)
+                    row[q >> 2] = make_float4(q < n_q ? A[q] : 0.0f, q + 1 < n_q ? A[q + 1] : 0.0f,
+                                              q + 2 < n_q ? A[q + 2] : 0.0f, q + 3 < n_q ? A[q + 3] : 0.0f);
+        }
+    }
+};
+
 } // namespace
+
+cudaError_t launch_logits(const void *F, int64_t n, int D, const void *Q, int n_q, void *table, int ld, int out_bf16,
+                          DevStatus *status, cudaStream_t st, const char **why)
+{
+    const LogitEpi epi{n, n_q, table, ld, out_bf16};
+    return launch_row_gemm(F, n, D, Q, n_q, 0, epi, status, st, why);
+}
 
 cudaError_t launch_labels(const void *F, int64_t n, int D, const float *centres, const void *Q, int n_q,
                           const float *q_mu, const float *q_cov, void *labels, int ld, int out_bf16, DevStatus *status,

@@ -246,6 +246,20 @@ def surfel_labels(ctx, scene: DeviceScene, queries, q_mu, q_cov, ld: int | None 
     return out
 
 
+def surfel_logits(ctx, scene: DeviceScene, queries, ld: int | None = None, dtype: int = psi.BF16,
+                  stream=None) -> torch.Tensor:
+    """Per-surfel query logits [N, ld] (f_q^T f_g, zero past Q): rendered
+    with label_scene and Renderer.render(argmax=True) they give the decoded
+    ids without a feature map."""
+    dev = scene.mu.device
+    nq = int(queries.shape[0])
+    ld = ld or ((nq + 15) // 16) * 16
+    Q = torch.as_tensor(queries).to(dev).to(torch.bfloat16).contiguous()
+    out = torch.empty(scene.n, ld, dtype=torch.bfloat16 if dtype == psi.BF16 else torch.float32, device=dev)
+    psi.psi_surfel_logits(ctx, scene.features_struct(), scene.n, Q, nq, out, dtype, ld, stream)
+    return out
+
+
 def label_scene(scene: DeviceScene, labels: torch.Tensor) -> DeviceScene:
     """The same surfels with the label table as their feature table, so a
     Renderer composites the label mixture of Eq. 8."""

@@ -100,6 +100,8 @@ def lib():
         L.psi_quat_frames_bwd.argtypes = [_P, _P, _i64, _P, _P, _P, _P]
         L.psi_surfel_regularisers.argtypes = [_P, ctypes.POINTER(PsiSurfels), _P, _P, _P, _i64, ctypes.c_float,
                                                ctypes.c_float, ctypes.c_float, _P, ctypes.POINTER(PsiGrads), _P]
+        L.psi_surfel_logits.argtypes = [_P, ctypes.POINTER(PsiFeatures), _i64, _P, ctypes.c_int, _P, ctypes.c_int,
+                                         ctypes.c_int, _P]
         L.psi_surfel_labels.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _i64, _P, ctypes.c_int, _P, _P, _P,
                                          ctypes.c_int, ctypes.c_int, _P]
         L.psi_decode_queries.argtypes = [_P, _P, _i64, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]
@@ -298,6 +300,11 @@ def psi_surfel_regularisers(ctx, s, node_of, node_mu, node_n, n_nodes, lambda_n,
     ctx.check(lib().psi_surfel_regularisers(ctx.handle, ctypes.byref(s), _ptr(node_of), _ptr(node_mu), _ptr(node_n),
                                             int(n_nodes), float(lambda_n), float(w_geo), float(w_iso), _ptr(losses),
                                             ctypes.byref(grads), _stream(stream)), "psi_surfel_regularisers")
+
+
+def psi_surfel_logits(ctx, feats, n, Q, n_q, table, table_dtype, ld, stream=None):
+    ctx.check(lib().psi_surfel_logits(ctx.handle, ctypes.byref(feats), int(n), _ptr(Q), int(n_q), _ptr(table),
+                                      int(table_dtype), int(ld), _stream(stream)), "psi_surfel_logits")
 
 
 def psi_surfel_labels(ctx, feats, centres, n, Q, n_q, q_mu, q_cov, labels, labels_dtype, ld, stream=None):

@@ -111,3 +111,48 @@ def test_rendered_identity(ctx):
         assert np.array_equal(gids[a:b][sure], own[sure])
         compared += int(ok.sum())
     assert compared > 0.5 * sum(c.width * c.height for c in cams)
+
+
+def test_fused_decode_through_logit_table(ctx):
+    """The decode fused into compositing: per-surfel logits f_q^T f_g rendered
+    with the Top-K weights and the fused argmax give the decode's ids (a6)
+    without a feature map; compared with the FP64 oracle's decode of the
+    oracle's own feature map and with the tensor-core decode of the GPU's F."""
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    w, scene, Qb, mu, cov = _case(100, 128, n=6000)
+    T = pl.surfel_logits(ctx, scene, Qb, dtype=psi.F32)
+    torch.cuda.synchronize()
+    f = pl.dequantize(scene.q, None, psi.BF16)
+    qf = Qb.float().numpy().astype(np.float64)
+    ref_tab = f @ qf.T
+    tab = T.cpu().numpy().astype(np.float64)
+    assert np.all(tab[:, 100:] == 0)
+    assert np.abs(tab[:, :100] - ref_tab).max() <= 1e-5 * max(1.0, np.abs(ref_tab).max())
+    cams = multi_cams()[:2]
+    o = orc.Opts(mode=orc.EXACT, top_k=8, opacity_radius=True)
+    ts = pl.label_scene(scene, T)
+    r = pl.make_renderer(ctx, ts, cams, opts_of(o), D=ts.D)
+    r.frame(ts, want_F=False)
+    r.render(ts, want_F=False, argmax=True)
+    ids_fused = r.argmax.cpu().numpy()
+    # the unfused path: features rendered to F (BF16), then the tensor-core decode
+    rf = pl.make_renderer(ctx, scene, cams, opts_of(o), D=128, F_dtype=psi.BF16)
+    rf.frame(scene)
+    ids_dec = torch.empty(rf.n_pix, dtype=torch.int32, device="cuda")
+    psi.psi_decode_queries(ctx, rf.F, rf.n_pix, 128, Qb.cuda(), 100, rf.T, ids_dec)
+    torch.cuda.synchronize()
+    assert ctx.status_fetch()[0] == 0
+    ids_dec = ids_dec.cpu().numpy()
+    compared = 0
+    for v, cam in enumerate(cams):
+        a, b = int(r.pix_base[v]), int(r.pix_base[v + 1])
+        ref = orc.render(w.surfels, cam, o, feat=f)
+        rid, L, gap = orc.decode(ref["F"], qf, ref["T"])
+        st, ic, nt = flags(ref, cam)
+        ok = ~(st | ic | nt) & ((gap > 1e-3 * (np.abs(L).max(1) + 1e-6)) | (rid == -1))
+        assert np.array_equal(ids_fused[a:b][ok], rid[ok])
+        # the unfused decode rounds F to BF16 first: equal wherever the margin is clear
+        clear = ok & (gap > 2e-2 * (np.abs(L).max(1) + 1e-6))
+        assert np.array_equal(ids_fused[a:b][clear], ids_dec[a:b][clear])
+        compared += int(ok.sum())
+    assert compared > 0.5 * sum(c.width * c.height for c in cams)
