@@ -628,14 +628,28 @@ def run_psi(args):
             out[name] = {"render_ms": float(np.median(rt)), "frame_ms": float(np.median(ft)),
                          "table": f"[{scene.n}, {ts.D}] BF16"}
             del rl, ts
+        # the unfused forward on the same frames, timed the same way: the
+        # feature map composited and written, then the tensor-core decode
+        ut = []
+        for k in range(args.label_frames + 1):
+            r.set_cameras([cams[fidx(k)]])
+            r.project(scene)
+            r.intersect()
+            r.sort()
+            ev[1].record()
+            r.render(scene)
+            psi.psi_decode_queries(ctx, r.F, r.n_pix, D, Qd, nq, r.T, ids)
+            ev[2].record()
+            torch.cuda.synchronize()
+            if k > 0:
+                ut.append(ev[1].elapsed_time(ev[2]))
+        out["unfused_render_plus_decode_ms"] = float(np.median(ut))
         st, _ = ctx.status_fetch()
         assert st == 0, f"device status {st}"
         lab_bytes = scene.n * (2.0 * D + 12.0 + 2.0 * Lt.shape[1])  # features + centres read, table written
         labels = {"labels_table_ms": float(lab_ms), "logits_table_ms": float(logit_ms), "queries": nq,
                   "labels_table_hbm_frac": lab_bytes / (lab_ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
                   **out,
-                  "unfused_render_plus_decode_ms": float(mean_stage[names.index("render_fwd")] +
-                                                         mean_stage[names.index("decode")]),
                   "form": "tables once per map on the tensor cores (labels: sigmoid x query-Gaussian density ratio, "
                           "softmax; logits: f_q^T f_g); per frame: project+intersect+sort (eager) and the compositing "
                           "of the table (K=8, EXACT) with the fused per-pixel argmax (render_ms)"}
