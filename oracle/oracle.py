@@ -396,3 +396,64 @@ def quat_frames_grad(q, g_tu, g_tv):
     gq_hat = np.stack([np.sum(gu * du[k], 1) + np.sum(gv * dv[k], 1) for k in range(4)], axis=1)
     # through q / |q|
     return (gq_hat - np.sum(gq_hat * u, axis=1, keepdims=True) * u) / nq
+
+
+CHI2_99_2D = -2.0 * np.log(0.01)  # chi-square quantile of 2 DOF at 99 %: the 99 % disc has radius 3.035 sigma
+
+
+def attn_pos_enc(mu, C: int):
+    """Positional encoding psi(mu) [N, C] of surfel centres (Sec. 4.1): channel
+    c encodes axis c mod 3 with sin (t = c // 3 even) or cos (t odd) at the
+    frequency w_k = 10000^(-6k/C), k = t // 2 (a sinusoidal encoding per
+    axis; the paper names psi without fixing it)."""
+    mu = np.asarray(mu, np.float64)
+    c = np.arange(C)
+    a = c % 3
+    t = c // 3
+    w = np.exp(-np.log(10000.0) * 6.0 * (t // 2) / C)
+    arg = mu[:, a] * w[None, :]
+    return np.where((t % 2 == 0)[None, :], np.sin(arg), np.cos(arg))
+
+
+def frustum_active(s, cam, z_near: float):
+    """Surfels whose 99 % confidence disc (radius sqrt(chi2_2(0.99)) max(s_u,
+    s_v) around mu, bounded by its sphere) meets the view frustum: the
+    sphere is not wholly behind the near plane or outside a side plane of
+    the image rectangle. Returns (active [N] bool, margin [N]: the smallest
+    signed plane distance plus the radius, in metres)."""
+    mu = np.asarray(s.mu, np.float64)
+    sc = np.asarray(s.scale, np.float64)
+    R, t = np.asarray(cam.R, np.float64), np.asarray(cam.t, np.float64)
+    x = mu @ R.T + t
+    r = np.sqrt(CHI2_99_2D) * sc.max(axis=1)
+    fx, fy, cx, cy, W, H = cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height
+    planes = [np.array([0.0, 0.0, 1.0, -z_near]),           # z >= z_near
+              np.array([fx, 0.0, cx, 0.0]),                  # x / z >= -cx / fx
+              np.array([-fx, 0.0, W - cx, 0.0]),             # x / z <= (W - cx) / fx
+              np.array([0.0, fy, cy, 0.0]),                  # y / z >= -cy / fy
+              np.array([0.0, -fy, H - cy, 0.0])]             # y / z <= (H - cy) / fy
+    d = np.stack([(x @ p[:3] + p[3]) / np.linalg.norm(p[:3]) for p in planes], axis=1)
+    margin = (d + r[:, None]).min(axis=1)
+    return margin >= 0.0, margin
+
+
+def frustum_attention(s, feat, cam, z_near, Q, WQ, WK, WV, plant: int = 0):
+    """Frustum-constrained cross-attention (Sec. 4.1), FP64: over the active
+    surfels j, K_j = f_j + psi(mu_j), V_j = f_j,
+      e_ij = (Q_i W_Q)(K_j W_K)^T / sqrt(d),  Q'_i = softmax_j(e_ij) (V_j W_V).
+    feat [N, C] (stored values), Q [n_q, C], W_Q/W_K/W_V [C, d].
+    Returns (Q' [n_q, d], active [N], margin [N])."""
+    f = np.asarray(feat, np.float64)
+    active, margin = frustum_active(s, cam, z_near)
+    C = f.shape[1]
+    K = f + attn_pos_enc(s.mu, C)
+    q = np.asarray(Q, np.float64) @ np.asarray(WQ, np.float64)
+    k = K[active] @ np.asarray(WK, np.float64)
+    v = f[active] @ np.asarray(WV, np.float64)
+    d = q.shape[1]
+    e = q @ k.T if plant == 1 else q @ k.T / np.sqrt(d)
+    axis = 0 if plant == 2 else 1
+    e = e - e.max(axis=axis, keepdims=True)
+    P = np.exp(e)
+    P /= P.sum(axis=axis, keepdims=True)
+    return P @ v, active, margin

@@ -270,3 +270,88 @@ def test_quat_frames_gradient_central_differences():
 
 def test_quat_frames_planted_mistake_is_caught():
     assert _frames_vs_scipy(plant=1) > 1e-3
+
+
+# ---------------------------------------------------------------- frustum cross-attention (Sec. 4.1)
+def _attn_case(n=300, C=16, d=8, nq=5, seed=6):
+    w = sg.dense_box(n=n, d=C)
+    rng = np.random.default_rng(seed)
+    W = [rng.normal(size=(C, d)) / np.sqrt(C) for _ in range(3)]
+    Q = rng.normal(size=(nq, C))
+    return w, w.features.astype(np.float64), Q, W
+
+
+def test_attention_closed_forms():
+    w, f, Q, (WQ, WK, WV) = _attn_case()
+    cam = w.cameras[0]
+    out, act, _ = orc.frustum_attention(w.surfels, f, cam, 0.2, Q, WQ, WK, WV)
+    assert act.sum() > 10 and (~act).sum() > 0
+    # W_K = 0: every score equal, the update is the mean value of the active set
+    out0, _, _ = orc.frustum_attention(w.surfels, f, cam, 0.2, Q, WQ, np.zeros_like(WK), WV)
+    assert np.allclose(out0, np.repeat((f[act] @ WV).mean(0, keepdims=True), len(Q), 0), atol=1e-12)
+    # one active surfel: every query takes its value
+    one = sg.Surfels(*(np.asarray(getattr(w.surfels, k))[act][:1] for k in ("mu", "tu", "tv", "scale", "opacity", "rgb")))
+    o1, a1, _ = orc.frustum_attention(one, f[act][:1], cam, 0.2, Q, WQ, WK, WV)
+    assert a1.all() and np.allclose(o1, np.repeat(f[act][:1] @ WV, len(Q), 0), atol=1e-12)
+
+
+def test_attention_pos_enc_values():
+    P = orc.attn_pos_enc(np.zeros((1, 3)), 12)
+    # t = c // 3: even -> sin(0) = 0, odd -> cos(0) = 1
+    assert np.array_equal(P[0], [0, 0, 0, 1, 1, 1, 0, 0, 0, 1, 1, 1])
+    x = np.array([[0.7, -1.2, 2.5]])
+    P = orc.attn_pos_enc(x, 12)
+    assert np.isclose(P[0, 0], np.sin(0.7)) and np.isclose(P[0, 4], np.cos(-1.2))
+    w2 = np.exp(-np.log(10000.0) * 6.0 / 12.0)  # k = 1 from channel 6 on
+    assert np.isclose(P[0, 8], np.sin(2.5 * w2)) and np.isclose(P[0, 10], np.cos(-1.2 * w2))
+
+
+def test_frustum_test_is_conservative_by_sampling():
+    """Brute force: sample each sphere; a surfel with any sample in front of
+    the near plane projecting inside the image must be active."""
+    w = sg.dense_box(n=400)
+    cam = w.cameras[0]
+    act, _ = orc.frustum_active(w.surfels, cam, 0.2)
+    rng = np.random.default_rng(0)
+    dirs = rng.normal(size=(400, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    rad = np.sqrt(orc.CHI2_99_2D) * np.asarray(w.surfels.scale, np.float64).max(1)
+    mu = np.asarray(w.surfels.mu, np.float64)
+    R, t = np.asarray(cam.R, np.float64), np.asarray(cam.t, np.float64)
+    for i in range(len(mu)):
+        pts = mu[i] + rad[i] * dirs * rng.uniform(0, 1, size=(400, 1))
+        x = pts @ R.T + t
+        ok = x[:, 2] > 0.2
+        u = cam.fx * x[ok, 0] / x[ok, 2] + cam.cx
+        v = cam.fy * x[ok, 1] / x[ok, 2] + cam.cy
+        inside = (u >= 0) & (u <= cam.width) & (v >= 0) & (v <= cam.height)
+        if inside.any():
+            assert act[i], i
+
+
+def _two_surfel_closed_form(plant=0):
+    """Two active surfels whose scores differ by exactly sqrt(d) ln 3: the
+    softmax weights are 3/4 and 1/4, so Q' = 3/4 v_1 + 1/4 v_2 (W = I)."""
+    w = sg.dense_box(n=400, d=4)
+    cam = w.cameras[0]
+    act, _ = orc.frustum_active(w.surfels, cam, 0.2)
+    idx = np.nonzero(act)[0][:2]
+    two = sg.Surfels(*(np.asarray(getattr(w.surfels, k))[idx] for k in ("mu", "tu", "tv", "scale", "opacity", "rgb")))
+    C = d = 4
+    I = np.eye(C)
+    q = np.array([[1.0, 0.0, 0.0, 0.0]])
+    K_want = np.array([[np.sqrt(d) * np.log(3.0), 0.3, -0.2, 0.5], [0.0, 0.1, 0.4, -0.6]])
+    f = K_want - orc.attn_pos_enc(two.mu, C)  # so that K = f + psi(mu) = K_want
+    out, a2, _ = orc.frustum_attention(two, f, cam, 0.2, q, I, I, I, plant=plant)
+    assert a2.all()
+    return np.abs(out - (0.75 * f[0] + 0.25 * f[1])[None]).max()
+
+
+def test_attention_two_surfel_closed_form():
+    assert _two_surfel_closed_form() < 1e-12
+
+
+@pytest.mark.parametrize("plant", [1, 2])
+def test_attention_planted_mistake_is_caught(plant):
+    # missing 1/sqrt(d); softmax over queries instead of surfels
+    assert _two_surfel_closed_form(plant) > 1e-3
