@@ -293,6 +293,25 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
 int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
                        int32_t *ids, void *logits, psi_stream stream);
 
+/* ---- frustum-constrained cross-attention (Sec. 4.1), forward -------------
+ * Over the surfels j whose 99 % confidence disc meets the view frustum of
+ * `cam` (the disc's bounding sphere, radius sqrt(chi2_2(0.99)) max(s_u, s_v),
+ * against the near plane z_near and the image rectangle's four side planes):
+ *   K_j = f_j + psi(mu_j), V_j = f_j,
+ *   Q'_i = softmax_j((Q_i W_Q)(K_j W_K)^T / sqrt(d)) (V_j W_V).
+ * psi: channel c encodes axis c mod 3 with sin (t = c/3 even) or cos (t odd)
+ * at frequency 10000^(-6k/C), k = t/2 (the paper leaves psi open).
+ * Products are FP32 cuBLAS GEMMs (the context creates its handle on first
+ * use) over all n surfels with the inactive ones masked in the softmax (no
+ * host synchronisation). An empty active set gives Q' = 0.
+ *  f: the feature table (any dtype, dim C); Q: [n_q, C]; W_Q, W_K, W_V:
+ *  [C, d]; out: [n_q, d]; all float32 row-major, device.
+ *  workspace: psi_attention_workspace_size(n, C, d, n_q) bytes. */
+int psi_attention_workspace_size(int64_t n, int C, int d, int n_q, size_t *bytes);
+int psi_frustum_attention(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const psi_camera *cam,
+                          float z_near, const float *Q, int n_q, const float *W_Q, const float *W_K, const float *W_V,
+                          int d, float *out, void *workspace, size_t workspace_bytes, psi_stream stream);
+
 /* ---- quaternion-parameterised tangent frames (2DGS form) ------------------
  * The paper's surfels follow 2DGS (Sec. 3.1), whose tangent frame is a
  * rotation R(q / |q|) of a quaternion q = (w, x, y, z): t_u, t_v are R's first

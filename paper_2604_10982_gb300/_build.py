@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "project.cu", "intersect.cu", "sort.cu", "render_fwd.cu", "render_bwd.cu", "feat_bwd.cu",
-           "decode.cu", "labels.cu", "regularisers.cu", "frames.cu"]
+           "decode.cu", "labels.cu", "regularisers.cu", "frames.cu", "attention.cu"]
 # the binning path takes integer decisions in float32 with an explicit
 # operation order: forbid FMA contraction there as well
 NO_FMAD = {"project.cu", "intersect.cu"}
@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lcublas"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

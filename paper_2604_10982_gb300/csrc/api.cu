@@ -4,12 +4,15 @@
 #include <cstring>
 #include <new>
 
+#include <cublas_v2.h>
+
 #include "common.cuh"
 
 struct psi_ctx {
     int device;
     psi::DevStatus *status;
     char err[512];
+    void *cublas; // created on first use by psi_frustum_attention
     // armed kernel-timing events per psi_kernel_id: [id][0] begin, [id][1] end
     cudaEvent_t time_ev[3][2];
 };
@@ -140,6 +143,7 @@ void psi_ctx_destroy(psi_ctx *ctx)
     {
         DeviceGuard g(ctx->device);
         if (ctx->status) cudaFree(ctx->status);
+        if (ctx->cublas) cublasDestroy(static_cast<cublasHandle_t>(ctx->cublas));
     }
     delete ctx;
 }
@@ -395,6 +399,44 @@ int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const 
                                        reinterpret_cast<cudaStream_t>(stream), &why);
     if (why) return fail(ctx, PSI_ERR_CUDA, "psi_decode_queries: %s", why);
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_decode_queries", e);
+}
+
+int psi_attention_workspace_size(int64_t n, int C, int d, int n_q, size_t *bytes)
+{
+    if (!bytes || n < 0 || C < 1 || d < 1 || n_q < 1) return PSI_ERR_INVALID_ARG;
+    *bytes = psi::attention_workspace_bytes(n, C, d, n_q);
+    return PSI_OK;
+}
+
+int psi_frustum_attention(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const psi_camera *cam,
+                          float z_near, const float *Q, int n_q, const float *W_Q, const float *W_K, const float *W_V,
+                          int d, float *out, void *workspace, size_t workspace_bytes, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = check_surfels(ctx, s))) return rc;
+    psi::FeatView fv;
+    if ((rc = check_feat(ctx, f, fv))) return rc;
+    if (!fv.data) return fail(ctx, PSI_ERR_INVALID_ARG, "features are required");
+    if (!cam || cam->width < 1 || cam->height < 1) return fail(ctx, PSI_ERR_INVALID_ARG, "bad camera");
+    if (s->n >= (int64_t(1) << 31) || static_cast<int64_t>(n_q) * s->n >= (int64_t(1) << 40))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "too many surfels");
+    if (n_q < 1 || d < 1 || !Q || !W_Q || !W_K || !W_V || !out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = psi::attention_workspace_bytes(s->n, fv.dim, d, n_q);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
+    if (s->n == 0) return fail(ctx, PSI_ERR_INVALID_ARG, "no surfels to attend to");
+    DeviceGuard g(ctx->device);
+    if (!ctx->cublas) {
+        cublasHandle_t h = nullptr;
+        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return fail(ctx, PSI_ERR_CUDA, "cublasCreate failed");
+        ctx->cublas = h;
+    }
+    const char *why = nullptr;
+    cudaError_t e = psi::launch_attention(ctx->cublas, *s, fv.data, fv.scale, fv.dtype, fv.dim, *cam, z_near, Q, n_q,
+                                          W_Q, W_K, W_V, d, out, workspace, reinterpret_cast<cudaStream_t>(stream), &why);
+    if (why) return fail(ctx, PSI_ERR_CUDA, "psi_frustum_attention: %s", why);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_frustum_attention", e);
 }
 
 int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream)

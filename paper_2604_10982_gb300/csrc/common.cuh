@@ -198,6 +198,11 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
                               DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2]);
 
+size_t attention_workspace_bytes(int64_t n, int C, int d, int n_q);
+cudaError_t launch_attention(void *cublas, const psi_surfels &s, const void *feat, const float *fscale, int dtype, int C,
+                             const psi_camera &cam, float z_near, const float *Q, int n_q, const float *WQ,
+                             const float *WK, const float *WV, int d, float *out, void *ws, cudaStream_t st,
+                             const char **why);
 cudaError_t launch_frames(const float *q, int64_t n, float *tu, float *tv, cudaStream_t st);
 cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
                               cudaStream_t st);

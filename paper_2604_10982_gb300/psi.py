@@ -96,6 +96,10 @@ def lib():
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.psi_attention_workspace_size.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(sz)]
+        L.psi_frustum_attention.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures),
+                                            ctypes.POINTER(PsiCamera), ctypes.c_float, _P, ctypes.c_int, _P, _P, _P,
+                                            ctypes.c_int, _P, _P, sz, _P]
         L.psi_quat_frames.argtypes = [_P, _P, _i64, _P, _P, _P]
         L.psi_quat_frames_bwd.argtypes = [_P, _P, _i64, _P, _P, _P, _P]
         L.psi_surfel_regularisers.argtypes = [_P, ctypes.POINTER(PsiSurfels), _P, _P, _P, _i64, ctypes.c_float,
@@ -283,6 +287,22 @@ def psi_ctx_time_kernel(ctx, kernel, ev_begin, ev_end):
     b = None if ev_begin is None else ctypes.c_void_p(ev_begin.cuda_event)
     e = None if ev_end is None else ctypes.c_void_p(ev_end.cuda_event)
     ctx.check(lib().psi_ctx_time_kernel(ctx.handle, int(kernel), b, e), "psi_ctx_time_kernel")
+
+
+def attention_workspace_size(n, C, d, n_q):
+    b = ctypes.c_size_t(0)
+    rc = lib().psi_attention_workspace_size(int(n), int(C), int(d), int(n_q), ctypes.byref(b))
+    if rc != PSI_OK:
+        raise PsiError(rc, "psi_attention_workspace_size")
+    return int(b.value)
+
+
+def psi_frustum_attention(ctx, s, feats, cam, z_near, Q, n_q, WQ, WK, WV, d, out, workspace, stream=None):
+    """cam: one PsiCamera (e.g. cameras([c])[0])."""
+    ctx.check(lib().psi_frustum_attention(ctx.handle, ctypes.byref(s), ctypes.byref(feats), ctypes.byref(cam),
+                                          float(z_near), _ptr(Q), int(n_q), _ptr(WQ), _ptr(WK), _ptr(WV), int(d),
+                                          _ptr(out), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                          _stream(stream)), "psi_frustum_attention")
 
 
 def psi_quat_frames(ctx, q, n, tu, tv, stream=None):

@@ -1,0 +1,68 @@
+"""Frustum-constrained cross-attention (Sec. 4.1) against the oracle (needs a GPU)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc
+from paper_2604_10982_gb300 import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_10982_gb300 import psi
+    return psi.Context(0)
+
+
+def _run(ctx, w, cam, dtype, nq, d, seed=1):
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    C = w.features.shape[1]
+    rng = np.random.default_rng(seed)
+    W = [(rng.normal(size=(C, d)) / np.sqrt(C)).astype(np.float32) for _ in range(3)]
+    Q = rng.normal(size=(nq, C)).astype(np.float32)
+    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=dtype)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.empty(nq, d, device="cuda")
+    ws = torch.empty(psi.attention_workspace_size(scene.n, C, d, nq), dtype=torch.uint8, device="cuda")
+    camarr = psi.cameras([cam])
+    psi.psi_frustum_attention(ctx, scene.surfels_struct(), scene.features_struct(), camarr[0], 0.2, dev(Q), nq,
+                              dev(W[0]), dev(W[1]), dev(W[2]), d, out, ws)
+    torch.cuda.synchronize()
+    assert ctx.status_fetch()[0] == 0
+    feat = pl.dequantize(scene.q, scene.qscale, dtype) if dtype != psi.F32 else w.features.astype(np.float64)
+    ref, act, margin = orc.frustum_attention(w.surfels, feat, cam, 0.2, Q.astype(np.float64), *W)
+    return out.cpu().numpy().astype(np.float64), ref, act, margin
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_attention_matches_oracle(ctx, dtype):
+    from paper_2604_10982_gb300 import psi
+    w = sg.dense_box(n=5000, d=64)
+    cam = w.cameras[0]
+    got, ref, act, margin = _run(ctx, w, cam, psi.F32 if dtype == "f32" else psi.BF16, 7, 32)
+    # the float32 frustum test agrees with the FP64 one away from the planes
+    assert np.min(np.abs(margin)) > 1e-4, "a surfel sits on a frustum plane: pick another seed"
+    assert 0 < act.sum() < len(act)
+    assert np.abs(got - ref).max() <= 2e-4 * max(1.0, np.abs(ref).max())
+
+
+def test_attention_street_view(ctx):
+    """200k surfels of the street, one 720p view: most surfels outside the
+    frustum. Surfels within 1e-4 m of a frustum plane (where float32 and FP64
+    may decide differently) are left out of the input, by the oracle's margin."""
+    import dataclasses
+    from paper_2604_10982_gb300 import psi
+    w = sg.street()
+    cam = w.cameras[0]
+    _, margin = orc.frustum_active(w.surfels, cam, 0.2)
+    keep = np.abs(margin) >= 1e-4
+    s = sg.Surfels(*(np.ascontiguousarray(np.asarray(getattr(w.surfels, k))[keep])
+                     for k in ("mu", "tu", "tv", "scale", "opacity", "rgb")))
+    w2 = dataclasses.replace(w, surfels=s, features=np.ascontiguousarray(w.features[keep]))
+    got, ref, act, _ = _run(ctx, w2, cam, psi.F32, 100, 64)
+    assert act.mean() < 0.9 and keep.mean() > 0.999
+    assert np.abs(got - ref).max() <= 5e-4 * max(1.0, np.abs(ref).max())
