@@ -457,3 +457,49 @@ def frustum_attention(s, feat, cam, z_near, Q, WQ, WK, WV, plant: int = 0):
     P = np.exp(e)
     P /= P.sum(axis=axis, keepdims=True)
     return P @ v, active, margin
+
+
+def frustum_attention_grad(s, feat, cam, z_near, Q, WQ, WK, WV, G):
+    """Gradients of L = <G, Q'> through frustum_attention (Sec. 4.1), FP64,
+    written by hand from the chain rule:
+      dP = G v^T, dv = P^T G, de = P (dP - rowsum(P dP)), dq = de k / sqrt(d),
+      dk = de^T q / sqrt(d), dQ = dq W_Q^T, dW_Q = Q^T dq, dK = dk W_K^T,
+      dW_K = K^T dk, dV = dv W_V^T, dW_V = V^T dv,
+      df = dK + dV, dmu_a = sum_c dK_c dpsi_c/dmu_a (active surfels only).
+    Returns a dict with Q, WQ, WK, WV, feat [N, C], mu [N, 3]."""
+    f = np.asarray(feat, np.float64)
+    Q = np.asarray(Q, np.float64)
+    WQ, WK, WV = (np.asarray(x, np.float64) for x in (WQ, WK, WV))
+    G = np.asarray(G, np.float64)
+    active, _ = frustum_active(s, cam, z_near)
+    C = f.shape[1]
+    mu = np.asarray(s.mu, np.float64)
+    K = f + attn_pos_enc(mu, C)
+    Ka, Va = K[active], f[active]
+    q, k, v = Q @ WQ, Ka @ WK, Va @ WV
+    d = q.shape[1]
+    e = q @ k.T / np.sqrt(d)
+    P = np.exp(e - e.max(axis=1, keepdims=True))
+    P /= P.sum(axis=1, keepdims=True)
+    dP = G @ v.T
+    dv = P.T @ G
+    de = P * (dP - np.sum(P * dP, axis=1, keepdims=True))
+    dq = de @ k / np.sqrt(d)
+    dk = de.T @ q / np.sqrt(d)
+    out = {"Q": dq @ WQ.T, "WQ": Q.T @ dq, "WK": Ka.T @ dk, "WV": Va.T @ dv}
+    dK = np.zeros_like(f)
+    dV = np.zeros_like(f)
+    dK[active] = dk @ WK.T
+    dV[active] = dv @ WV.T
+    out["feat"] = dK + dV
+    # d psi / d mu: channel c depends on axis c mod 3 only
+    c = np.arange(C)
+    a, t = c % 3, c // 3
+    w = np.exp(-np.log(10000.0) * 6.0 * (t // 2) / C)
+    arg = mu[:, a] * w[None, :]
+    dpsi = np.where((t % 2 == 0)[None, :], np.cos(arg), -np.sin(arg)) * w[None, :]
+    dmu = np.zeros_like(mu)
+    for ax in range(3):
+        dmu[:, ax] = np.sum((dK * dpsi)[:, a == ax], axis=1)
+    out["mu"] = dmu
+    return out

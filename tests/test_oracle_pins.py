@@ -355,3 +355,30 @@ def test_attention_two_surfel_closed_form():
 def test_attention_planted_mistake_is_caught(plant):
     # missing 1/sqrt(d); softmax over queries instead of surfels
     assert _two_surfel_closed_form(plant) > 1e-3
+
+
+def test_attention_gradients_central_differences():
+    w, f, Q, (WQ, WK, WV) = _attn_case(n=120, C=12, d=6, nq=4)
+    cam = w.cameras[0]
+    rng = np.random.default_rng(2)
+    G = rng.normal(size=(4, 6))
+    g = orc.frustum_attention_grad(w.surfels, f, cam, 0.2, Q, WQ, WK, WV, G)
+    act, margin = orc.frustum_active(w.surfels, cam, 0.2)
+    mu0 = np.asarray(w.surfels.mu, np.float64)
+
+    def L(Q_=Q, WQ_=WQ, WK_=WK, WV_=WV, f_=f, mu_=mu0):
+        s = sg.Surfels(mu=mu_, tu=w.surfels.tu, tv=w.surfels.tv, scale=w.surfels.scale, opacity=w.surfels.opacity,
+                       rgb=w.surfels.rgb)
+        return float(np.sum(orc.frustum_attention(s, f_, cam, 0.2, Q_, WQ_, WK_, WV_)[0] * G))
+
+    h = 1e-6
+    for key, base in (("Q", Q), ("WQ", WQ), ("WK", WK), ("WV", WV), ("feat", f), ("mu", mu0)):
+        for idx in [(0, 0), (1, 2), (base.shape[0] - 1, base.shape[1] - 1), (base.shape[0] // 2, 1)]:
+            if key in ("feat", "mu") and (not act[idx[0]] or abs(margin[idx[0]]) < 1e-3):
+                continue  # inactive surfels carry no gradient; avoid moving one across a plane
+            p, m = base.copy(), base.copy()
+            p[idx] += h
+            m[idx] -= h
+            arg = {"Q": "Q_", "WQ": "WQ_", "WK": "WK_", "WV": "WV_", "feat": "f_", "mu": "mu_"}[key]
+            fd = (L(**{arg: p}) - L(**{arg: m})) / (2 * h)
+            assert abs(fd - g[key][idx]) < 1e-6 * max(1.0, abs(fd)), (key, idx, fd, g[key][idx])
