@@ -311,6 +311,15 @@ int psi_attention_workspace_size(int64_t n, int C, int d, int n_q, size_t *bytes
 int psi_frustum_attention(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const psi_camera *cam,
                           float z_near, const float *Q, int n_q, const float *W_Q, const float *W_K, const float *W_V,
                           int d, float *out, void *workspace, size_t workspace_bytes, psi_stream stream);
+/* Its adjoint for L = <g_out, Q'> ([n_q, d]), reusing the workspace exactly as
+ * the preceding psi_frustum_attention left it (same surfels, features and
+ * weights): writes g_Q [n_q, C], g_WQ / g_WK / g_WV [C, d] (each may be
+ * NULL) and ADDS dL/df (grads->feat, w.r.t. the dequantised values) and
+ * dL/dmu through psi (grads->mu) for the active surfels. */
+int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const float *Q, int n_q,
+                              const float *W_Q, const float *W_K, const float *W_V, int d, const float *g_out,
+                              float *g_Q, float *g_WQ, float *g_WK, float *g_WV, const psi_grads *grads,
+                              void *workspace, size_t workspace_bytes, psi_stream stream);
 
 /* ---- quaternion-parameterised tangent frames (2DGS form) ------------------
  * The paper's surfels follow 2DGS (Sec. 3.1), whose tangent frame is a

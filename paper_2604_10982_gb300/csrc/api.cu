@@ -439,6 +439,32 @@ int psi_frustum_attention(psi_ctx *ctx, const psi_surfels *s, const psi_features
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_frustum_attention", e);
 }
 
+int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const float *Q, int n_q,
+                              const float *W_Q, const float *W_K, const float *W_V, int d, const float *g_out,
+                              float *g_Q, float *g_WQ, float *g_WK, float *g_WV, const psi_grads *grads,
+                              void *workspace, size_t workspace_bytes, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = check_surfels(ctx, s))) return rc;
+    psi::FeatView fv;
+    if ((rc = check_feat(ctx, f, fv))) return rc;
+    if (!fv.data || s->n == 0) return fail(ctx, PSI_ERR_INVALID_ARG, "features and surfels are required");
+    if (n_q < 1 || d < 1 || !Q || !W_Q || !W_K || !W_V || !g_out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = psi::attention_workspace_bytes(s->n, fv.dim, d, n_q);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
+    if (!ctx->cublas) return fail(ctx, PSI_ERR_INVALID_ARG, "run psi_frustum_attention first");
+    DeviceGuard g(ctx->device);
+    const char *why = nullptr;
+    cudaError_t e = psi::launch_attention_bwd(ctx->cublas, s->n, fv.dim, n_q, Q, W_Q, W_K, W_V, d, g_out, g_Q, g_WQ,
+                                              g_WK, g_WV, s->mu, grads ? grads->feat : nullptr,
+                                              grads ? grads->mu : nullptr, workspace,
+                                              reinterpret_cast<cudaStream_t>(stream), &why);
+    if (why) return fail(ctx, PSI_ERR_CUDA, "psi_frustum_attention_bwd: %s", why);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_frustum_attention_bwd", e);
+}
+
 int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream)
 {
     if (!ctx) return PSI_ERR_INVALID_ARG;

@@ -7,6 +7,9 @@
 //     e_ij = (Q_i W_Q)(K_j W_K)^T / sqrt(d),  Q'_i = softmax_j(e_ij) (V_j W_V)
 // psi: channel c encodes axis c mod 3 with sin (t = c / 3 even) or cos (t odd)
 // at frequency 10000^(-6k/C), k = t / 2.
+// Backward (L = <G, Q'>): dP = G v^T, dv = P^T G, dE = P (dP - rowsum(P dP))
+// / sqrt(d), dq = dE k, dk = dE^T q, and the projections' gradients; dK and
+// dV land on the surfels' feature gradient and dK, through psi, on mu.
 // A kernel builds K, V (float32 rows) and the active mask for every surfel;
 // the four products run as FP32 cuBLAS GEMMs (plain library GEMMs) over all
 // surfels; the row softmax masks inactive surfels (weight 0) and applies the
@@ -131,37 +134,127 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int m, int n, int k, const float *A, co
     return cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n, m, k, &one, B, n, A, k, &zero, C, n);
 }
 
+// row-major C[m x n] = A[m x k] B[n x k]^T
+cublasStatus_t gemm_nt(cublasHandle_t h, int m, int n, int k, const float *A, const float *B, float *C)
+{
+    const float one = 1.0f, zero = 0.0f;
+    return cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, n, m, k, &one, B, k, A, k, &zero, C, n);
+}
+
+// row-major C[m x n] = A[k x m]^T B[k x n]
+cublasStatus_t gemm_tn(cublasHandle_t h, int m, int n, int k, const float *A, const float *B, float *C)
+{
+    const float one = 1.0f, zero = 0.0f;
+    return cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, n, m, k, &one, B, n, A, m, &zero, C, n);
+}
+
+// One CTA per query row: dE = P (dP - sum_j P dP) * scale, in place over dP.
+__global__ void __launch_bounds__(1024) attn_softmax_bwd_kernel(const float *P, float *dP, int64_t N, float scale)
+{
+    const float *p = P + static_cast<int64_t>(blockIdx.x) * N;
+    float *g = dP + static_cast<int64_t>(blockIdx.x) * N;
+    __shared__ float red[32];
+    float s = 0.0f;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) s += p[j] * g[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (threadIdx.x == 0) red[0] = x;
+    }
+    __syncthreads();
+    const float rs = red[0];
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) g[j] = p[j] * (g[j] - rs) * scale;
+}
+
+// One warp per active surfel: feature gradient dK + dV, centre gradient
+// sum_c dK_c dpsi_c/dmu (added to the gradient buffers).
+__global__ void __launch_bounds__(256) attn_scatter_kernel(const float *dK, const float *dV, const uint8_t *active,
+                                                           const float *mu, int64_t n, int C, float *g_feat,
+                                                           float *g_mu)
+{
+    const int64_t j = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n || !active[j]) return;
+    float gm[3] = {0.f, 0.f, 0.f};
+    const float m[3] = {mu[3 * j], mu[3 * j + 1], mu[3 * j + 2]};
+    const float lnb = 9.21034037198f; // ln 10000
+    for (int c = lane; c < C; c += 32) {
+        const float k = dK[j * C + c];
+        if (g_feat) g_feat[j * C + c] += k + dV[j * C + c];
+        const int t = c / 3, axis = c - 3 * t;
+        const float w = __expf(-lnb * 6.0f * static_cast<float>(t >> 1) / static_cast<float>(C));
+        const float arg = m[axis] * w;
+        const float dpsi = ((t & 1) ? -sinf(arg) : cosf(arg)) * w;
+        gm[axis] += k * dpsi;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm[a] += __shfl_xor_sync(0xffffffffu, gm[a], o);
+    if (lane == 0 && g_mu) {
+        g_mu[3 * j] += gm[0];
+        g_mu[3 * j + 1] += gm[1];
+        g_mu[3 * j + 2] += gm[2];
+    }
+}
+
 } // namespace
 
+// forward: K, V [N, C]; k, v [N, d]; q [n_q, d]; S -> P [n_q, N]; mask [N];
+// backward scratch: dP -> dE [n_q, N]; dq [n_q, d]; dk, dv [N, d]
 size_t attention_workspace_bytes(int64_t n, int C, int d, int n_q)
 {
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t N = static_cast<size_t>(std::max<int64_t>(n, 1));
-    return up(N * C * 4) * 2 + up(N * d * 4) * 2 + up(static_cast<size_t>(n_q) * d * 4) +
-           up(static_cast<size_t>(n_q) * N * 4) + up(N);
+    const size_t fwd = up(N * C * 4) * 2 + up(N * d * 4) * 2 + up(static_cast<size_t>(n_q) * d * 4) +
+                       up(static_cast<size_t>(n_q) * N * 4) + up(N);
+    return fwd + up(static_cast<size_t>(n_q) * N * 4) + up(static_cast<size_t>(n_q) * d * 4) + up(N * d * 4) * 2;
 }
+
+namespace {
+struct AttnWs {
+    float *K, *V, *k, *v, *q, *S, *dP, *dq, *dk, *dv;
+    uint8_t *active;
+};
+AttnWs carve(void *ws, int64_t N, int C, int d, int n_q)
+{
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char *p = static_cast<char *>(ws);
+    auto take = [&](size_t bytes) {
+        char *r = p;
+        p += up(bytes);
+        return r;
+    };
+    AttnWs w;
+    w.K = reinterpret_cast<float *>(take(static_cast<size_t>(N) * C * 4));
+    w.V = reinterpret_cast<float *>(take(static_cast<size_t>(N) * C * 4));
+    w.k = reinterpret_cast<float *>(take(static_cast<size_t>(N) * d * 4));
+    w.v = reinterpret_cast<float *>(take(static_cast<size_t>(N) * d * 4));
+    w.q = reinterpret_cast<float *>(take(static_cast<size_t>(n_q) * d * 4));
+    w.S = reinterpret_cast<float *>(take(static_cast<size_t>(n_q) * N * 4));
+    w.active = reinterpret_cast<uint8_t *>(take(static_cast<size_t>(N)));
+    w.dP = reinterpret_cast<float *>(take(static_cast<size_t>(n_q) * N * 4));
+    w.dq = reinterpret_cast<float *>(take(static_cast<size_t>(n_q) * d * 4));
+    w.dk = reinterpret_cast<float *>(take(static_cast<size_t>(N) * d * 4));
+    w.dv = reinterpret_cast<float *>(take(static_cast<size_t>(N) * d * 4));
+    return w;
+}
+} // namespace
 
 cudaError_t launch_attention(void *cublas, const psi_surfels &s, const void *feat, const float *fscale, int dtype, int C,
                              const psi_camera &cam, float z_near, const float *Q, int n_q, const float *WQ,
                              const float *WK, const float *WV, int d, float *out, void *ws, cudaStream_t st,
                              const char **why)
 {
-    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     const int64_t N = s.n;
-    char *p = static_cast<char *>(ws);
-    float *K = reinterpret_cast<float *>(p);
-    p += up(static_cast<size_t>(N) * C * 4);
-    float *V = reinterpret_cast<float *>(p);
-    p += up(static_cast<size_t>(N) * C * 4);
-    float *k = reinterpret_cast<float *>(p);
-    p += up(static_cast<size_t>(N) * d * 4);
-    float *v = reinterpret_cast<float *>(p);
-    p += up(static_cast<size_t>(N) * d * 4);
-    float *q = reinterpret_cast<float *>(p);
-    p += up(static_cast<size_t>(n_q) * d * 4);
-    float *S = reinterpret_cast<float *>(p);
-    p += up(static_cast<size_t>(n_q) * N * 4);
-    uint8_t *active = reinterpret_cast<uint8_t *>(p);
+    const AttnWs w = carve(ws, N, C, d, n_q);
+    float *K = w.K, *V = w.V, *k = w.k, *v = w.v, *q = w.q, *S = w.S;
+    uint8_t *active = w.active;
 
     AttnPrep a{};
     a.s = s;
@@ -208,6 +301,41 @@ cudaError_t launch_attention(void *cublas, const psi_surfels &s, const void *fea
         return cudaErrorUnknown;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_attention_bwd(void *cublas, int64_t N, int C, int n_q, const float *Q, const float *WQ,
+                                 const float *WK, const float *WV, int d, const float *G, float *gQ, float *gWQ,
+                                 float *gWK, float *gWV, const float *mu, float *g_feat, float *g_mu, void *ws,
+                                 cudaStream_t st, const char **why)
+{
+    const AttnWs w = carve(ws, N, C, d, n_q);
+    cublasHandle_t h = static_cast<cublasHandle_t>(cublas);
+    const int n = static_cast<int>(N);
+    auto ok = [&](cublasStatus_t s) { return s == CUBLAS_STATUS_SUCCESS; };
+    if (!ok(cublasSetStream(h, st)) || !ok(gemm_nt(h, n_q, n, d, G, w.v, w.dP)) ||  // dP = G v^T
+        !ok(gemm_tn(h, n, d, n_q, w.S, G, w.dv))) {                              // dv = P^T G
+        *why = "cuBLAS GEMM failed";
+        return cudaErrorUnknown;
+    }
+    attn_softmax_bwd_kernel<<<static_cast<unsigned>(n_q), 1024, 0, st>>>(w.S, w.dP, N,
+                                                                         1.0f / sqrtf(static_cast<float>(d)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (!ok(gemm_rm(h, n_q, d, n, w.dP, w.k, w.dq)) ||          // dq = dE k
+        !ok(gemm_tn(h, n, d, n_q, w.dP, w.q, w.dk)) ||          // dk = dE^T q
+        (gQ && !ok(gemm_nt(h, n_q, C, d, w.dq, WQ, gQ))) ||     // dQ = dq W_Q^T
+        (gWQ && !ok(gemm_tn(h, C, d, n_q, Q, w.dq, gWQ))) ||    // dW_Q = Q^T dq
+        (gWK && !ok(gemm_tn(h, C, d, n, w.K, w.dk, gWK))) ||    // dW_K = K^T dk
+        (gWV && !ok(gemm_tn(h, C, d, n, w.V, w.dv, gWV))) ||    // dW_V = V^T dv
+        !ok(gemm_nt(h, n, C, d, w.dk, WK, w.K)) ||              // dK = dk W_K^T (over K)
+        !ok(gemm_nt(h, n, C, d, w.dv, WV, w.V))) {              // dV = dv W_V^T (over V)
+        *why = "cuBLAS GEMM failed";
+        return cudaErrorUnknown;
+    }
+    if (g_feat || g_mu)
+        attn_scatter_kernel<<<static_cast<unsigned>((N * 32 + 255) / 256), 256, 0, st>>>(w.K, w.V, w.active, mu, N,
+                                                                                         C, g_feat, g_mu);
+    return cudaGetLastError();
 }
 
 } // namespace psi

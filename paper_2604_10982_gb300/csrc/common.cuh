@@ -203,6 +203,10 @@ cudaError_t launch_attention(void *cublas, const psi_surfels &s, const void *fea
                              const psi_camera &cam, float z_near, const float *Q, int n_q, const float *WQ,
                              const float *WK, const float *WV, int d, float *out, void *ws, cudaStream_t st,
                              const char **why);
+cudaError_t launch_attention_bwd(void *cublas, int64_t N, int C, int n_q, const float *Q, const float *WQ,
+                                 const float *WK, const float *WV, int d, const float *G, float *gQ, float *gWQ,
+                                 float *gWK, float *gWV, const float *mu, float *g_feat, float *g_mu, void *ws,
+                                 cudaStream_t st, const char **why);
 cudaError_t launch_frames(const float *q, int64_t n, float *tu, float *tv, cudaStream_t st);
 cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
                               cudaStream_t st);

@@ -100,6 +100,9 @@ def lib():
         L.psi_frustum_attention.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures),
                                             ctypes.POINTER(PsiCamera), ctypes.c_float, _P, ctypes.c_int, _P, _P, _P,
                                             ctypes.c_int, _P, _P, sz, _P]
+        L.psi_frustum_attention_bwd.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures), _P,
+                                                ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P,
+                                                ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_quat_frames.argtypes = [_P, _P, _i64, _P, _P, _P]
         L.psi_quat_frames_bwd.argtypes = [_P, _P, _i64, _P, _P, _P, _P]
         L.psi_surfel_regularisers.argtypes = [_P, ctypes.POINTER(PsiSurfels), _P, _P, _P, _i64, ctypes.c_float,
@@ -303,6 +306,15 @@ def psi_frustum_attention(ctx, s, feats, cam, z_near, Q, n_q, WQ, WK, WV, d, out
                                           float(z_near), _ptr(Q), int(n_q), _ptr(WQ), _ptr(WK), _ptr(WV), int(d),
                                           _ptr(out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                           _stream(stream)), "psi_frustum_attention")
+
+
+def psi_frustum_attention_bwd(ctx, s, feats, Q, n_q, WQ, WK, WV, d, g_out, g_Q, g_WQ, g_WK, g_WV,
+                              grads: PsiGrads, workspace, stream=None):
+    ctx.check(lib().psi_frustum_attention_bwd(ctx.handle, ctypes.byref(s), ctypes.byref(feats), _ptr(Q), int(n_q),
+                                              _ptr(WQ), _ptr(WK), _ptr(WV), int(d), _ptr(g_out), _ptr(g_Q), _ptr(g_WQ),
+                                              _ptr(g_WK), _ptr(g_WV), ctypes.byref(grads), _ptr(workspace),
+                                              workspace.numel() * workspace.element_size(), _stream(stream)),
+              "psi_frustum_attention_bwd")
 
 
 def psi_quat_frames(ctx, q, n, tu, tv, stream=None):

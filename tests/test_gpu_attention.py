@@ -66,3 +66,36 @@ def test_attention_street_view(ctx):
     got, ref, act, _ = _run(ctx, w2, cam, psi.F32, 100, 64)
     assert act.mean() < 0.9 and keep.mean() > 0.999
     assert np.abs(got - ref).max() <= 5e-4 * max(1.0, np.abs(ref).max())
+
+
+def test_attention_gradients_match_oracle(ctx):
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    w = sg.dense_box(n=4000, d=32)
+    cam = w.cameras[0]
+    C, d, nq = 32, 16, 6
+    rng = np.random.default_rng(3)
+    W = [(rng.normal(size=(C, d)) / np.sqrt(C)).astype(np.float32) for _ in range(3)]
+    Q = rng.normal(size=(nq, C)).astype(np.float32)
+    G = rng.normal(size=(nq, d)).astype(np.float32)
+    scene = pl.DeviceScene(w.surfels, w.features)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.empty(nq, d, device="cuda")
+    ws = torch.empty(psi.attention_workspace_size(scene.n, C, d, nq), dtype=torch.uint8, device="cuda")
+    Qd, Wd = dev(Q), [dev(x) for x in W]
+    psi.psi_frustum_attention(ctx, scene.surfels_struct(), scene.features_struct(), psi.cameras([cam])[0], 0.2, Qd,
+                              nq, *Wd, d, out, ws)
+    gQ, gWQ, gWK, gWV = torch.empty(nq, C, device="cuda"), *(torch.empty(C, d, device="cuda") for _ in range(3))
+    gfeat = torch.zeros(scene.n, C, device="cuda")
+    gmu = torch.zeros(scene.n, 3, device="cuda")
+    gs = psi.PsiGrads(psi._ptr(gmu), None, None, None, None, None, psi._ptr(gfeat))
+    psi.psi_frustum_attention_bwd(ctx, scene.surfels_struct(), scene.features_struct(), Qd, nq, *Wd, d, dev(G),
+                                  gQ, gWQ, gWK, gWV, gs, ws)
+    torch.cuda.synchronize()
+    assert ctx.status_fetch()[0] == 0
+    _, margin = orc.frustum_active(w.surfels, cam, 0.2)
+    assert np.min(np.abs(margin)) > 1e-4
+    ref = orc.frustum_attention_grad(w.surfels, w.features.astype(np.float64), cam, 0.2, Q, *W, G)
+    for key, got in (("Q", gQ), ("WQ", gWQ), ("WK", gWK), ("WV", gWV), ("feat", gfeat), ("mu", gmu)):
+        g = got.cpu().numpy().astype(np.float64)
+        r = ref[key]
+        assert np.linalg.norm(g - r) <= 1e-4 * max(np.linalg.norm(r), 1e-12), key
