@@ -130,6 +130,7 @@ int psi_ctx_create(psi_ctx **out, int device)
     cudaError_t e = cudaMalloc(&c->status, sizeof(psi::DevStatus));
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(psi::DevStatus));
     if (e != cudaSuccess) {
+        if (c->status) cudaFree(c->status);
         delete c;
         return PSI_ERR_CUDA;
     }
