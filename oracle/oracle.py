@@ -40,20 +40,20 @@ def lib():
         L = ctypes.CDLL(path)
         P = ctypes.c_void_p
         i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_double
-        L.or_bin_view.argtypes = [i64, P, P, P, P, P, P, f32, f32, i32, i32, i32, i32, P, P, P, P, P]
+        L.or_bin_view.argtypes = [i64, P, P, P, P, P, P, f32, f32, i32, i32, i32, i32, i32, P, P, P, P, P]
         L.or_bin_view.restype = None
-        L.or_emit_view.argtypes = [i64, P, P, P, P, P, P, f32, f32, i32, i32, i32, i32,
+        L.or_emit_view.argtypes = [i64, P, P, P, P, P, P, f32, f32, i32, i32, i32, i32, i32,
                                    ctypes.c_uint32, ctypes.c_uint32, P, P, i64]
         L.or_emit_view.restype = i64
         L.or_rho_opacity.argtypes = [f32]
         L.or_rho_opacity.restype = f32
-        L.or_render.argtypes = [i64, P, P, P, P, P, P, P, i32, P, i32, P, P, i64, P, i32, f64,
+        L.or_render.argtypes = [i64, P, P, P, P, P, P, P, i32, P, i32, P, P, i64, P, i32, f64, i32,
                                 P, P, P, P, P, P, P, P]
         L.or_render.restype = None
-        L.or_render_grad.argtypes = [i64, P, P, P, P, P, P, P, i32, P, i32, P, P, i64, P, i32, f64,
+        L.or_render_grad.argtypes = [i64, P, P, P, P, P, P, P, i32, P, i32, P, P, i64, P, i32, f64, i32,
                                      P, P, P, P, P, P, P, P, P, P]
         L.or_render_grad.restype = None
-        L.or_pixel_walk.argtypes = [i64, P, P, P, P, P, P, i32, P, P, i32, i32, i32, f64, P, P, P, i32]
+        L.or_pixel_walk.argtypes = [i64, P, P, P, P, P, P, i32, P, P, i32, i32, i32, f64, i32, P, P, P, i32]
         L.or_pixel_walk.restype = i32
         L.or_num_threads.restype = i32
         L.or_set_threads.argtypes = [i32]
@@ -80,6 +80,7 @@ class Opts:
     tile_w: int = 16
     tile_h: int = 16
     t_eps: float = T_EPS
+    lowpass: bool = False   # 2DGS object-space low-pass filter: rho = min(u^2+v^2, 2|x-c|^2)
 
 
 def num_threads() -> int:
@@ -110,7 +111,7 @@ def bin_view(s, cam, opts: Opts):
     rect = np.zeros((n, 4), np.int32)
     ell = np.zeros((n, 9), np.float32)
     lib().or_bin_view(n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(camv), opts.chi2, opts.z_near,
-                      int(opts.opacity_radius), int(opts.mode), opts.tile_w, opts.tile_h,
+                      int(opts.opacity_radius), int(opts.mode), int(opts.lowpass), opts.tile_w, opts.tile_h,
                       _p(count), _p(dbits), _p(r2), _p(rect), _p(ell))
     return dict(count=count, depth_bits=dbits, r2=r2, rect=rect, ell=ell, visible=rect[:, 0] >= 0)
 
@@ -135,8 +136,8 @@ def emit_pairs(s, cams, opts: Opts):
         keys = np.zeros(max(cap, 1), np.uint64)
         vals = np.zeros(max(cap, 1), np.uint32)
         got = lib().or_emit_view(n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(camv), opts.chi2, opts.z_near,
-                                 int(opts.opacity_radius), int(opts.mode), opts.tile_w, opts.tile_h,
-                                 base, v * n, _p(keys), _p(vals), cap)
+                                 int(opts.opacity_radius), int(opts.mode), int(opts.lowpass), opts.tile_w,
+                                 opts.tile_h, base, v * n, _p(keys), _p(vals), cap)
         assert got == cap, (got, cap)
         keys_all.append(keys[:cap])
         vals_all.append(vals[:cap])
@@ -195,7 +196,7 @@ def render(s, cam, opts: Opts, feat=None, pixels=None, b=None):
                sumw=np.zeros(npix), diag=np.zeros((npix, 6)), hash=np.zeros(npix, np.uint64))
     camv = _c(cam.as_array(), np.float64)
     lib().or_render(s.n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(rgb), _p(f64), D, _p(order), len(order),
-                    _p(r2), _p(camv), npix, _p(pix), K, opts.t_eps,
+                    _p(r2), _p(camv), npix, _p(pix), K, opts.t_eps, int(opts.lowpass),
                     _p(out["rgb"]), _p(out["T"]), _p(out["F"]) if D else None,
                     _p(out["topk"]) if K > 0 else None, _p(out["ncontrib"]), _p(out["sumw"]), _p(out["diag"]),
                     _p(out["hash"]))
@@ -217,7 +218,7 @@ def pixel_walk(s, cam, opts: Opts, px: int, py: int, b=None, cap: int = 4096):
     uvat = np.zeros((cap, 4))
     sel = np.zeros(cap, np.uint8)
     cnt = lib().or_pixel_walk(s.n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(order), len(order), _p(r2), _p(camv),
-                              int(px), int(py), int(opts.top_k), opts.t_eps, _p(ids), _p(uvat), _p(sel), cap)
+                              int(px), int(py), int(opts.top_k), opts.t_eps, int(opts.lowpass), _p(ids), _p(uvat), _p(sel), cap)
     cnt = min(cnt, cap)
     return dict(id=ids[:cnt], u=uvat[:cnt, 0], v=uvat[:cnt, 1], alpha=uvat[:cnt, 2], T=uvat[:cnt, 3],
                 sel=sel[:cnt].astype(bool))
@@ -242,7 +243,7 @@ def render_grad(s, cam, opts: Opts, gC, feat=None, gF=None, gT=None, pixels=None
     gF = None if (gF is None or D == 0) else _c(gF, np.float64).reshape(npix, D)
     gT = None if gT is None else _c(gT, np.float64).reshape(npix)
     lib().or_render_grad(n, _p(mu), _p(tu), _p(tv), _p(sc), _p(o), _p(rgb), _p(f64), D, _p(order), len(order),
-                         _p(r2), _p(camv), npix, _p(pix), int(opts.top_k), opts.t_eps,
+                         _p(r2), _p(camv), npix, _p(pix), int(opts.top_k), opts.t_eps, int(opts.lowpass),
                          _p(gC), _p(gF), _p(gT), _p(g["mu"]), _p(g["tu"]), _p(g["tv"]), _p(g["scale"]),
                          _p(g["opacity"]), _p(g["rgb"]), _p(g["feat"]) if D else None)
     if not D:

@@ -28,6 +28,14 @@
  *      of the blending adjoint with suffix sums plus implicit differentiation
  *      of the ray-plane solve.
  *
+ * Optional 2DGS object-space low-pass filter (the surfel model of Sec. 3.1
+ * follows 2D Gaussian Splatting): with it the Gaussian argument is
+ * rho = min(u^2+v^2, 2 |x - c|^2), c the pixel position of the projected
+ * centre, i.e. the larger of the surfel's value and that of a screen-space
+ * Gaussian of standard deviation sqrt(2)/2 pixel at c, so a surfel seen edge
+ * on still covers about one pixel. The support becomes rho <= r^2; binning
+ * covers the ellipse and the disc 2 |x - c|^2 <= r_b^2.
+ *
  * Conventions: OpenCV camera (x right, y down, z forward), x_c = R x_w + t,
  * pixel (px,py) samples (px+1/2, py+1/2). Thresholds: alpha < 1/255 skipped,
  * alpha clamped to 0.99, stop after the surfel that takes T below T_eps.
@@ -84,11 +92,13 @@ typedef struct {
     float hx, hy;           /* exact AABB half-widths */
     float extx, exty;       /* half-extents used for the rectangle (mode) */
     int px0, px1, py0, py1; /* pixel-index rectangle of covered pixel centres */
+    float p0x, p0y;         /* projected centre (pixels) */
+    float rd2;              /* low-pass disc radius^2 in pixels (binning), < 0: no filter */
 } disc_t;
 
 /* camera: R[9] row-major, t[3], fx, fy, cx, cy, W, H (all float) */
 static void disc_surfel(const float *mu, const float *tu, const float *tv, float su, float sv, float o,
-                        const float *cam, float chi2, float znear, int oprad, int mode, disc_t *d)
+                        const float *cam, float chi2, float znear, int oprad, int mode, int lowpass, disc_t *d)
 {
     const float *R = cam, *t = cam + 9;
     const float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
@@ -161,6 +171,15 @@ static void disc_surfel(const float *mu, const float *tu, const float *tv, float
 
     float lox = ceilf((ex - extx) - 0.5f), hix = floorf((ex + extx) - 0.5f);
     float loy = ceilf((ey - exty) - 0.5f), hiy = floorf((ey + exty) - 0.5f);
+    /* low-pass filter: the rectangle also covers the disc 2 |x - c|^2 <= r2b */
+    const float rd2 = lowpass ? r2b * 0.5f : -1.0f;
+    if (lowpass) {
+        const float rd = sqrtf(rd2);
+        lox = fminf(lox, ceilf((p0x - rd) - 0.5f));
+        hix = fmaxf(hix, floorf((p0x + rd) - 0.5f));
+        loy = fminf(loy, ceilf((p0y - rd) - 0.5f));
+        hiy = fmaxf(hiy, floorf((p0y + rd) - 0.5f));
+    }
     lox = fmaxf(lox, 0.0f);
     loy = fmaxf(loy, 0.0f);
     hix = fminf(hix, (float)(W - 1));
@@ -176,6 +195,8 @@ static void disc_surfel(const float *mu, const float *tu, const float *tv, float
     d->extx = extx; d->exty = exty;
     d->px0 = (int)lox; d->px1 = (int)hix;
     d->py0 = (int)loy; d->py1 = (int)hiy;
+    d->p0x = p0x; d->p0y = p0y;
+    d->rd2 = rd2;
 }
 
 /* x-coordinate of the ellipse boundary on the horizontal line y = ey + dy */
@@ -214,7 +235,26 @@ static int row_tiles(const disc_t *d, int mode, int ty, int tw, int th, int *c0,
     float fl = ceilf(xmin - 0.5f), fh = floorf(xmax - 0.5f);
     fl = fmaxf(fl, (float)d->px0);
     fh = fminf(fh, (float)d->px1);
-    if (!(fl <= fh)) return 0;
+    int ok = fl <= fh;
+    if (d->rd2 >= 0.0f) {
+        /* low-pass disc: its chord at the band's row nearest to the centre;
+         * the row's columns are the hull of both ranges */
+        const float lo = (float)r0 + 0.5f, hi = (float)r1 + 0.5f;
+        const float dy = d->p0y < lo ? lo - d->p0y : (d->p0y > hi ? d->p0y - hi : 0.0f);
+        const float tt = fmaf(-dy, dy, d->rd2);
+        if (tt >= 0.0f) {
+            const float h = sqrtf(tt);
+            float gl = ceilf((d->p0x - h) - 0.5f), gh = floorf((d->p0x + h) - 0.5f);
+            gl = fmaxf(gl, (float)d->px0);
+            gh = fminf(gh, (float)d->px1);
+            if (gl <= gh) {
+                fl = ok ? fminf(fl, gl) : gl;
+                fh = ok ? fmaxf(fh, gh) : gh;
+                ok = 1;
+            }
+        }
+    }
+    if (!ok) return 0;
     *c0 = (int)fl / tw;
     *c1 = (int)fh / tw;
     return 1;
@@ -235,13 +275,14 @@ static uint32_t disc_count(const disc_t *d, int mode, int tw, int th)
  * out_count[n]: tiles touched; out_depth_bits[n]: float bits of the depth;
  * out_r2[n]; out_rect[4n]: px0,px1,py0,py1 (or -1); out_ell[9n]: ex,ey,A00,A01,A11,hx,hy,extx,exty. */
 void or_bin_view(int64_t n, const float *mu, const float *tu, const float *tv, const float *s, const float *o,
-                 const float *cam, float chi2, float znear, int oprad, int mode, int tw, int th,
+                 const float *cam, float chi2, float znear, int oprad, int mode, int lowpass, int tw, int th,
                  uint32_t *out_count, uint32_t *out_depth_bits, float *out_r2, int32_t *out_rect, float *out_ell)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         disc_t d;
-        disc_surfel(mu + 3 * i, tu + 3 * i, tv + 3 * i, s[2 * i], s[2 * i + 1], o[i], cam, chi2, znear, oprad, mode, &d);
+        disc_surfel(mu + 3 * i, tu + 3 * i, tv + 3 * i, s[2 * i], s[2 * i + 1], o[i], cam, chi2, znear, oprad, mode, lowpass,
+                    &d);
         out_count[i] = disc_count(&d, mode, tw, th);
         out_depth_bits[i] = d.ok ? f_float_to_bits(d.depth) : 0xFFFFFFFFu;
         out_r2[i] = d.ok ? d.r2 : 0.0f;
@@ -262,7 +303,7 @@ void or_bin_view(int64_t n, const float *mu, const float *tu, const float *tv, c
  * key = (tile_base + ty*tiles_x + tx) << 32 | depth_bits; value = value_base + i.
  * Returns the number of pairs (writes at most cap). */
 int64_t or_emit_view(int64_t n, const float *mu, const float *tu, const float *tv, const float *s, const float *o,
-                     const float *cam, float chi2, float znear, int oprad, int mode, int tw, int th,
+                     const float *cam, float chi2, float znear, int oprad, int mode, int lowpass, int tw, int th,
                      uint32_t tile_base, uint32_t value_base, uint64_t *keys, uint32_t *vals, int64_t cap)
 {
     const int W = (int)cam[16];
@@ -270,7 +311,8 @@ int64_t or_emit_view(int64_t n, const float *mu, const float *tu, const float *t
     int64_t p = 0;
     for (int64_t i = 0; i < n; i++) {
         disc_t d;
-        disc_surfel(mu + 3 * i, tu + 3 * i, tv + 3 * i, s[2 * i], s[2 * i + 1], o[i], cam, chi2, znear, oprad, mode, &d);
+        disc_surfel(mu + 3 * i, tu + 3 * i, tv + 3 * i, s[2 * i], s[2 * i + 1], o[i], cam, chi2, znear, oprad, mode, lowpass,
+                    &d);
         if (!d.ok) continue;
         const uint64_t db = f_float_to_bits(d.depth);
         for (int ty = d.py0 / th; ty <= d.py1 / th; ty++) {
@@ -298,7 +340,8 @@ float or_rho_opacity(float o) { return rho_opacity(o); }
 /* OR_PLANT selects a deliberately wrong variant, built only by the test that
  * checks that the pins catch it: 1 drops the 1/2 in the Gaussian, 2 updates T
  * before taking the weight, 3 keeps the K smallest weights, 4 flips the sign
- * of the centre gradient, 5 mirrors the exact-test chord. 0 = correct. */
+ * of the centre gradient, 5 mirrors the exact-test chord, 6 drops the factor 2
+ * of the low-pass term, 7 flips the sign of its centre gradient. 0 = correct. */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -383,6 +426,8 @@ typedef struct {
     int idx;       /* position in the canonical order */
     double u, v, lam, G, alpha, T; /* T = transmittance before this surfel */
     int clamped;
+    int filt;      /* low-pass term won: rho = 2 (dx^2 + dy^2) */
+    double dx, dy; /* pixel centre minus projected centre (low-pass) */
 } contrib_t;
 
 typedef struct {
@@ -404,7 +449,7 @@ static void push_contrib(scratch_t *s, const contrib_t *c)
 /* Front-to-back walk for one pixel. Fills s->c with the composited surfels,
  * returns final T. diag (may be NULL) receives threshold distances. */
 static double walk_pixel(const surf64_t *sf, const double *o, const int *order, int n_order, const double *r2,
-                         const double *cam, int px, int py, double t_eps, scratch_t *s, double *diag)
+                         const double *cam, int px, int py, double t_eps, int lowpass, scratch_t *s, double *diag)
 {
     const double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
     const double dir[3] = {((double)px + 0.5 - cx) / fx, ((double)py + 0.5 - cy) / fy, 1.0};
@@ -413,11 +458,26 @@ static double walk_pixel(const surf64_t *sf, const double *o, const int *order, 
     s->n = 0;
     for (int k = 0; k < n_order; k++) {
         const int i = order[k];
-        double u, v, lam;
-        if (!ray_splat(&sf[i], dir, &u, &v, &lam)) continue;
-        if (!(lam > 0.0)) continue;
-        const double d2 = u * u + v * v;
-        if (diag && o[i] * exp(-0.5 * r2[i]) >= OR_ALPHA_MIN * 0.5) {
+        double u = 0.0, v = 0.0, lam = 0.0;
+        const int hit = ray_splat(&sf[i], dir, &u, &v, &lam) && lam > 0.0;
+        if (!hit && !lowpass) continue;
+        double d2 = hit ? u * u + v * v : INFINITY; /* rho of the surfel's own Gaussian */
+        double ddx = 0.0, ddy = 0.0;
+        int filt = 0;
+        if (lowpass) {
+            /* screen-space term: pixel distance to the projected centre */
+            const double *xc = sf[i].xc;
+            ddx = ((double)px + 0.5) - (fx * xc[0] / xc[2] + cx);
+            ddy = ((double)py + 0.5) - (fy * xc[1] / xc[2] + cy);
+            const double rho2 = ((OR_PLANT == 6) ? 1.0 : 2.0) * (ddx * ddx + ddy * ddy);
+            const double rho3 = d2 <= r2[i] ? d2 : INFINITY;
+            if (diag && o[i] * exp(-0.5 * r2[i]) >= OR_ALPHA_MIN * 0.5) {
+                double rel = fabs(fmin(d2, rho2) - r2[i]) / r2[i];
+                if (rel < dmin_r) dmin_r = rel;
+            }
+            filt = rho2 < rho3;
+            d2 = filt ? rho2 : rho3;
+        } else if (diag && o[i] * exp(-0.5 * r2[i]) >= OR_ALPHA_MIN * 0.5) {
             double rel = fabs(d2 - r2[i]) / r2[i];
             if (rel < dmin_r) dmin_r = rel;
         }
@@ -432,9 +492,14 @@ static double walk_pixel(const surf64_t *sf, const double *o, const int *order, 
         }
         if (a < OR_ALPHA_MIN) continue;
         const double Tn = T * (1.0 - a);
-        contrib_t c = {k, u, v, lam, G, a, (OR_PLANT == 2) ? Tn : T, clamped};
+        contrib_t c = {k, u, v, lam, G, a, (OR_PLANT == 2) ? Tn : T, clamped, filt, ddx, ddy};
         push_contrib(s, &c);
-        if (diag) {
+        if (diag && filt) {
+            /* d rho / d pixel = 4 (dx, dy) */
+            const double sens = clamped ? 0.0 : 0.5 * a * 4.0 * sqrt(ddx * ddx + ddy * ddy);
+            cond += sens * T;
+            if (sens > cond1) cond1 = sens;
+        } else if (diag) {
             /* sensitivity of d2 to the pixel position: d(u,v,lam)/dx = B^-1 lam e_x / fx */
             double c2[3] = {-dir[0], -dir[1], -dir[2]};
             double ex_[3] = {lam / fx, 0.0, 0.0}, ey_[3] = {0.0, lam / fy, 0.0}, zx[3], zy[3];
@@ -446,6 +511,8 @@ static double walk_pixel(const surf64_t *sf, const double *o, const int *order, 
                 cond += sens * T;
                 if (sens > cond1) cond1 = sens;
             }
+        }
+        if (diag) {
             double rel = fabs(Tn - t_eps) / t_eps;
             if (rel < dmin_t) dmin_t = rel;
         }
@@ -460,7 +527,7 @@ static double walk_pixel(const surf64_t *sf, const double *o, const int *order, 
  * before it, selection flag. Returns the count (writes at most cap). */
 int or_pixel_walk(int64_t n, const double *mu, const double *tu, const double *tv, const double *s, const double *o,
                   const int *order, int n_order, const double *r2, const double *cam, int px, int py, int K,
-                  double t_eps, int32_t *out_id, double *out_uvat, uint8_t *out_sel, int cap);
+                  double t_eps, int lowpass, int32_t *out_id, double *out_uvat, uint8_t *out_sel, int cap);
 
 /* Select Top-K contributors: sets sel[j]=1 for chosen entries of s->c. Returns
  * the gap omega_(K) - omega_(K+1) (INFINITY if no (K+1)-th). K <= 0: all. */
@@ -489,7 +556,7 @@ static double select_topk(scratch_t *s, int K, unsigned char *sel)
  * order, -1 padded; if K>0), ncontrib, sumw, diag[6], hash (contributor ids + selection). */
 void or_render(int64_t n, const double *mu, const double *tu, const double *tv, const double *s, const double *o,
                const double *rgb, const double *feat, int D, const int *order, int n_order, const double *r2,
-               const double *cam, int64_t npix, const int32_t *pix, int K, double t_eps,
+               const double *cam, int64_t npix, const int32_t *pix, int K, double t_eps, int lowpass,
                double *out_rgb, double *out_T, double *out_F, int32_t *out_topk, int32_t *out_ncontrib,
                double *out_sumw, double *out_diag, uint64_t *out_hash)
 {
@@ -503,7 +570,7 @@ void or_render(int64_t n, const double *mu, const double *tu, const double *tv, 
 #pragma omp for schedule(dynamic, 16)
         for (int64_t p = 0; p < npix; p++) {
             double diag[6] = {0};
-            const double T = walk_pixel(sf, o, order, n_order, r2, cam, pix[2 * p], pix[2 * p + 1], t_eps, &sc, diag);
+            const double T = walk_pixel(sf, o, order, n_order, r2, cam, pix[2 * p], pix[2 * p + 1], t_eps, lowpass, &sc, diag);
             if (selcap < sc.n) { selcap = sc.n; sel = (unsigned char *)realloc(sel, (size_t)selcap); }
             diag[3] = select_topk(&sc, K, sel);
             double c3[3] = {0, 0, 0}, sw = 0.0;
@@ -513,7 +580,7 @@ void or_render(int64_t n, const double *mu, const double *tu, const double *tv, 
                 const double w = sc.c[j].alpha * sc.c[j].T;
                 for (int c = 0; c < 3; c++) c3[c] += w * rgb[3 * i + c];
                 sw += w;
-                h = (h ^ (uint64_t)(i * 2 + sel[j])) * 1099511628211ull;
+                h = (h ^ (uint64_t)(i * 4 + sel[j] * 2 + sc.c[j].filt)) * 1099511628211ull;
             }
             for (int c = 0; c < 3; c++) out_rgb[3 * p + c] = c3[c];
             out_T[p] = T;
@@ -547,7 +614,7 @@ void or_render(int64_t n, const double *mu, const double *tu, const double *tv, 
  * g_o[n], g_rgb[3n], g_feat[n*D] (if feat). gF, gT may be NULL. */
 void or_render_grad(int64_t n, const double *mu, const double *tu, const double *tv, const double *s, const double *o,
                     const double *rgb, const double *feat, int D, const int *order, int n_order, const double *r2,
-                    const double *cam, int64_t npix, const int32_t *pix, int K, double t_eps,
+                    const double *cam, int64_t npix, const int32_t *pix, int K, double t_eps, int lowpass,
                     const double *gC, const double *gF, const double *gT,
                     double *g_mu, double *g_tu, double *g_tv, double *g_s, double *g_o, double *g_rgb, double *g_feat)
 {
@@ -563,7 +630,7 @@ void or_render_grad(int64_t n, const double *mu, const double *tu, const double 
 #pragma omp for schedule(dynamic, 16)
         for (int64_t p = 0; p < npix; p++) {
             const int px = pix[2 * p], py = pix[2 * p + 1];
-            const double Tf = walk_pixel(sf, o, order, n_order, r2, cam, px, py, t_eps, &sc, NULL);
+            const double Tf = walk_pixel(sf, o, order, n_order, r2, cam, px, py, t_eps, lowpass, &sc, NULL);
             if (selcap < sc.n) { selcap = sc.n; sel = (unsigned char *)realloc(sel, (size_t)selcap); }
             select_topk(&sc, K, sel);
             const double dir[3] = {((double)px + 0.5 - cx) / fx, ((double)py + 0.5 - cy) / fy, 1.0};
@@ -595,9 +662,24 @@ void or_render_grad(int64_t n, const double *mu, const double *tu, const double 
                     }
                 }
                 if (c->clamped) continue; /* alpha held at 0.99: no dependence on o, u, v */
-                /* alpha = o G, G = exp(-(u^2+v^2)/2) */
+                /* alpha = o G, G = exp(-rho/2) */
 #pragma omp atomic
                 g_o[i] += dL_da * c->G;
+                if (c->filt) {
+                    /* rho = 2 |x - p|^2 with p = (fx X/Z + cx, fy Y/Z + cy), (X, Y, Z) = R mu + t:
+                     * dL/dp = dL/drho * (-4 (dx, dy)), dL/drho = -dL/dalpha alpha / 2 */
+                    const double grho = -0.5 * dL_da * c->alpha;
+                    const double sgn = (OR_PLANT == 7) ? -1.0 : 1.0;
+                    const double gpx = sgn * grho * (-4.0 * c->dx), gpy = sgn * grho * (-4.0 * c->dy);
+                    const double *xc = sf[i].xc;
+                    const double gxc[3] = {gpx * fx / xc[2], gpy * fy / xc[2],
+                                           -(gpx * fx * xc[0] + gpy * fy * xc[1]) / (xc[2] * xc[2])};
+                    for (int k = 0; k < 3; k++) {
+#pragma omp atomic
+                        g_mu[3 * i + k] += R[k] * gxc[0] + R[3 + k] * gxc[1] + R[6 + k] * gxc[2];
+                    }
+                    continue;
+                }
                 const double gu = dL_da * (-c->alpha * c->u);
                 const double gv = dL_da * (-c->alpha * c->v);
                 /* implicit differentiation of B (u,v,lam) = -xc, B = [a | b | -dir]:
@@ -653,12 +735,12 @@ void or_set_threads(int n)
 
 int or_pixel_walk(int64_t n, const double *mu, const double *tu, const double *tv, const double *s, const double *o,
                   const int *order, int n_order, const double *r2, const double *cam, int px, int py, int K,
-                  double t_eps, int32_t *out_id, double *out_uvat, uint8_t *out_sel, int cap)
+                  double t_eps, int lowpass, int32_t *out_id, double *out_uvat, uint8_t *out_sel, int cap)
 {
     surf64_t *sf = (surf64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(surf64_t));
     prep_surfels(n, mu, tu, tv, s, cam, sf);
     scratch_t sc = {0};
-    walk_pixel(sf, o, order, n_order, r2, cam, px, py, t_eps, &sc, NULL);
+    walk_pixel(sf, o, order, n_order, r2, cam, px, py, t_eps, lowpass, &sc, NULL);
     unsigned char *sel = (unsigned char *)malloc((size_t)(sc.n > 0 ? sc.n : 1));
     select_topk(&sc, K, sel);
     for (int j = 0; j < sc.n && j < cap; j++) {

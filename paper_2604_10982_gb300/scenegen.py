@@ -285,10 +285,10 @@ def grad_scene(seed: int = 0, n: int = 500_000, d: int = 128) -> Workload:
     return Workload("grad-500k-960x540-D128-K16", s, [cam], d, 16, make_features(n, d, seed))
 
 
-def crop_scene(seed: int = 0, n: int = 500, d: int = 128, size: int = 64) -> Workload:
+def crop_scene(seed: int = 0, n: int = 500, d: int = 128, size: int = 64, scale_median: float = 0.05) -> Workload:
     """A 64x64 crop camera (f=480) with 500 street surfels inside its frustum."""
     cam = look_camera((0.0, 5.0, 1.5), 0.0, size, size, 480.0)
-    pool = make_surfels(40 * n, street_planes(), seed)
+    pool = make_surfels(40 * n, street_planes(), seed, scale_median=scale_median)
     xc = pool.mu.astype(np.float64) @ cam.R.T + cam.t
     z = xc[:, 2]
     ok = z > 0.5

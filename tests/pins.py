@@ -67,6 +67,76 @@ def pin_fronto_parallel():
     assert np.max(np.abs(out["T"][m] - (1.0 - exp_a[m]))) < 1e-12
 
 
+def _screen_term(cam, s, o, pix, r2):
+    """The screen-space term of the 2DGS low-pass filter for one surfel: a
+    Gaussian of standard deviation sqrt(2)/2 pixel about the projected centre
+    c = K (R mu + t) (dehomogenised), i.e. o exp(-|x - c|^2) with the opacity
+    clamp and cut-offs of Sec. 3.1; 0 outside 2 |x - c|^2 <= r2. Also returns
+    the squared-distance argument 2 |x - c|^2."""
+    R, t, fx, fy, cx, cy = _cam_f64(cam)
+    K = np.array([[fx, 0.0, cx], [0.0, fy, cy], [0.0, 0.0, 1.0]])
+    h = K @ (R @ s.mu[0].astype(np.float64) + t)
+    d = pix.astype(np.float64) + 0.5 - h[:2] / h[2]
+    rho = 2.0 * np.sum(d * d, axis=1)
+    a = min(float(np.float32(o)), 1.0) * np.exp(-0.5 * rho)
+    return np.where((rho <= r2) & (a >= 1 / 255), np.minimum(a, 0.99), 0.0), rho, a
+
+
+def _edge_on_surfel(cam, xc, su, sv, o):
+    """A surfel whose plane contains the camera centre (seen exactly edge on):
+    t_u = camera x axis, t_v = unit vector from the camera to the centre."""
+    R, t, *_ = _cam_f64(cam)
+    xc = np.asarray(xc, np.float64)
+    mu = R.T @ (xc - t)
+    tu = R.T @ np.array([1.0, 0.0, 0.0])
+    tv = R.T @ (xc / np.linalg.norm(xc))
+    tv -= tu * (tu @ tv)
+    tv /= np.linalg.norm(tv)
+    return sg.Surfels(np.array([mu], np.float32), np.array([tu], np.float32), np.array([tv], np.float32),
+                      np.array([[su, sv]], np.float32), np.array([o], np.float32), np.array([[1.0, 1.0, 1.0]], np.float32))
+
+
+def pin_lowpass():
+    """2DGS object-space low-pass filter: for one surfel the filtered alpha is
+    the larger of the surfel's own alpha (the unfiltered render, pinned above)
+    and the screen-space Gaussian term; an edge-on surfel is invisible without
+    the filter and exactly the screen-space term with it; a surfel several
+    pixels wide is unchanged."""
+    cases = [
+        fronto_surfel(CAM, 0.10, -0.05, 3.0, 0.01, 0.012, 0.8)[0],   # ~0.4 px: the screen term wins
+        fronto_surfel(CAM, -0.2, 0.07, 3.0, 0.10, 0.008, 0.7)[0],    # 3.7 x 0.3 px: both terms win somewhere
+        _edge_on_surfel(CAM, (0.13, -0.08, 2.5), 0.3, 0.2, 0.9),
+    ]
+    rng = np.random.default_rng(8)
+    for _ in range(3):  # small surfels at random tilts
+        mu = np.array([rng.uniform(-0.4, 0.4), rng.uniform(-0.3, 0.3), rng.uniform(2.0, 4.0)])
+        n = rng.normal(size=3); n /= np.linalg.norm(n)
+        a = np.cross(n, [0.3, 0.5, 0.8]); a /= np.linalg.norm(a)
+        R, t, *_ = _cam_f64(CAM)
+        cases.append(sg.Surfels(np.array([R.T @ (mu - t)], np.float32), np.array([R.T @ a], np.float32),
+                                np.array([R.T @ np.cross(n, a)], np.float32),
+                                np.array(rng.uniform(0.005, 0.03, (1, 2)), np.float32), np.array([0.85], np.float32),
+                                np.array([[1.0, 1.0, 1.0]], np.float32)))
+    for k, s in enumerate(cases):
+        plain = orc.render(s, CAM, orc.Opts(mode=orc.EXACT))
+        filt = orc.render(s, CAM, orc.Opts(mode=orc.EXACT, lowpass=True))
+        pix = filt["pixels"]
+        r2 = float(orc.bin_view(s, CAM, orc.Opts(mode=orc.EXACT, lowpass=True))["r2"][0])
+        scr, rho, a_raw = _screen_term(CAM, s, s.opacity[0], pix, r2)
+        safe = (np.abs(rho - r2) > 1e-9) & (np.abs(a_raw - 1 / 255) > 1e-12)
+        want = np.maximum(1.0 - plain["T"], scr)
+        got = 1.0 - filt["T"]
+        assert np.max(np.abs(got[safe] - want[safe])) < 1e-12, k
+        assert (scr > 0).sum() >= 3, k
+        if k == 2:
+            assert np.all(plain["T"] == 1.0)
+    # several pixels wide: the surfel's own term wins everywhere
+    s, _ = fronto_surfel(CAM, 0.21, -0.13, 3.0, 0.35, 0.22, 0.8)
+    a = orc.render(s, CAM, orc.Opts(mode=orc.EXACT))
+    b = orc.render(s, CAM, orc.Opts(mode=orc.EXACT, lowpass=True))
+    assert np.array_equal(a["T"], b["T"]) and np.array_equal(a["rgb"], b["rgb"])
+
+
 def pin_rotated_point():
     """A point placed on a tilted surfel at (u0, v0) and projected by hand onto a
     pixel centre is recovered by the ray-splat intersection."""
@@ -172,7 +242,7 @@ def pin_topk_special_cases(w=None):
                 assert np.max(np.abs(out["F"][j] - om[order[0]] * feats[i])) < 1e-12
 
 
-def pin_coverage(w=None, modes=(orc.SPHERE, orc.AABB, orc.EXACT), opacity_radius=False):
+def pin_coverage(w=None, modes=(orc.SPHERE, orc.AABB, orc.EXACT), opacity_radius=False, lowpass=False):
     """Brute force: every (pixel, surfel) that contributes in FP64 has the
     surfel listed in that pixel's tile (all modes); EXACT <= AABB <= SPHERE."""
     w = w or sg.dense_box(n=3000)
@@ -181,7 +251,7 @@ def pin_coverage(w=None, modes=(orc.SPHERE, orc.AABB, orc.EXACT), opacity_radius
     tiles_x = (cam.width + 15) // 16
     sets = {}
     for mode in modes:
-        opts = orc.Opts(mode=mode, top_k=100000, opacity_radius=opacity_radius)
+        opts = orc.Opts(mode=mode, top_k=100000, opacity_radius=opacity_radius, lowpass=lowpass)
         keys, vals = orc.emit_pairs(w.surfels, [cam], opts)
         code = (keys >> np.uint64(32)).astype(np.int64) * n + vals.astype(np.int64)
         sets[mode] = np.unique(code)
@@ -252,13 +322,14 @@ def pin_rho():
         assert ref <= r <= ref + 2e-3, (o32, r, ref)
 
 
-def fd_check(w, params_per_kind=12, seed=0, h_rel=1e-5, tol_rel=1e-6, tol_abs=2e-7):
+def fd_check(w, params_per_kind=12, seed=0, h_rel=1e-5, tol_rel=1e-6, tol_abs=2e-7, lowpass=False):
     """Central finite differences (Richardson-extrapolated from steps h and
     h/2, error O(h^4)) of the FP64 loss against the analytic gradient,
-    skipping perturbations that change any discrete decision."""
+    skipping perturbations that change any discrete decision (with the
+    low-pass filter, also which of its two terms wins)."""
     cam = w.cameras[0]
     s0 = w.surfels
-    opts = orc.Opts(mode=orc.EXACT, top_k=w.top_k)
+    opts = orc.Opts(mode=orc.EXACT, top_k=w.top_k, lowpass=lowpass)
     npix = cam.width * cam.height
     D = w.features.shape[1]
     gC = sg.make_upstream(3 * npix, seed, 0).reshape(npix, 3).astype(np.float64)

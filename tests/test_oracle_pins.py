@@ -63,6 +63,20 @@ def test_fd_gradients(oracle_lib):
     assert checked >= 40
 
 
+def test_lowpass_filter_max_of_terms(oracle_lib):
+    pins.pin_lowpass()
+
+
+def test_tile_coverage_lowpass(oracle_lib):
+    pins.pin_coverage(sg.dense_box(n=1500, scale_median=0.05), lowpass=True)
+
+
+def test_fd_gradients_lowpass(oracle_lib):
+    w = sg.crop_scene(n=500, d=16, size=64, scale_median=0.08)
+    checked, worst = pins.fd_check(w, params_per_kind=8, lowpass=True)
+    assert checked >= 32
+
+
 def test_tiny_config_shape(oracle_lib):
     w = sg.tiny()
     assert w.surfels.n == 2000 and w.cameras[0].width == 128 and w.features.shape == (2000, 16)
@@ -71,7 +85,7 @@ def test_tiny_config_shape(oracle_lib):
 
 
 @pytest.mark.parametrize("plant,check", [
-    (1, "fronto"), (2, "two"), (3, "topk"), (4, "fd"), (5, "coverage"),
+    (1, "fronto"), (2, "two"), (3, "topk"), (4, "fd"), (5, "coverage"), (6, "lowpass"), (7, "fd_lowpass"),
 ])
 def test_planted_mistake_is_caught(plant, check):
     """A deliberately wrong oracle build fails the pin aimed at that mistake."""
@@ -81,6 +95,9 @@ def test_planted_mistake_is_caught(plant, check):
         "topk": lambda: pins.pin_topk_special_cases(sg.dense_box(n=3000)),
         "fd": lambda: pins.fd_check(sg.crop_scene(n=200, d=8, size=48), params_per_kind=6),
         "coverage": lambda: pins.pin_coverage(sg.dense_box(n=3000), modes=(orc.EXACT,)),
+        "lowpass": pins.pin_lowpass,
+        "fd_lowpass": lambda: pins.fd_check(sg.crop_scene(n=300, d=8, size=48, scale_median=0.08),
+                                            params_per_kind=6, lowpass=True),
     }[check]
     orc.use_variant(plant)
     try:
