@@ -62,6 +62,7 @@ enum psi_dtype { PSI_F32 = 0, PSI_BF16 = 1, PSI_FP8_E4M3 = 2 };
 #define PSI_MAX_VIEWS 64
 #define PSI_RECORD_BYTES 80     /* render record per (view, surfel) */
 #define PSI_BIN_RECORD_BYTES 32 /* binning record per (view, surfel) */
+#define PSI_BIN_RECORD_BYTES_LOWPASS 48 /* the same with psi_render_opts.lowpass set */
 #define PSI_MAX_TOPK 32
 
 /* Surfels (Sec. 3.1): a 2D Gaussian in the plane through mu spanned by the
@@ -105,6 +106,12 @@ typedef struct {
     int32_t opacity_radius; /* 1: shrink the radius to where o*exp(-d^2/2) reaches 1/255 */
     int32_t tile_w, tile_h; /* tile size in pixels (16x16 supported) */
     float t_eps;            /* stop a pixel after the surfel that takes T below this */
+    int32_t lowpass;        /* 1: the 2DGS object-space low-pass filter (Sec. 3.1 surfels
+                               follow 2DGS): the Gaussian argument is min(u^2+v^2, 2|x-c|^2),
+                               c the pixel position of the projected centre, so a surfel
+                               seen edge on still covers about one pixel; the support is
+                               that argument <= r^2. Bin records are then
+                               PSI_BIN_RECORD_BYTES_LOWPASS bytes. 0: off (default) */
 } psi_render_opts;
 
 /* Forward outputs (device pointers; NULL = not written unless stated). Pixel p of
@@ -192,7 +199,8 @@ int psi_render_bwd_workspace_size(int64_t n_records, int64_t n_pix, int top_k, s
  * z_near), the support radius, the ellipse bounds of the projected covariance
  * (Sec. 5, Precise Tile Intersection) and the tile count of `o->mode`.
  *  records:       [n_views*N] x PSI_RECORD_BYTES, 16-byte aligned (written for visible records)
- *  bin_records:   [n_views*N] x PSI_BIN_RECORD_BYTES, 16-byte aligned
+ *  bin_records:   [n_views*N] x PSI_BIN_RECORD_BYTES (PSI_BIN_RECORD_BYTES_LOWPASS with
+ *                 o->lowpass), 16-byte aligned
  *  tiles_touched: [n_views*N] uint32, 0 for culled records
  * cams is a HOST array of n_views (<= PSI_MAX_VIEWS) cameras. */
 int psi_project_surfels(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cams, int n_views,

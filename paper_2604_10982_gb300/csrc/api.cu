@@ -47,6 +47,7 @@ int check_opts(psi_ctx *ctx, const psi_render_opts *o)
     if (!(o->chi2 > 0.0f) || !(o->chi2 < 1e4f)) return fail(ctx, PSI_ERR_INVALID_ARG, "chi2 must be in (0, 1e4)");
     if (!(o->z_near > 0.0f)) return fail(ctx, PSI_ERR_INVALID_ARG, "z_near must be > 0");
     if (!(o->t_eps >= 0.0f) || !(o->t_eps < 1.0f)) return fail(ctx, PSI_ERR_INVALID_ARG, "t_eps must be in [0,1)");
+    if (o->lowpass != 0 && o->lowpass != 1) return fail(ctx, PSI_ERR_INVALID_ARG, "lowpass must be 0 or 1");
     return PSI_OK;
 }
 
@@ -198,6 +199,7 @@ void psi_default_opts(psi_render_opts *o)
     o->tile_w = 16;
     o->tile_h = 16;
     o->t_eps = 1e-4f;
+    o->lowpass = 0;
 }
 
 int psi_view_layout(const psi_camera *cams, int n_views, const psi_render_opts *o, int64_t *tile_base, int64_t *pix_base)

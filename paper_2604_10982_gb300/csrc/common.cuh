@@ -54,6 +54,7 @@ struct FrameParams {
     float chi2, z_near, t_eps;
     int32_t opacity_radius;
     int32_t top_k;
+    int32_t lowpass; // 2DGS object-space low-pass filter
     uint32_t n_tiles_total;
     int64_t n_pix_total;
     ViewParams v[PSI_MAX_VIEWS];

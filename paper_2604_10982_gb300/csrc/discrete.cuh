@@ -57,6 +57,8 @@ struct Bin {
     float ex, ey;          // ellipse centre (pixels)
     float A00, A01, A11;   // ellipse shape matrix at the binning radius
     int px0, px1, py0, py1; // rectangle of pixel indices whose centres may be covered
+    float p0x, p0y;        // projected centre (pixels)
+    float rd2;             // low-pass disc 2|x - p0|^2 <= r_b^2 as radius^2 in pixels; < 0: no filter
 };
 
 // x of the ellipse boundary on the line y = ey + dy (left or right branch)
@@ -104,24 +106,57 @@ __device__ __forceinline__ bool row_tiles(const Bin &b, int mode, int ty, int tw
     float fh = floorf(sub(xmax, 0.5f));
     fl = fmaxf(fl, static_cast<float>(b.px0));
     fh = fminf(fh, static_cast<float>(b.px1));
-    if (!(fl <= fh)) return false;
+    bool ok = fl <= fh;
+    if (b.rd2 >= 0.0f) {
+        // low-pass disc: its chord at the band's row nearest to the centre; the
+        // row's columns are the hull of both ranges
+        const float lo = add(static_cast<float>(r0), 0.5f), hi = add(static_cast<float>(r1), 0.5f);
+        const float dy = b.p0y < lo ? sub(lo, b.p0y) : (b.p0y > hi ? sub(b.p0y, hi) : 0.0f);
+        const float tt = fma(-dy, dy, b.rd2);
+        if (tt >= 0.0f) {
+            const float h = sqrt(tt);
+            float gl = ceilf(sub(sub(b.p0x, h), 0.5f));
+            float gh = floorf(sub(add(b.p0x, h), 0.5f));
+            gl = fmaxf(gl, static_cast<float>(b.px0));
+            gh = fminf(gh, static_cast<float>(b.px1));
+            if (gl <= gh) {
+                fl = ok ? fminf(fl, gl) : gl;
+                fh = ok ? fmaxf(fh, gh) : gh;
+                ok = true;
+            }
+        }
+    }
+    if (!ok) return false;
     c0 = static_cast<int>(fl) / tw;
     c1 = static_cast<int>(fh) / tw;
     return true;
 }
 
-// Bin records are 32 bytes: ex, ey, A00, A01, A11, depth, px0|px1<<16, py0|py1<<16.
-__device__ __forceinline__ void store_bin(float4 *dst, const Bin &b, float depth)
+// Bin records are 32 bytes: ex, ey, A00, A01, A11, depth, px0|px1<<16,
+// py0|py1<<16; with the low-pass filter 48 bytes: then p0x, p0y, rd2, 0.
+__device__ __forceinline__ int bin_stride(bool lowpass) { return lowpass ? 3 : 2; } // float4 per record
+
+__device__ __forceinline__ void store_bin(float4 *dst, const Bin &b, float depth, bool lowpass)
 {
     dst[0] = make_float4(b.ex, b.ey, b.A00, b.A01);
     dst[1] = make_float4(b.A11, depth, __uint_as_float(static_cast<uint32_t>(b.px0) | (static_cast<uint32_t>(b.px1) << 16)),
                          __uint_as_float(static_cast<uint32_t>(b.py0) | (static_cast<uint32_t>(b.py1) << 16)));
+    if (lowpass) dst[2] = make_float4(b.p0x, b.p0y, b.rd2, 0.0f);
 }
 
-__device__ __forceinline__ Bin load_bin(const float4 *src, float &depth)
+__device__ __forceinline__ Bin load_bin(const float4 *src, float &depth, bool lowpass)
 {
     const float4 a = src[0], c = src[1];
     Bin b;
+    if (lowpass) {
+        const float4 l = src[2];
+        b.p0x = l.x;
+        b.p0y = l.y;
+        b.rd2 = l.z;
+    } else {
+        b.p0x = b.p0y = 0.0f;
+        b.rd2 = -1.0f;
+    }
     b.ex = a.x;
     b.ey = a.y;
     b.A00 = a.z;

@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const __grid_constant__ Frame
     const int v = static_cast<int>(r / fp.n);
     const ViewParams &cam = fp.v[v];
     float depth;
-    const Bin b = load_bin(bins + 2 * r, depth);
+    const bool lp = fp.lowpass != 0;
+    const Bin b = load_bin(bins + bin_stride(lp) * r, depth, lp);
     const uint64_t dbits = __float_as_uint(depth);
     const int tw = fp.tile_w, th = fp.tile_h;
     const uint32_t val = static_cast<uint32_t>(r);

@@ -28,6 +28,7 @@ void fill_frame_params(FrameParams &fp, const psi_camera *cams, int n_views, con
     fp.t_eps = o->t_eps;
     fp.opacity_radius = o->opacity_radius;
     fp.top_k = o->top_k;
+    fp.lowpass = o->lowpass;
     uint32_t tb = 0;
     int64_t pb = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -151,6 +152,18 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Fr
     }
     float lox = ceilf(sub(sub(b.ex, extx), 0.5f)), hix = floorf(sub(add(b.ex, extx), 0.5f));
     float loy = ceilf(sub(sub(b.ey, exty), 0.5f)), hiy = floorf(sub(add(b.ey, exty), 0.5f));
+    // low-pass filter: the rectangle also covers the disc 2 |x - p0|^2 <= r2b
+    const bool lp = fp.lowpass != 0;
+    b.p0x = p0x;
+    b.p0y = p0y;
+    b.rd2 = lp ? mul(r2b, 0.5f) : -1.0f;
+    if (lp) {
+        const float rd = sqrt(b.rd2);
+        lox = fminf(lox, ceilf(sub(sub(p0x, rd), 0.5f)));
+        hix = fmaxf(hix, floorf(sub(add(p0x, rd), 0.5f)));
+        loy = fminf(loy, ceilf(sub(sub(p0y, rd), 0.5f)));
+        hiy = fmaxf(hiy, floorf(sub(add(p0y, rd), 0.5f)));
+    }
     lox = fmaxf(lox, 0.0f);
     loy = fmaxf(loy, 0.0f);
     hix = fminf(hix, static_cast<float>(cam.W - 1));
@@ -164,7 +177,7 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Fr
     b.py0 = static_cast<int>(loy);
     b.py1 = static_cast<int>(hiy);
     counts[r] = count_tiles(b, fp.mode, fp.tile_w, fp.tile_h);
-    store_bin(bins + 2 * r, b, w);
+    store_bin(bins + bin_stride(lp) * r, b, w, lp);
 
     // render record (80 bytes): rows of adj(M') (q = adj(M') (x - p0x, y - p0y, 1)),
     // projected centre, opacity, support radius^2, colour, covered-pixel rectangle

@@ -39,10 +39,12 @@ __device__ __forceinline__ void pixel_of_thread(int tid, int &lx, int &ly)
 }
 
 // Staged render record after the per-tile transform: q = A (lx, ly, 1) with
-// (lx, ly) the pixel's integer offset inside the tile.
+// (lx, ly) the pixel's integer offset inside the tile; (ox, oy) = centre of the
+// tile's first pixel minus the projected centre (the low-pass term's offset).
 struct Rec {
     float a00, a01, c0, a10, a11, c1, a20, a21, c2;
     float o, r2;
+    float ox, oy;
 };
 
 __device__ __forceinline__ Rec load_rec(const float4 *r)
@@ -52,12 +54,15 @@ __device__ __forceinline__ Rec load_rec(const float4 *r)
     q.a00 = x.x; q.a01 = x.y; q.c0 = x.z; q.a10 = x.w;
     q.a11 = y.x; q.c1 = y.y; q.a20 = y.z; q.a21 = y.w;
     q.c2 = z.x; q.o = z.w; q.r2 = w.x;
+    q.ox = z.y; q.oy = z.z;
     return q;
 }
 
 struct Eval {
     float q0, q1, q2, d2, G, alpha;
     bool clamped;
+    bool filt;    // low-pass filter only: its screen-space term won
+    float dx, dy; // low-pass filter only: pixel centre minus projected centre
 };
 
 // alpha = min(0.99, o exp(-(u^2+v^2)/2)) of one surfel at one pixel (Sec. 3.1),
@@ -65,6 +70,11 @@ struct Eval {
 // disc (u^2+v^2 > r^2) or alpha < 1/255. Every operation is an explicitly
 // rounded intrinsic, so forward and adjoint kernels reproduce the same alpha
 // (and hence the same Top-K sets) bit for bit.
+// LP: the 2DGS object-space low-pass filter. The Gaussian's argument is
+// min(u^2+v^2, 2 (dx^2+dy^2)), (dx, dy) the pixel centre minus the projected
+// centre (a screen-space Gaussian of standard deviation sqrt(2)/2 pixel), and
+// the support is that argument <= r^2. The surfel's own term wins ties.
+template <bool LP = false>
 __device__ __forceinline__ bool eval_alpha(const Rec &r, float lx, float ly, Eval &e)
 {
     e.q0 = __fmaf_rn(r.a00, lx, __fmaf_rn(r.a01, ly, r.c0));
@@ -72,8 +82,19 @@ __device__ __forceinline__ bool eval_alpha(const Rec &r, float lx, float ly, Eva
     e.q2 = __fmaf_rn(r.a20, lx, __fmaf_rn(r.a21, ly, r.c2));
     const float nn = __fmaf_rn(e.q0, e.q0, __fmul_rn(e.q1, e.q1));
     const float dd = __fmul_rn(e.q2, e.q2);
-    if (!(nn <= __fmul_rn(r.r2, dd)) || !(dd > 0.0f)) return false;
-    e.d2 = __fmul_rn(nn, rcp_approx(dd));
+    if constexpr (LP) {
+        const bool ell = (nn <= __fmul_rn(r.r2, dd)) && (dd > 0.0f);
+        const float rho3 = ell ? __fmul_rn(nn, rcp_approx(dd)) : __int_as_float(0x7f800000);
+        e.dx = __fadd_rn(lx, r.ox);
+        e.dy = __fadd_rn(ly, r.oy);
+        const float rho2 = __fmul_rn(2.0f, __fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)));
+        e.filt = rho2 < rho3;
+        if (e.filt ? !(rho2 <= r.r2) : !ell) return false;
+        e.d2 = e.filt ? rho2 : rho3;
+    } else {
+        if (!(nn <= __fmul_rn(r.r2, dd)) || !(dd > 0.0f)) return false;
+        e.d2 = __fmul_rn(nn, rcp_approx(dd));
+    }
     e.G = ex2_approx(__fmul_rn(e.d2, kNegHalfLog2e));
     const float a = __fmul_rn(r.o, e.G);
     e.clamped = a > kAlphaMax;
@@ -216,6 +237,8 @@ __device__ __forceinline__ void transform_record(float4 *r, int tile_x0, int til
     x.z = __fmaf_rn(x.x, ox, __fmaf_rn(x.y, oy, x.z));
     y.y = __fmaf_rn(x.w, ox, __fmaf_rn(y.x, oy, y.y));
     z.x = __fmaf_rn(y.z, ox, __fmaf_rn(y.w, oy, z.x));
+    z.y = ox; // the projected centre becomes the tile-relative offset (low-pass term)
+    z.z = oy;
     r[0] = x;
     r[1] = y;
     r[2] = z;

@@ -16,6 +16,10 @@
 // Per-surfel sums are reduced across the warp (a transposing butterfly: 11
 // values in 13 shuffles) and added with one atomic per value per warp; the
 // feature gradient is accumulated warp-cooperatively across channels.
+// With the 2DGS low-pass filter, a pixel where the screen-space term
+// rho = 2 |x - p0|^2 wins adds dL/dp0 = 2 a (x - p0) (a = dL/dalpha * alpha)
+// instead of the (u, v) moments: 13 sums (16-slot butterfly, 16 shuffles)
+// and two more moments per record, taken through the projection of mu.
 // Both passes stream the list through the same producer-warp pipeline as the
 // forward kernel (raster.cuh): pass A front to back until every pixel is
 // saturated, pass B back to front from the largest last-composited position
@@ -30,7 +34,9 @@ namespace {
 
 using namespace raster;
 
-constexpr int kMoments = 8; // per record: dL/do, Suu, Suv, Svv, Su, Sv, Sdu, Sdv
+// per record: dL/do, Suu, Suv, Svv, Su, Sv, Sdu, Sdv; with the low-pass filter
+// also dL/dp0x, dL/dp0y and two padding floats
+__host__ __device__ constexpr int moments_per_record(bool lp) { return lp ? 12 : 8; }
 
 struct BwdArgs {
     const float4 *records;
@@ -45,7 +51,7 @@ struct BwdArgs {
     const float *g_T;   // [P_total] or NULL
     float *g_col;       // [N,3] or NULL
     float *g_feat;      // [N,D] or NULL
-    float *moments;     // [R, 8]
+    float *moments;     // [R, moments_per_record]
     DevStatus *status;
     // forward state of the same frame (all NULL: recompute it in pass A)
     const float *saved_T;      // [P_total]
@@ -92,6 +98,42 @@ __device__ __forceinline__ float warp_transpose_sum12(float v[12], int lane)
     return v[0];
 }
 
+// Sum 16 per-lane values over the warp (transposing butterfly, 16 shuffles):
+// afterwards lane l (and l ^ 1) holds the total of value index
+// 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l).
+__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[k] : v[k + 8];
+        const float keep = hi ? v[k + 8] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[k] : v[k + 4];
+        const float keep = hi ? v[k + 4] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool hi = lane & 4;
+        const float send = hi ? v[k] : v[k + 2];
+        const float keep = hi ? v[k + 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1];
+        const float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
 // Up to this many contributing lanes add their values with their own atomics
 // instead of reducing over the warp first.
 constexpr int kDirectLanes = 1;
@@ -100,10 +142,13 @@ constexpr int kDirectLanes = 1;
 // otherwise pass A recomputes them. With SAVED and K > 0 the feature terms
 // (<gF, f_j> and dL/df) come from the per-pixel feature kernel instead of this
 // walk. CH (channel chunk) matters only for K = 0.
-template <int KMAX, int DT, int CH, bool SAVED>
+template <int KMAX, int DT, int CH, bool SAVED, bool LP>
 __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED ? 4 : 3) : 1)
     render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
 {
+    constexpr int kM = moments_per_record(LP);
+    constexpr int kSums = LP ? 13 : 11; // colour (3), dL/do, moments
+    constexpr int kSlots = LP ? 16 : 12;
     __shared__ __align__(128) Pipe P;
     __shared__ int s_maxlast;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -171,7 +216,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED
                     const int j = q * 32 + __ffs(bits) - 1;
                     const Rec r = load_rec(P.rec[st][j]);
                     Eval e;
-                    const bool hit = !done && eval_alpha(r, lx, ly, e);
+                    const bool hit = !done && eval_alpha<LP>(r, lx, ly, e);
                     const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
                     if constexpr (KMAX > 0) top.offer(hit, w, lo + j);
                     if (hit) {
@@ -298,14 +343,14 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED
                     const int pos = lo + j;
                     const Rec r = load_rec(P.rec[st][j]);
                     Eval e;
-                    const bool act = inside && pos < last && eval_alpha(r, lx, ly, e);
+                    const bool act = inside && pos < last && eval_alpha<LP>(r, lx, ly, e);
                     const uint32_t amask = __ballot_sync(0xffffffffu, act);
                     if (!amask) continue;
                     const uint32_t rid = P.val[st][j];
                     const int64_t sid = static_cast<int64_t>(rid) - surf0;
-                    float vals[12];
+                    float vals[kSlots];
 #pragma unroll
-                    for (int k2 = 0; k2 < 12; ++k2) vals[k2] = 0.0f;
+                    for (int k2 = 0; k2 < kSlots; ++k2) vals[k2] = 0.0f;
                     float w = 0.0f;
                     bool sel = false;
                     if (act) {
@@ -342,7 +387,13 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED
                         vals[0] = w * gr;
                         vals[1] = w * gg;
                         vals[2] = w * gb;
-                        if (!e.clamped) {
+                        if (LP && !e.clamped && e.filt) {
+                            // rho = 2 |x - p0|^2: dL/dp0 = (-a / 2)(-4 (x - p0))
+                            const float aa = dLda * e.alpha;
+                            vals[3] = dLda * e.G;
+                            vals[kSlots > 12 ? 11 : 0] = 2.0f * aa * e.dx;
+                            vals[kSlots > 12 ? 12 : 0] = 2.0f * aa * e.dy;
+                        } else if (!e.clamped) {
                             const float rq = rcp_approx(e.q2);
                             const float u = e.q0 * rq, vv = e.q1 * rq;
                             const float d2 = u * u + vv * vv;
@@ -361,24 +412,34 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED
                         // few contributing lanes add their values directly
                         if (act) {
 #pragma unroll
-                            for (int k2 = 0; k2 < 11; ++k2) {
+                            for (int k2 = 0; k2 < kSums; ++k2) {
                                 if (vals[k2] == 0.0f) continue;
                                 if (k2 < 3) {
                                     if (a.g_col) atomicAdd(a.g_col + 3 * sid + k2, vals[k2]);
                                 } else {
-                                    atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (k2 - 3), vals[k2]);
+                                    atomicAdd(a.moments + static_cast<int64_t>(rid) * kM + (k2 - 3), vals[k2]);
                                 }
                             }
                         }
                     } else {
-                        const float tot = warp_transpose_sum12(vals, lane);
-                        const int g = ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-                        const int idx = ((lane >> 4) & 1) * 6 + ((lane >> 3) & 1) * 3 + g;
-                        if ((lane & 1) == 0 && g < 3 && tot != 0.0f) {
+                        float tot;
+                        int idx;
+                        bool mine;
+                        if constexpr (LP) {
+                            tot = warp_transpose_sum16(vals, lane);
+                            idx = (lane >> 1) & 15;
+                            mine = (lane & 1) == 0 && idx < kSums;
+                        } else {
+                            tot = warp_transpose_sum12(vals, lane);
+                            const int g = ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                            idx = ((lane >> 4) & 1) * 6 + ((lane >> 3) & 1) * 3 + g;
+                            mine = (lane & 1) == 0 && g < 3;
+                        }
+                        if (mine && tot != 0.0f) {
                             if (idx < 3) {
                                 if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
                             } else {
-                                atomicAdd(a.moments + static_cast<int64_t>(rid) * kMoments + (idx - 3), tot);
+                                atomicAdd(a.moments + static_cast<int64_t>(rid) * kM + (idx - 3), tot);
                             }
                         }
                     }
@@ -440,15 +501,18 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED
 
 // Per record: dL/dM = T^T M'^-T W (M' = T M is the map shifted to the projected
 // centre), then through M = [K R s_u t_u | K R s_v t_v | K (R mu + t)].
+template <bool LP>
 __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ FrameParams fp, psi_surfels s,
                                                     const float4 *__restrict__ moments, psi_grads g)
 {
     const int64_t total = fp.n * fp.n_views;
     const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= total) return;
-    const float4 m0 = moments[2 * r], m1 = moments[2 * r + 1];
+    constexpr int kV = moments_per_record(LP) / 4;
+    const float4 m0 = moments[kV * r], m1 = moments[kV * r + 1];
+    const float2 gp = LP ? make_float2(moments[kV * r + 2].x, moments[kV * r + 2].y) : make_float2(0.0f, 0.0f);
     if (m0.x == 0.0f && m0.y == 0.0f && m0.z == 0.0f && m0.w == 0.0f && m1.x == 0.0f && m1.y == 0.0f &&
-        m1.z == 0.0f && m1.w == 0.0f)
+        m1.z == 0.0f && m1.w == 0.0f && gp.x == 0.0f && gp.y == 0.0f)
         return;
     const int v = static_cast<int>(r / fp.n);
     const int64_t i = r - static_cast<int64_t>(v) * fp.n;
@@ -473,6 +537,13 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     const float fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
     const float w = xc[2];
     const float p0x = (fx * xc[0] + cx * w) / w, p0y = (fy * xc[1] + cy * w) / w;
+    // low-pass term: p0 = (fx X / Z + cx, fy Y / Z + cy), (X, Y, Z) = x_c
+    float gxc[3] = {0.0f, 0.0f, 0.0f};
+    if (LP) {
+        gxc[0] = gp.x * fx / w;
+        gxc[1] = gp.y * fy / w;
+        gxc[2] = -(gp.x * fx * xc[0] + gp.y * fy * xc[1]) / (w * w);
+    }
     // shifted columns of M'
     const float c0[3] = {fx * su * au[0] + (cx - p0x) * su * au[2], fy * su * au[1] + (cy - p0y) * su * au[2], su * au[2]};
     const float c1[3] = {fx * sv * av[0] + (cx - p0x) * sv * av[2], fy * sv * av[1] + (cy - p0y) * sv * av[2], sv * av[2]};
@@ -489,7 +560,12 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     A[2][1] = c0[2] * c1[0] - c0[0] * c1[2];
     A[2][2] = c0[0] * c1[1] - c0[1] * c1[0];
     const float det = c0[0] * A[0][0] + c0[1] * A[0][1] + c0[2] * A[0][2];
-    if (!(fabsf(det) > 0.0f)) return;
+    if (!(fabsf(det) > 0.0f)) {
+        // a singular map: only the low-pass term has a gradient
+        if (LP && g.mu)
+            for (int k = 0; k < 3; ++k) atomicAdd(g.mu + 3 * i + k, R[k] * gxc[0] + R[3 + k] * gxc[1] + R[6 + k] * gxc[2]);
+        return;
+    }
     const float idet = 1.0f / det;
     const float W[3][3] = {{Suu, Suv, Su}, {Suv, Svv, Sv}, {-Sdu, -Sdv, -(Suu + Svv)}};
     // G' = M'^-T W = adj^T W / det
@@ -499,16 +575,16 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     // dL/dM = T^T G': third row picks up -p0x row0 - p0y row1
     for (int b = 0; b < 3; ++b) G[2][b] = G[2][b] - p0x * G[0][b] - p0y * G[1][b];
     // columns through K^T
-    float guu[3], gvv[3], gxc[3];
+    float guu[3], gvv[3];
     guu[0] = fx * G[0][0];
     guu[1] = fy * G[1][0];
     guu[2] = cx * G[0][0] + cy * G[1][0] + G[2][0];
     gvv[0] = fx * G[0][1];
     gvv[1] = fy * G[1][1];
     gvv[2] = cx * G[0][1] + cy * G[1][1] + G[2][1];
-    gxc[0] = fx * G[0][2];
-    gxc[1] = fy * G[1][2];
-    gxc[2] = cx * G[0][2] + cy * G[1][2] + G[2][2];
+    gxc[0] += fx * G[0][2];
+    gxc[1] += fy * G[1][2];
+    gxc[2] += cx * G[0][2] + cy * G[1][2] + G[2][2];
     // uu = s_u R t_u, vv = s_v R t_v, xc = R mu + t
     float gsu = 0.0f, gsv = 0.0f;
     for (int k = 0; k < 3; ++k) {
@@ -529,16 +605,22 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     }
 }
 
-template <int KMAX, int CH, bool SAVED>
-cudaError_t launch_kcs(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+template <int KMAX, int CH, bool SAVED, bool LP>
+cudaError_t launch_kcsl(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
 {
     const unsigned grid = fp.n_tiles_total;
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH, SAVED><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    default: render_bwd_kernel<KMAX, PSI_F32, CH, SAVED><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH, SAVED, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    default: render_bwd_kernel<KMAX, PSI_F32, CH, SAVED, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
+}
+
+template <int KMAX, int CH, bool SAVED>
+cudaError_t launch_kcs(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+{
+    return fp.lowpass ? launch_kcsl<KMAX, CH, SAVED, true>(fp, f, a, st) : launch_kcsl<KMAX, CH, SAVED, false>(fp, f, a, st);
 }
 
 template <int KMAX, int CH>
@@ -560,16 +642,17 @@ cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const BwdArgs &a,
 } // namespace
 
 namespace {
-size_t moments_bytes(int64_t n_records)
+size_t moments_bytes(int64_t n_records, bool lp)
 {
-    return align_up(static_cast<size_t>(std::max<int64_t>(n_records, 1)) * kMoments * sizeof(float), 256);
+    return align_up(static_cast<size_t>(std::max<int64_t>(n_records, 1)) * moments_per_record(lp) * sizeof(float), 256);
 }
 } // namespace
 
+// sized for the low-pass layout, which is the larger one
 size_t render_bwd_workspace_bytes(int64_t n_records, int64_t n_pix, int top_k)
 {
     const size_t kd = top_k > 0 ? align_up(static_cast<size_t>(n_pix) * top_k * sizeof(float), 256) : 0;
-    return moments_bytes(n_records) + kd;
+    return moments_bytes(n_records, true) + kd;
 }
 
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
@@ -582,7 +665,8 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
         if (time_ev && time_ev[kernel][which]) cudaEventRecord(time_ev[kernel][which], st);
     };
     const int64_t R = fp.n * fp.n_views;
-    cudaError_t e = cudaMemsetAsync(ws, 0, moments_bytes(R), st);
+    const bool lp = fp.lowpass != 0;
+    cudaError_t e = cudaMemsetAsync(ws, 0, moments_bytes(R, lp), st);
     if (e != cudaSuccess || R == 0 || fp.n_tiles_total == 0) return e;
     BwdArgs a{};
     a.records = records;
@@ -605,7 +689,7 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
         a.saved_topk = saved->topk_ids;
         if (fp.top_k > 0 && a.g_F) {
             // feature terms from the saved selection: kd for the walk, dL/df
-            float *kd = reinterpret_cast<float *>(static_cast<char *>(ws) + moments_bytes(R));
+            float *kd = reinterpret_cast<float *>(static_cast<char *>(ws) + moments_bytes(R, lp));
             mark(PSI_KERNEL_BWD_FEAT, 0);
             e = launch_feat_bwd(fp, f, saved->topk_ids, saved->topk_w, a.g_F, kd, a.g_feat, st);
             if (e != cudaSuccess) return e;
@@ -626,7 +710,10 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
         e = launch_k<32>(fp, f, a, ch, st);
     if (e != cudaSuccess) return e;
     mark(PSI_KERNEL_BWD_WALK, 1);
-    chain_kernel<<<static_cast<unsigned>((R + 255) / 256), 256, 0, st>>>(fp, s, static_cast<const float4 *>(ws), g);
+    if (lp)
+        chain_kernel<true><<<static_cast<unsigned>((R + 255) / 256), 256, 0, st>>>(fp, s, static_cast<const float4 *>(ws), g);
+    else
+        chain_kernel<false><<<static_cast<unsigned>((R + 255) / 256), 256, 0, st>>>(fp, s, static_cast<const float4 *>(ws), g);
     return cudaGetLastError();
 }
 

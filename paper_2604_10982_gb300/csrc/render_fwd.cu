@@ -40,7 +40,7 @@ struct FwdArgs {
     DevStatus *status;
 };
 
-template <int KMAX, int DT, int CH>
+template <int KMAX, int DT, int CH, bool LP>
 __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
 {
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
                 const int j = q * 32 + __ffs(bits) - 1;
                 const Rec r = load_rec(P.rec[st][j]);
                 Eval e;
-                const bool hit = !done && eval_alpha(r, lx, ly, e);
+                const bool hit = !done && eval_alpha<LP>(r, lx, ly, e);
                 const float w = hit ? __fmul_rn(e.alpha, T) : 0.0f;
                 const int pos = lo + j;
                 if (hit) {
@@ -200,16 +200,22 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     }
 }
 
-template <int KMAX, int CH>
-cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
+template <int KMAX, int CH, bool LP>
+cudaError_t launch_kcl(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
 {
     const unsigned grid = fp.n_tiles_total;
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    default: render_fwd_kernel<KMAX, PSI_F32, CH><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    default: render_fwd_kernel<KMAX, PSI_F32, CH, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
+}
+
+template <int KMAX, int CH>
+cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
+{
+    return fp.lowpass ? launch_kcl<KMAX, CH, true>(fp, f, a, st) : launch_kcl<KMAX, CH, false>(fp, f, a, st);
 }
 
 template <int KMAX>

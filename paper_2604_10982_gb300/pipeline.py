@@ -98,7 +98,7 @@ class Renderer:
         R = self.V * self.n
         u8 = lambda nbytes: torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.dev)
         self.records = u8(R * psi.RECORD_BYTES)
-        self.bins = u8(R * psi.BIN_RECORD_BYTES)
+        self.bins = u8(R * (psi.BIN_RECORD_BYTES_LOWPASS if opts.lowpass else psi.BIN_RECORD_BYTES))
         self.counts = torch.empty(max(R, 1), dtype=torch.int32, device=self.dev)
         self.ws_isect = u8(psi.intersect_workspace_size(R))
         self.set_capacity(capacity)

@@ -22,6 +22,7 @@ KERNEL_BWD_FEAT, KERNEL_BWD_WALK = 1, 2  # enum psi_kernel_id
 MAX_VIEWS = 64
 RECORD_BYTES = 80
 BIN_RECORD_BYTES = 32
+BIN_RECORD_BYTES_LOWPASS = 48
 MAX_TOPK = 32
 
 _P = ctypes.c_void_p
@@ -44,7 +45,8 @@ class PsiFeatures(ctypes.Structure):
 
 class PsiRenderOpts(ctypes.Structure):
     _fields_ = [("mode", _i32), ("top_k", _i32), ("chi2", ctypes.c_float), ("z_near", ctypes.c_float),
-                ("opacity_radius", _i32), ("tile_w", _i32), ("tile_h", _i32), ("t_eps", ctypes.c_float)]
+                ("opacity_radius", _i32), ("tile_w", _i32), ("tile_h", _i32), ("t_eps", ctypes.c_float),
+                ("lowpass", _i32)]
 
 
 class PsiFwdOut(ctypes.Structure):

@@ -25,7 +25,8 @@ GROSS = 5e-2
 def opts_of(o: "orc.Opts"):
     from paper_2604_10982_gb300 import psi
     return psi.default_opts(mode=o.mode, top_k=o.top_k, chi2=o.chi2, z_near=o.z_near,
-                            opacity_radius=int(o.opacity_radius), tile_w=o.tile_w, tile_h=o.tile_h, t_eps=o.t_eps)
+                            opacity_radius=int(o.opacity_radius), tile_w=o.tile_w, tile_h=o.tile_h, t_eps=o.t_eps,
+                            lowpass=int(o.lowpass))
 
 
 def flags(out, cam):
