@@ -720,11 +720,12 @@ def run_psi(args):
     # render), eager launches, median over frames
     ablation = None
     if args.ablation_frames > 0:
-        rows = [("baseline", psi.SPHERE, 0), ("precise_tile_aabb", psi.AABB, 0), ("precise_tile_exact", psi.EXACT, 0),
-                ("topk", psi.SPHERE, K), ("full_aabb", psi.AABB, K), ("full_exact", psi.EXACT, K)]
+        rows = [("baseline", psi.SPHERE, 0, 0), ("precise_tile_aabb", psi.AABB, 0, 0),
+                ("precise_tile_exact", psi.EXACT, 0, 0), ("topk", psi.SPHERE, K, 0), ("full_aabb", psi.AABB, K, 0),
+                ("full_exact", psi.EXACT, K, 0), ("full_exact_lowpass", psi.EXACT, K, 1)]
         ablation = {}
-        for name, mode, kk in rows:
-            ao = psi.default_opts(mode=mode, top_k=kk, opacity_radius=1 if mode == psi.EXACT else 0)
+        for name, mode, kk, lp in rows:
+            ao = psi.default_opts(mode=mode, top_k=kk, opacity_radius=1 if mode == psi.EXACT else 0, lowpass=lp)
             ra = pl.Renderer(ctx, scene.n, [cams[0]], ao, 1024, D=D, F_dtype=psi.BF16, device=dev)
             nf = min(args.ablation_frames, len(cams))
             need = 0
@@ -745,7 +746,8 @@ def run_psi(args):
                     prs.append(int(ra.num_pairs.item()))
             ablation[name] = {"fwd_ms": float(np.median(ts)), "pairs_per_frame": float(np.mean(prs)),
                               "pairs_per_tile": float(np.mean(prs)) / ra.n_tiles,
-                              "tiles": {0: "sphere", 1: "aabb", 2: "exact+opacity-radius"}[mode], "top_k": kk}
+                              "tiles": {0: "sphere", 1: "aabb", 2: "exact+opacity-radius"}[mode], "top_k": kk,
+                              "lowpass": bool(lp)}
             del ra
         ablation["form"] = ("forward (project+intersect+sort+render) of one 1920x1080 frame, BF16 features, "
                             "K=0 dense / K=8 Top-K, median over %d frames" % min(args.ablation_frames, len(cams)))
