@@ -291,6 +291,44 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
                    const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
                    psi_stream stream);
 
+/* ---- launch-shape autotuner for a4 and a5 (no counterpart in the paper) ---
+ * The compositing kernels are compiled in PSI_RENDER_SHAPES launch shapes:
+ * bit 0 of a shape builds the kernel for the other number of resident CTAs
+ * per SM (top_k <= 8: 3 or 4; larger K and dense features: 1 or 2), i.e.
+ * registers per thread against occupancy; bit 1 composites dense features
+ * (top_k = 0, dim a multiple of 32) 16 channels per pass instead of 32.
+ * Every shape computes the same result: the forward bit for bit, the adjoint
+ * up to the order of its float32 atomic additions. Which one is fastest
+ * depends on K, the feature dtype, the scene and the resolution, so it is
+ * measured on the caller's own frame.
+ * psi_tune_render_fwd / psi_tune_render_bwd take the arguments of
+ * psi_render_fwd / psi_render_bwd (same requirements and errors) and run each
+ * shape that exists for them once untimed, then `reps` times between two CUDA
+ * events on `stream`; they write the mean ms per shape to ms[PSI_RENDER_SHAPES]
+ * (-1 for a shape that does not exist), the fastest to *best, and store it in
+ * the context for this (call, K class {0, <=8, <=16, <=32}, feature dtype,
+ * lowpass, and for the adjoint whether `saved` is given). Later
+ * psi_render_fwd / psi_render_bwd calls on the context launch that shape
+ * (shape 0 until tuned). They wait for the stream (PSI_ERR_INVALID_ARG inside
+ * a stream capture): tune before capturing a graph. The outputs hold a valid
+ * result afterwards; the adjoint's gradient buffers are used as scratch and
+ * are left zeroed.
+ * psi_ctx_set_render_shape / psi_ctx_get_render_shape write or read the
+ * stored shape directly: which = 0 forward, 1 adjoint; feat_dtype a
+ * psi_dtype, or -1 without features; saved 0/1 (adjoint only). */
+#define PSI_RENDER_SHAPES 4
+int psi_tune_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
+                        const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
+                        const psi_render_opts *o, const psi_fwd_out *out, int reps, float *ms, int *best,
+                        psi_stream stream);
+int psi_tune_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
+                        const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
+                        const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
+                        const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
+                        int reps, float *ms, int *best, psi_stream stream);
+int psi_ctx_set_render_shape(psi_ctx *ctx, int which, const psi_render_opts *o, int feat_dtype, int saved, int shape);
+int psi_ctx_get_render_shape(psi_ctx *ctx, int which, const psi_render_opts *o, int feat_dtype, int saved, int *shape);
+
 /* ---- a6: query decode (Sec. 4.1, Eq. 4 without the monotone sigmoid) -----
  * logits[p,q] = sum_c F[p,c] Q[q,c] on the tensor cores (BF16 in, FP32
  * accumulate), ids[p] = argmax_q (lowest q on ties), or -1 where 1 - T[p] <

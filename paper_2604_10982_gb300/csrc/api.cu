@@ -15,6 +15,10 @@ struct psi_ctx {
     void *cublas; // created on first use by psi_frustum_attention
     // armed kernel-timing events per psi_kernel_id: [id][0] begin, [id][1] end
     cudaEvent_t time_ev[3][2];
+    // launch shape of the compositing kernels per (K class, feature dtype,
+    // low-pass[, saved state]) (0 = default; set by the autotuner)
+    uint8_t shape_fwd[4][3][2];
+    uint8_t shape_bwd[4][3][2][2];
 };
 
 namespace {
@@ -88,14 +92,6 @@ int check_feat(psi_ctx *ctx, const psi_features *f, psi::FeatView &fv)
     if (!aligned(f->data, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "feature rows must be 16-byte aligned");
     fv = psi::FeatView{f->data, f->scale, f->dtype, f->dim};
     return PSI_OK;
-}
-
-int64_t n_tiles_of(const psi_camera *cams, int n_views, const psi_render_opts *o)
-{
-    int64_t t = 0;
-    for (int v = 0; v < n_views; ++v)
-        t += static_cast<int64_t>((cams[v].width + o->tile_w - 1) / o->tile_w) * ((cams[v].height + o->tile_h - 1) / o->tile_h);
-    return t;
 }
 
 struct DeviceGuard {
@@ -321,14 +317,69 @@ int psi_sort_keys_noalloc(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const in
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_sort_keys_noalloc", e);
 }
 
-int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
-                   const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
-                   const psi_render_opts *o, const psi_fwd_out *out, psi_stream stream)
+} // extern "C"
+
+namespace {
+
+int k_class(int K) { return K == 0 ? 0 : K <= 8 ? 1 : K <= 16 ? 2 : 3; }
+int dt_class(int dtype) { return dtype == PSI_BF16 ? 1 : dtype == PSI_FP8_E4M3 ? 2 : 0; }
+
+uint8_t &fwd_shape(psi_ctx *ctx, const psi::FrameParams &fp, const psi::FeatView &fv)
 {
-    if (!ctx) return PSI_ERR_INVALID_ARG;
+    return ctx->shape_fwd[k_class(fp.top_k)][fv.data ? dt_class(fv.dtype) : 0][fp.lowpass ? 1 : 0];
+}
+
+uint8_t &bwd_shape(psi_ctx *ctx, const psi::FrameParams &fp, const psi::FeatView &fv, bool saved)
+{
+    return ctx->shape_bwd[k_class(fp.top_k)][fv.data ? dt_class(fv.dtype) : 0][fp.lowpass ? 1 : 0][saved ? 1 : 0];
+}
+
+// Runs launch(shape) for every shape that exists for (D, K): once untimed,
+// then `reps` times between two events on the stream; ms[shape] = mean ms
+// (-1: shape does not exist), *best = the fastest.
+template <class Launch>
+int time_shapes(psi_ctx *ctx, int D, int K, int reps, cudaStream_t st, Launch launch, float *ms, int *best,
+                const char *who)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "%s: cannot time shapes inside a stream capture", who);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_ms = 0.0f;
+    int b = -1;
+    for (int sh = 0; sh < psi::kShapes && e == cudaSuccess; ++sh) {
+        ms[sh] = -1.0f;
+        if (!psi::render_shape_valid(D, K, sh)) continue;
+        e = launch(sh);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch(sh);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess) {
+            ms[sh] = t / static_cast<float>(reps);
+            if (b < 0 || ms[sh] < best_ms) {
+                best_ms = ms[sh];
+                b = sh;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, who, e);
+    *best = b;
+    return PSI_OK;
+}
+
+int prepare_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
+                const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
+                const psi_render_opts *o, const psi_fwd_out *out, psi::FrameParams &fp, psi::FeatView &fv)
+{
     int rc;
     if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o))) return rc;
-    psi::FeatView fv;
     if ((rc = check_feat(ctx, f, fv))) return rc;
     if (!out || !out->rgb || !out->T) return fail(ctx, PSI_ERR_INVALID_ARG, "out.rgb and out.T are required");
     if (out->F && out->F_dtype != PSI_F32 && out->F_dtype != PSI_BF16)
@@ -339,24 +390,18 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
     if (!records || !vals || !tile_ranges) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
     if (!aligned(records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 16-byte aligned");
     if (n_surfels < 0) return fail(ctx, PSI_ERR_INVALID_ARG, "n_surfels < 0");
-    DeviceGuard g(ctx->device);
-    psi::FrameParams fp;
     psi::fill_frame_params(fp, cams, n_views, o, n_surfels);
-    cudaError_t e = psi::launch_render_fwd(fp, fv, static_cast<const float4 *>(records), vals, tile_ranges, *out,
-                                           ctx->status, reinterpret_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_render_fwd", e);
+    return PSI_OK;
 }
 
-int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
-                   const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
-                   const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
-                   const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
-                   psi_stream stream)
+int prepare_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
+                const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
+                const psi_render_opts *o, const float *g_rgb, const float *g_F, const psi_fwd_out *saved,
+                const psi_grads *grads, void *workspace, size_t workspace_bytes, psi::FrameParams &fp,
+                psi::FeatView &fv)
 {
-    if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc;
     if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o)) || (rc = check_surfels(ctx, s))) return rc;
-    psi::FeatView fv;
     if ((rc = check_feat(ctx, f, fv))) return rc;
     if (!records || !vals || !tile_ranges || !g_rgb || !grads) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL input");
     if (!aligned(records, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "records must be 16-byte aligned");
@@ -374,14 +419,135 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
     const size_t need = psi::render_bwd_workspace_bytes(s->n * n_views, n_pix_total, o->top_k);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
         return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
-    DeviceGuard g(ctx->device);
-    psi::FrameParams fp;
     psi::fill_frame_params(fp, cams, n_views, o, s->n);
+    return PSI_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
+                   const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
+                   const psi_render_opts *o, const psi_fwd_out *out, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    psi::FrameParams fp;
+    psi::FeatView fv;
+    int rc = prepare_fwd(ctx, f, records, vals, tile_ranges, cams, n_views, n_surfels, o, out, fp, fv);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_render_fwd(fp, fv, static_cast<const float4 *>(records), vals, tile_ranges, *out,
+                                           ctx->status, reinterpret_cast<cudaStream_t>(stream), fwd_shape(ctx, fp, fv));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_render_fwd", e);
+}
+
+int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
+                   const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
+                   const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
+                   const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
+                   psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    psi::FrameParams fp;
+    psi::FeatView fv;
+    int rc = prepare_bwd(ctx, s, f, records, vals, tile_ranges, cams, n_views, o, g_rgb, g_F, saved, grads, workspace,
+                         workspace_bytes, fp, fv);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
     cudaError_t e = psi::launch_render_bwd(fp, *s, fv, static_cast<const float4 *>(records), vals, tile_ranges, g_rgb,
                                            g_F, g_T, saved, *grads, workspace, ctx->status,
-                                           reinterpret_cast<cudaStream_t>(stream), ctx->time_ev);
+                                           reinterpret_cast<cudaStream_t>(stream), ctx->time_ev,
+                                           bwd_shape(ctx, fp, fv, saved != nullptr));
     for (int k = PSI_KERNEL_BWD_FEAT; k <= PSI_KERNEL_BWD_WALK; ++k) ctx->time_ev[k][0] = ctx->time_ev[k][1] = nullptr;
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_render_bwd", e);
+}
+
+int psi_tune_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
+                        const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
+                        const psi_render_opts *o, const psi_fwd_out *out, int reps, float *ms, int *best,
+                        psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (reps < 1 || !ms || !best) return fail(ctx, PSI_ERR_INVALID_ARG, "need reps >= 1, ms and best");
+    psi::FrameParams fp;
+    psi::FeatView fv;
+    int rc = prepare_fwd(ctx, f, records, vals, tile_ranges, cams, n_views, n_surfels, o, out, fp, fv);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    auto launch = [&](int shape) {
+        return psi::launch_render_fwd(fp, fv, static_cast<const float4 *>(records), vals, tile_ranges, *out,
+                                      ctx->status, st, shape);
+    };
+    rc = time_shapes(ctx, fv.data ? fv.dim : 16, fp.top_k, reps, st, launch, ms, best, "psi_tune_render_fwd");
+    if (rc) return rc;
+    fwd_shape(ctx, fp, fv) = static_cast<uint8_t>(*best);
+    return PSI_OK;
+}
+
+int psi_tune_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const void *records,
+                        const uint32_t *vals, const uint32_t *tile_ranges, const psi_camera *cams, int n_views,
+                        const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
+                        const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
+                        int reps, float *ms, int *best, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (reps < 1 || !ms || !best) return fail(ctx, PSI_ERR_INVALID_ARG, "need reps >= 1, ms and best");
+    psi::FrameParams fp;
+    psi::FeatView fv;
+    int rc = prepare_bwd(ctx, s, f, records, vals, tile_ranges, cams, n_views, o, g_rgb, g_F, saved, grads, workspace,
+                         workspace_bytes, fp, fv);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    auto launch = [&](int shape) {
+        return psi::launch_render_bwd(fp, *s, fv, static_cast<const float4 *>(records), vals, tile_ranges, g_rgb, g_F,
+                                      g_T, saved, *grads, workspace, ctx->status, st, nullptr, shape);
+    };
+    rc = time_shapes(ctx, fv.data ? fv.dim : 16, fp.top_k, reps, st, launch, ms, best, "psi_tune_render_bwd");
+    if (rc) return rc;
+    bwd_shape(ctx, fp, fv, saved != nullptr) = static_cast<uint8_t>(*best);
+    // the gradient buffers served as scratch: leave them zeroed
+    const size_t n = static_cast<size_t>(s->n);
+    const struct {
+        float *p;
+        size_t count;
+    } bufs[] = {{grads->mu, 3 * n},      {grads->tu, 3 * n},  {grads->tv, 3 * n},
+                {grads->scale, 2 * n},   {grads->opacity, n}, {grads->rgb, 3 * n},
+                {fv.data ? grads->feat : nullptr, fv.data ? n * static_cast<size_t>(fv.dim) : 0}};
+    for (const auto &b : bufs) {
+        if (!b.p || !b.count) continue;
+        cudaError_t e = cudaMemsetAsync(b.p, 0, b.count * sizeof(float), st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "psi_tune_render_bwd", e);
+    }
+    return PSI_OK;
+}
+
+int psi_ctx_set_render_shape(psi_ctx *ctx, int which, const psi_render_opts *o, int feat_dtype, int saved, int shape)
+{
+    if (!ctx || !o) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (which != 0 && which != 1) return fail(ctx, PSI_ERR_INVALID_ARG, "which must be 0 (forward) or 1 (adjoint)");
+    if (shape < 0 || shape >= psi::kShapes) return fail(ctx, PSI_ERR_INVALID_ARG, "shape %d out of range", shape);
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    const int kc = k_class(o->top_k), dc = feat_dtype < 0 ? 0 : dt_class(feat_dtype), lp = o->lowpass ? 1 : 0;
+    if (which == 0)
+        ctx->shape_fwd[kc][dc][lp] = static_cast<uint8_t>(shape);
+    else
+        ctx->shape_bwd[kc][dc][lp][saved ? 1 : 0] = static_cast<uint8_t>(shape);
+    return PSI_OK;
+}
+
+int psi_ctx_get_render_shape(psi_ctx *ctx, int which, const psi_render_opts *o, int feat_dtype, int saved, int *shape)
+{
+    if (!ctx || !o || !shape) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (which != 0 && which != 1) return fail(ctx, PSI_ERR_INVALID_ARG, "which must be 0 (forward) or 1 (adjoint)");
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    const int kc = k_class(o->top_k), dc = feat_dtype < 0 ? 0 : dt_class(feat_dtype), lp = o->lowpass ? 1 : 0;
+    *shape = which == 0 ? ctx->shape_fwd[kc][dc][lp] : ctx->shape_bwd[kc][dc][lp][saved ? 1 : 0];
+    return PSI_OK;
 }
 
 int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,

@@ -188,8 +188,30 @@ struct FeatView {
     int dim;
 };
 
+// Launch shapes of the compositing kernels (a4, a5), picked per workload by
+// the autotuner: bit 0 builds the kernel for the alternative number of CTAs
+// per SM (registers per thread against occupancy), bit 1 composites dense
+// features (K = 0) 16 channels per pass instead of 32. Every shape computes
+// the same result.
+constexpr int kShapeAltOcc = 1;
+constexpr int kShapeAltChunk = 2;
+constexpr int kShapes = 4;
+// channels per pass of the dense feature path for this shape
+inline int render_channel_chunk(int D, int K, int shape)
+{
+    const int ch = (D % 32 == 0) ? 32 : 16;
+    return (K == 0 && (shape & kShapeAltChunk)) ? 16 : ch;
+}
+// shapes that differ from shape 0 in something that exists for (D, K)
+inline bool render_shape_valid(int D, int K, int shape)
+{
+    if (shape < 0 || shape >= kShapes) return false;
+    return !(shape & kShapeAltChunk) || (K == 0 && D % 32 == 0);
+}
+
 cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const float4 *records, const uint32_t *vals,
-                              const uint32_t *ranges, const psi_fwd_out &out, DevStatus *status, cudaStream_t st);
+                              const uint32_t *ranges, const psi_fwd_out &out, DevStatus *status, cudaStream_t st,
+                              int shape);
 
 size_t render_bwd_workspace_bytes(int64_t n_records, int64_t n_pix, int top_k);
 cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int32_t *topk_ids, const float *topk_w,
@@ -197,7 +219,7 @@ cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int3
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
-                              DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2]);
+                              DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2], int shape);
 
 size_t attention_workspace_bytes(int64_t n, int C, int d, int n_q);
 cudaError_t launch_attention(void *cublas, const psi_surfels &s, const void *feat, const float *fscale, int dtype, int C,

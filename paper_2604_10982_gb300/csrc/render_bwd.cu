@@ -142,8 +142,9 @@ constexpr int kDirectLanes = 1;
 // otherwise pass A recomputes them. With SAVED and K > 0 the feature terms
 // (<gF, f_j> and dL/df) come from the per-pixel feature kernel instead of this
 // walk. CH (channel chunk) matters only for K = 0.
-template <int KMAX, int DT, int CH, bool SAVED, bool LP>
-__global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? (SAVED ? 4 : 3) : 1)
+// OCC: CTAs per SM the kernel is built for (the launch shape the autotuner picks)
+template <int KMAX, int DT, int CH, bool SAVED, bool LP, int OCC>
+__global__ void __launch_bounds__(kPipeThreads, OCC)
     render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
 {
     constexpr int kM = moments_per_record(LP);
@@ -605,38 +606,53 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     }
 }
 
-template <int KMAX, int CH, bool SAVED, bool LP>
-cudaError_t launch_kcsl(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+template <int KMAX, int CH, bool SAVED, bool LP, int OCC>
+cudaError_t launch_kcslo(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
 {
     const unsigned grid = fp.n_tiles_total;
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH, SAVED, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    default: render_bwd_kernel<KMAX, PSI_F32, CH, SAVED, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3:
+        render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH, SAVED, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a);
+        break;
+    default: render_bwd_kernel<KMAX, PSI_F32, CH, SAVED, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
 }
 
-template <int KMAX, int CH, bool SAVED>
-cudaError_t launch_kcs(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+template <int KMAX, int CH, bool SAVED, bool LP>
+cudaError_t launch_kcsl(const FrameParams &fp, const FeatView &f, const BwdArgs &a, bool alt, cudaStream_t st)
 {
-    return fp.lowpass ? launch_kcsl<KMAX, CH, SAVED, true>(fp, f, a, st) : launch_kcsl<KMAX, CH, SAVED, false>(fp, f, a, st);
+    // K <= 8: 4 CTAs per SM with the saved state (56 registers), 3 when pass A
+    // recomputes it; larger K (register Top-K of 16 or 32) and dense: 1 or 2
+    constexpr bool small = KMAX > 0 && KMAX <= 8;
+    constexpr int occ = small ? (SAVED ? 4 : 3) : 1;
+    constexpr int occ_alt = small ? (SAVED ? 3 : 4) : 2;
+    return alt ? launch_kcslo<KMAX, CH, SAVED, LP, occ_alt>(fp, f, a, st)
+               : launch_kcslo<KMAX, CH, SAVED, LP, occ>(fp, f, a, st);
+}
+
+template <int KMAX, int CH, bool SAVED>
+cudaError_t launch_kcs(const FrameParams &fp, const FeatView &f, const BwdArgs &a, bool alt, cudaStream_t st)
+{
+    return fp.lowpass ? launch_kcsl<KMAX, CH, SAVED, true>(fp, f, a, alt, st)
+                      : launch_kcsl<KMAX, CH, SAVED, false>(fp, f, a, alt, st);
 }
 
 template <int KMAX, int CH>
-cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
+cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const BwdArgs &a, bool alt, cudaStream_t st)
 {
-    return a.saved_T ? launch_kcs<KMAX, CH, true>(fp, f, a, st) : launch_kcs<KMAX, CH, false>(fp, f, a, st);
+    return a.saved_T ? launch_kcs<KMAX, CH, true>(fp, f, a, alt, st) : launch_kcs<KMAX, CH, false>(fp, f, a, alt, st);
 }
 
 template <int KMAX>
-cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const BwdArgs &a, int ch, cudaStream_t st)
+cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const BwdArgs &a, int ch, bool alt, cudaStream_t st)
 {
     // the channel chunk only shapes the dense (K = 0) feature dot product
     if constexpr (KMAX > 0)
-        return launch_kc<KMAX, 16>(fp, f, a, st);
+        return launch_kc<KMAX, 16>(fp, f, a, alt, st);
     else
-        return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
+        return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, alt, st) : launch_kc<KMAX, 16>(fp, f, a, alt, st);
 }
 
 } // namespace
@@ -658,7 +674,7 @@ size_t render_bwd_workspace_bytes(int64_t n_records, int64_t n_pix, int top_k)
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,
-                              DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2])
+                              DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2], int shape)
 {
     // optional timing events around one kernel (see psi_ctx_time_kernel)
     auto mark = [&](int kernel, int which) {
@@ -697,17 +713,18 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
             a.kd_saved = kd;
         }
     }
-    const int ch = (f.dim % 32 == 0) ? 32 : 16;
     const int K = fp.top_k;
+    const int ch = render_channel_chunk(f.dim, K, shape);
+    const bool alt = shape & kShapeAltOcc;
     mark(PSI_KERNEL_BWD_WALK, 0);
     if (K == 0)
-        e = launch_k<0>(fp, f, a, ch, st);
+        e = launch_k<0>(fp, f, a, ch, alt, st);
     else if (K <= 8)
-        e = launch_k<8>(fp, f, a, ch, st);
+        e = launch_k<8>(fp, f, a, ch, alt, st);
     else if (K <= 16)
-        e = launch_k<16>(fp, f, a, ch, st);
+        e = launch_k<16>(fp, f, a, ch, alt, st);
     else
-        e = launch_k<32>(fp, f, a, ch, st);
+        e = launch_k<32>(fp, f, a, ch, alt, st);
     if (e != cudaSuccess) return e;
     mark(PSI_KERNEL_BWD_WALK, 1);
     if (lp)

@@ -40,8 +40,9 @@ struct FwdArgs {
     DevStatus *status;
 };
 
-template <int KMAX, int DT, int CH, bool LP>
-__global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
+// OCC: CTAs per SM the kernel is built for (the launch shape the autotuner picks)
+template <int KMAX, int DT, int CH, bool LP, int OCC>
+__global__ void __launch_bounds__(kPipeThreads, OCC)
     render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
 {
     __shared__ __align__(128) Pipe P;
@@ -200,39 +201,48 @@ __global__ void __launch_bounds__(kPipeThreads, (KMAX > 0 && KMAX <= 8) ? 3 : 1)
     }
 }
 
-template <int KMAX, int CH, bool LP>
-cudaError_t launch_kcl(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
+template <int KMAX, int CH, bool LP, int OCC>
+cudaError_t launch_kclo(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
 {
     const unsigned grid = fp.n_tiles_total;
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    default: render_fwd_kernel<KMAX, PSI_F32, CH, LP><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    default: render_fwd_kernel<KMAX, PSI_F32, CH, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
 }
 
-template <int KMAX, int CH>
-cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
+template <int KMAX, int CH, bool LP>
+cudaError_t launch_kcl(const FrameParams &fp, const FeatView &f, const FwdArgs &a, bool alt, cudaStream_t st)
 {
-    return fp.lowpass ? launch_kcl<KMAX, CH, true>(fp, f, a, st) : launch_kcl<KMAX, CH, false>(fp, f, a, st);
+    constexpr int occ = (KMAX > 0 && KMAX <= 8) ? 3 : 1;
+    constexpr int occ_alt = (KMAX > 0 && KMAX <= 8) ? 4 : 2;
+    return alt ? launch_kclo<KMAX, CH, LP, occ_alt>(fp, f, a, st) : launch_kclo<KMAX, CH, LP, occ>(fp, f, a, st);
+}
+
+template <int KMAX, int CH>
+cudaError_t launch_kc(const FrameParams &fp, const FeatView &f, const FwdArgs &a, bool alt, cudaStream_t st)
+{
+    return fp.lowpass ? launch_kcl<KMAX, CH, true>(fp, f, a, alt, st) : launch_kcl<KMAX, CH, false>(fp, f, a, alt, st);
 }
 
 template <int KMAX>
-cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FwdArgs &a, int ch, cudaStream_t st)
+cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FwdArgs &a, int ch, bool alt, cudaStream_t st)
 {
     if (fp.n_tiles_total == 0) return cudaSuccess;
     // the channel chunk only shapes the dense (K = 0) accumulation
     if constexpr (KMAX > 0)
-        return launch_kc<KMAX, 16>(fp, f, a, st);
+        return launch_kc<KMAX, 16>(fp, f, a, alt, st);
     else
-        return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, st) : launch_kc<KMAX, 16>(fp, f, a, st);
+        return ch == 32 ? launch_kc<KMAX, 32>(fp, f, a, alt, st) : launch_kc<KMAX, 16>(fp, f, a, alt, st);
 }
 
 } // namespace
 
 cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const float4 *records, const uint32_t *vals,
-                              const uint32_t *ranges, const psi_fwd_out &out, DevStatus *status, cudaStream_t st)
+                              const uint32_t *ranges, const psi_fwd_out &out, DevStatus *status, cudaStream_t st,
+                              int shape)
 {
     FwdArgs a{};
     a.records = records;
@@ -254,20 +264,21 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
     a.argmax = out.argmax;
     a.status = status;
     const int K = fp.top_k;
-    const int ch = (f.dim % 32 == 0) ? 32 : 16;
+    const int ch = render_channel_chunk(f.dim, K, shape);
+    const bool alt = shape & kShapeAltOcc;
     if (K == 0) {
         // dense: one pass per chunk of channels (the first also writes rgb/T)
-        cudaError_t e = launch_k<0>(fp, f, a, ch, st);
+        cudaError_t e = launch_k<0>(fp, f, a, ch, alt, st);
         for (int c0 = ch; e == cudaSuccess && f.data && out.F && c0 < f.dim; c0 += ch) {
             a.c0 = c0;
             a.write_rgb = 0;
-            e = launch_k<0>(fp, f, a, ch, st);
+            e = launch_k<0>(fp, f, a, ch, alt, st);
         }
         return e;
     }
-    if (K <= 8) return launch_k<8>(fp, f, a, ch, st);
-    if (K <= 16) return launch_k<16>(fp, f, a, ch, st);
-    return launch_k<32>(fp, f, a, ch, st);
+    if (K <= 8) return launch_k<8>(fp, f, a, ch, alt, st);
+    if (K <= 16) return launch_k<16>(fp, f, a, ch, alt, st);
+    return launch_k<32>(fp, f, a, ch, alt, st);
 }
 
 } // namespace psi

@@ -208,6 +208,37 @@ class Renderer:
                            None if recompute else self.saved_state(), gs, self.ws_bwd, stream)
         return grads
 
+    def tune(self, scene: DeviceScene, g_rgb, g_F=None, g_T=None, grads=None, want_F: bool = True, reps: int = 3,
+             recompute: bool = False, stream=None):
+        """Pick the launch shapes of the compositing kernels for this workload
+        by timing each on the current frame (call frame() first; not inside a
+        graph capture). The context keeps the choice for later render() and
+        backward() calls. Returns {"fwd": (ms per shape, best), "bwd": ...}; the
+        gradient buffers, if given, are left zeroed."""
+        feats = scene.features_struct()
+        out = psi.PsiFwdOut(psi._ptr(self.rgb), psi._ptr(self.T), psi._ptr(self.n_last),
+                            psi._ptr(self.F) if (want_F and self.F is not None) else None, int(self.F_dtype),
+                            psi._ptr(self.topk_ids), psi._ptr(self.topk_w), None)
+        fwd = psi.psi_tune_render_fwd(self.ctx, feats, self.records, self.vals, self.ranges, self.cams, self.V, self.n,
+                                      self.opts, out, reps, stream)
+        dev = self.dev
+        n, D = self.n, scene.D
+        if grads is None:
+            grads = dict(mu=torch.zeros(n, 3, device=dev), tu=torch.zeros(n, 3, device=dev),
+                         tv=torch.zeros(n, 3, device=dev), scale=torch.zeros(n, 2, device=dev),
+                         opacity=torch.zeros(n, device=dev), rgb=torch.zeros(n, 3, device=dev),
+                         feat=torch.zeros(n, D, device=dev) if D else None)
+        if not hasattr(self, "ws_bwd"):
+            self.ws_bwd = torch.empty(psi.render_bwd_workspace_size(self.V * self.n, self.n_pix, int(self.opts.top_k)),
+                                      dtype=torch.uint8, device=dev)
+        gs = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
+        bwd = psi.psi_tune_render_bwd(self.ctx, scene.surfels_struct(), feats, self.records, self.vals, self.ranges,
+                                      self.cams, self.V, self.opts, g_rgb.contiguous(),
+                                      None if g_F is None else g_F.contiguous(),
+                                      None if g_T is None else g_T.contiguous(),
+                                      None if recompute else self.saved_state(), gs, self.ws_bwd, reps, stream)
+        return {"fwd": fwd, "bwd": bwd}
+
     def frame(self, scene: DeviceScene, want_F: bool = True, stream=None):
         self.project(scene, stream)
         self.intersect(stream)

@@ -98,6 +98,18 @@ def lib():
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.psi_tune_render_fwd.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _P, _P, ctypes.POINTER(PsiCamera),
+                                          ctypes.c_int, _i64, ctypes.POINTER(PsiRenderOpts),
+                                          ctypes.POINTER(PsiFwdOut), ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
+                                          _P]
+        L.psi_tune_render_bwd.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures), _P, _P, _P,
+                                          ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P,
+                                          _P, _P, ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz,
+                                          ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int), _P]
+        L.psi_ctx_set_render_shape.argtypes = [_P, ctypes.c_int, ctypes.POINTER(PsiRenderOpts), ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int]
+        L.psi_ctx_get_render_shape.argtypes = [_P, ctypes.c_int, ctypes.POINTER(PsiRenderOpts), ctypes.c_int,
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.psi_attention_workspace_size.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(sz)]
         L.psi_frustum_attention.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiFeatures),
                                             ctypes.POINTER(PsiCamera), ctypes.c_float, _P, ctypes.c_int, _P, _P, _P,
@@ -283,6 +295,48 @@ def psi_render_bwd(ctx, s, feats, records, vals, tile_ranges, cams_arr, n_views,
                                    _ptr(g_T), None if saved is None else ctypes.byref(saved), ctypes.byref(grads),
                                    _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), _stream(stream)), "psi_render_bwd")
+
+
+RENDER_SHAPES = 4
+
+
+def psi_tune_render_fwd(ctx, feats, records, vals, tile_ranges, cams_arr, n_views, n_surfels, opts, out: PsiFwdOut,
+                        reps=3, stream=None):
+    """Time every launch shape of the forward compositing kernel on this
+    frame, keep the fastest in the context; returns (ms per shape, best)."""
+    ms = (ctypes.c_float * RENDER_SHAPES)()
+    best = ctypes.c_int(-1)
+    ctx.check(lib().psi_tune_render_fwd(ctx.handle, ctypes.byref(feats), _ptr(records), _ptr(vals),
+                                        _ptr(tile_ranges), cams_arr, n_views, int(n_surfels), ctypes.byref(opts),
+                                        ctypes.byref(out), int(reps), ms, ctypes.byref(best), _stream(stream)),
+              "psi_tune_render_fwd")
+    return [float(x) for x in ms], int(best.value)
+
+
+def psi_tune_render_bwd(ctx, s, feats, records, vals, tile_ranges, cams_arr, n_views, opts, g_rgb, g_F, g_T,
+                        saved, grads: PsiGrads, workspace, reps=3, stream=None):
+    """The same for the adjoint (the gradient buffers are left zeroed)."""
+    ms = (ctypes.c_float * RENDER_SHAPES)()
+    best = ctypes.c_int(-1)
+    ctx.check(lib().psi_tune_render_bwd(ctx.handle, ctypes.byref(s), ctypes.byref(feats), _ptr(records), _ptr(vals),
+                                        _ptr(tile_ranges), cams_arr, n_views, ctypes.byref(opts), _ptr(g_rgb),
+                                        _ptr(g_F), _ptr(g_T), None if saved is None else ctypes.byref(saved),
+                                        ctypes.byref(grads), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), int(reps), ms,
+                                        ctypes.byref(best), _stream(stream)), "psi_tune_render_bwd")
+    return [float(x) for x in ms], int(best.value)
+
+
+def psi_ctx_set_render_shape(ctx, which, opts, feat_dtype, saved, shape):
+    ctx.check(lib().psi_ctx_set_render_shape(ctx.handle, int(which), ctypes.byref(opts), int(feat_dtype), int(saved),
+                                             int(shape)), "psi_ctx_set_render_shape")
+
+
+def psi_ctx_get_render_shape(ctx, which, opts, feat_dtype, saved):
+    v = ctypes.c_int(-1)
+    ctx.check(lib().psi_ctx_get_render_shape(ctx.handle, int(which), ctypes.byref(opts), int(feat_dtype), int(saved),
+                                             ctypes.byref(v)), "psi_ctx_get_render_shape")
+    return int(v.value)
 
 
 def psi_ctx_time_kernel(ctx, kernel, ev_begin, ev_end):

@@ -59,3 +59,12 @@ def test_ctx_create_without_device_fails_cleanly(lib):
 def test_time_kernel_rejects_bad_arguments(lib):
     # no context: refused before anything touches a device
     assert lib.psi_ctx_time_kernel(None, psi.KERNEL_BWD_WALK, None, None) == psi.PSI_ERR_INVALID_ARG
+
+
+def test_render_shape_calls_check_arguments(lib):
+    """The launch-shape calls refuse a missing context before touching a GPU."""
+    o = psi.default_opts(top_k=8)
+    v = ctypes.c_int(-1)
+    assert lib.psi_ctx_set_render_shape(None, 0, ctypes.byref(o), psi.F32, 0, 1) == psi.PSI_ERR_INVALID_ARG
+    assert lib.psi_ctx_get_render_shape(None, 1, ctypes.byref(o), psi.F32, 1, ctypes.byref(v)) == psi.PSI_ERR_INVALID_ARG
+    assert psi.RENDER_SHAPES == 4
