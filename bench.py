@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--surfels", type=int, default=3_000_000)
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--ablation-frames", type=int, default=6, help="frames per Table-3 row (0: skip)")
     ap.add_argument("--label-frames", type=int, default=8, help="frames of the instance-label path (0: skip)")
@@ -328,9 +329,19 @@ def run_psi(args):
     # runs eagerly so that the library can bracket its kernels with the
     # per-step timing events below (a graph replay cannot record them)
     EAGER = {"render_bwd"}
-    # warm every code path once (lazy buffers, function attributes), then capture
+    # warm every code path once (lazy buffers, function attributes), let the
+    # library pick the compositing kernels' launch shapes on frame 0, then
+    # capture (the graphs keep the tuned shapes)
     for fn in stage_fns(0):
         fn()
+    torch.cuda.synchronize()
+    tuned = None
+    if not args.no_tune:
+        tr = r.tune(scene, gC, gF, gT, grads=grads, reps=3)
+        tuned = {"forward": {"ms_per_shape": [round(x, 4) for x in tr["fwd"][0]], "shape": tr["fwd"][1]},
+                 "adjoint": {"ms_per_shape": [round(x, 4) for x in tr["bwd"][0]], "shape": tr["bwd"][1]},
+                 "shapes": "bit 0: the other CTAs-per-SM build (K<=8: 3/4, else 1/2); bit 1: dense 16-channel passes; "
+                           "-1: shape does not apply; timed on frame 0 before the graphs are captured"}
     torch.cuda.synchronize()
     use_graph = not args.no_graph
     graphs = None
@@ -776,7 +787,7 @@ def run_psi(args):
         "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)}, "kernel_ms": kernel_ms,
         "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
-        "plain_fp32": plain, "ablation": ablation, "labels": labels, "regularisers": regs, "attention": attn, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "autotune": tuned, "plain_fp32": plain, "ablation": ablation, "labels": labels, "regularisers": regs, "attention": attn, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),
         "clocks": clk, "paper_context": PAPER_CONTEXT, "setup_s": setup_s,
     }
