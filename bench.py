@@ -340,7 +340,7 @@ def run_psi(args):
         tr = r.tune(scene, gC, gF, gT, grads=grads, reps=3)
         tuned = {"forward": {"ms_per_shape": [round(x, 4) for x in tr["fwd"][0]], "shape": tr["fwd"][1]},
                  "adjoint": {"ms_per_shape": [round(x, 4) for x in tr["bwd"][0]], "shape": tr["bwd"][1]},
-                 "shapes": "bit 0: the other CTAs-per-SM build (K<=8: 3/4, else 1/2); bit 1: dense 16-channel passes; "
+                 "shapes": "bit 0: the other CTAs-per-SM build (K<=8: 3<->4, else 2->1); bit 1: dense 16-channel passes; "
                            "-1: shape does not apply; timed on frame 0 before the graphs are captured"}
     torch.cuda.synchronize()
     use_graph = not args.no_graph

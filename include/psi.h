@@ -294,8 +294,9 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
 /* ---- launch-shape autotuner for a4 and a5 (no counterpart in the paper) ---
  * The compositing kernels are compiled in PSI_RENDER_SHAPES launch shapes:
  * bit 0 of a shape builds the kernel for the other number of resident CTAs
- * per SM (top_k <= 8: 3 or 4; larger K and dense features: 1 or 2), i.e.
- * registers per thread against occupancy; bit 1 composites dense features
+ * per SM (top_k <= 8: forward 3 -> 4, adjoint 4 -> 3 with saved state and
+ * 3 -> 4 without; larger K and dense features: 2 -> 1), i.e. registers per
+ * thread against occupancy; bit 1 composites dense features
  * (top_k = 0, dim a multiple of 32) 16 channels per pass instead of 32.
  * Every shape computes the same result: the forward bit for bit, the adjoint
  * up to the order of its float32 atomic additions. Which one is fastest

@@ -216,8 +216,9 @@ cudaError_t launch_kclo(const FrameParams &fp, const FeatView &f, const FwdArgs 
 template <int KMAX, int CH, bool LP>
 cudaError_t launch_kcl(const FrameParams &fp, const FeatView &f, const FwdArgs &a, bool alt, cudaStream_t st)
 {
-    constexpr int occ = (KMAX > 0 && KMAX <= 8) ? 3 : 1;
-    constexpr int occ_alt = (KMAX > 0 && KMAX <= 8) ? 4 : 2;
+    // K <= 8: 3 CTAs per SM (4 as the alternative); larger K and dense: 2 (1)
+    constexpr int occ = (KMAX > 0 && KMAX <= 8) ? 3 : 2;
+    constexpr int occ_alt = (KMAX > 0 && KMAX <= 8) ? 4 : 1;
     return alt ? launch_kclo<KMAX, CH, LP, occ_alt>(fp, f, a, st) : launch_kclo<KMAX, CH, LP, occ>(fp, f, a, st);
 }
 
