@@ -16,6 +16,7 @@ namespace {
 using namespace tc;
 
 struct DecodeEpi {
+    static constexpr int kStages = 2; // two CTAs per SM: the per-row argmax dominates
     int64_t n_pix;
     int n_q;
     const float *T;

@@ -26,6 +26,7 @@ using namespace tc;
 constexpr int kQP = 12; // floats per query in shared memory: mu (3), precision (6), pad
 
 struct LabelEpi {
+    static constexpr int kStages = 2; // two CTAs per SM: the softmax epilogue dominates
     int64_t n;
     int n_q;
     const float *centres; // [n, 3]
@@ -118,6 +119,7 @@ struct LabelEpi {
 // or softmax): composited with the Top-K weights they give, by linearity,
 // the decode's logits <F, q> of every pixel without forming F.
 struct LogitEpi {
+    static constexpr int kStages = 4; // one CTA per SM: bound by the table's stores
     int64_t n;
     int n_q;
     void *table; // [n, ld]

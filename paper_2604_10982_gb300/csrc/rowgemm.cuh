@@ -2,8 +2,11 @@
 // query decode and the instance-label kernels.
 //
 // Persistent CTAs walk 128-row tiles of A [rows x D] (BF16, K-major). TMA
-// loads each [128 x D] tile (128-byte swizzle) into a 4-deep shared-memory
-// ring; one thread issues tcgen05.mma (M=128, N=n_pad, K=16 per instruction,
+// loads each [128 x D] tile (128-byte swizzle) into a shared-memory ring of
+// Epi::kStages stages: 4 with one CTA per SM, or 2 with two CTAs per SM, which
+// hides the latency of an epilogue that computes per row (the argmax of the
+// decode, the softmax of the labels) behind the other CTA; one thread issues
+// tcgen05.mma (M=128, N=n_pad, K=16 per instruction,
 // FP32 accumulation in TMEM) against B [n_b x D] (BF16, resident in shared
 // memory) into one of two TMEM accumulators, so the MMA of tile i+1 overlaps
 // the epilogue of tile i. Each thread owns one row (TMEM lane): it reads the
@@ -18,7 +21,6 @@ namespace psi {
 namespace tc {
 
 constexpr int kRowM = 128;              // rows per tile (TMEM lanes)
-constexpr int kRowStages = 4;
 constexpr int kRowThreads = 128;        // 4 warps: TMEM lane quarters 0..3
 constexpr uint32_t kRowTmemCols = 256;
 constexpr uint32_t kRowAccStride = 128; // column offset of the second accumulator
@@ -30,11 +32,15 @@ struct RowGemm {
     DevStatus *status;
 };
 
+// stages of the ring -> CTAs per SM (each CTA holds 256 TMEM columns: two fill TMEM)
+__host__ __device__ constexpr int row_ctas_per_sm(int stages) { return stages <= 2 ? 2 : 1; }
+
 template <class Epi>
-__global__ void __launch_bounds__(kRowThreads, 1) row_gemm_kernel(const __grid_constant__ CUtensorMap map_f,
-                                                                  const __grid_constant__ CUtensorMap map_q,
-                                                                  RowGemm p, Epi epi)
+__global__ void __launch_bounds__(kRowThreads, row_ctas_per_sm(Epi::kStages))
+    row_gemm_kernel(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_q, RowGemm p,
+                    Epi epi)
 {
+    constexpr int kRowStages = Epi::kStages;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned carve-up: [stages][D/64 atoms][128 rows][128 B], then Q
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -174,6 +180,8 @@ template <class Epi>
 cudaError_t launch_row_gemm(const void *A, int64_t rows, int D, const void *B, int n_b, size_t epi_smem_bytes,
                             const Epi &epi, DevStatus *status, cudaStream_t st, const char **why)
 {
+    constexpr int kRowStages = Epi::kStages;
+    constexpr int ctas = row_ctas_per_sm(kRowStages);
     const int n_pad = ((n_b + 15) / 16) * 16;
     CUtensorMap map_a, map_b;
     if (!encode_2d_bf16(&map_a, A, static_cast<uint64_t>(D), static_cast<uint64_t>(rows), 64, kRowM) ||
@@ -182,9 +190,15 @@ cudaError_t launch_row_gemm(const void *A, int64_t rows, int D, const void *B, i
         return cudaErrorInvalidValue;
     }
     RowGemm p{rows, D, n_pad, status};
-    // at least 120 KB so one CTA owns each SM (its 256 TMEM columns never wait on a co-resident CTA)
-    const size_t smem = std::max<size_t>(120 * 1024, 1024 + static_cast<size_t>(kRowStages) * (D / 64) * kRowM * 128 +
-                                                         static_cast<size_t>(D / 64) * n_pad * 128 + epi_smem_bytes);
+    // shared memory of at least 120 KB (one CTA per SM) or 80 KB (two): never
+    // more CTAs on an SM than their 256 TMEM columns each can be granted at once
+    const size_t smem = std::max<size_t>(ctas == 1 ? 120 * 1024 : 80 * 1024,
+                                         1024 + static_cast<size_t>(kRowStages) * (D / 64) * kRowM * 128 +
+                                             static_cast<size_t>(D / 64) * n_pad * 128 + epi_smem_bytes);
+    if (ctas == 2 && 3 * smem <= 228 * 1024) {
+        *why = "row GEMM shared memory too small to keep a third CTA off the SM";
+        return cudaErrorInvalidValue;
+    }
     cudaError_t e = cudaFuncSetAttribute(row_gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -192,7 +206,7 @@ cudaError_t launch_row_gemm(const void *A, int64_t rows, int D, const void *B, i
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (rows + kRowM - 1) / kRowM;
-    const int grid = static_cast<int>(std::min<int64_t>(tiles, std::max(sms, 1)));
+    const int grid = static_cast<int>(std::min<int64_t>(tiles, std::max(ctas * sms, 1)));
     row_gemm_kernel<Epi><<<grid, kRowThreads, smem, st>>>(map_a, map_b, p, epi);
     return cudaGetLastError();
 }
