@@ -399,6 +399,47 @@ def quat_frames_grad(q, g_tu, g_tv):
     return (gq_hat - np.sum(gq_hat * u, axis=1, keepdims=True) * u) / nq
 
 
+def surfel_geometry(s, cam, plant: int = 0):
+    """Per-surfel geometry table for depth and normal maps, FP64.
+
+    For surfel i seen by `cam`: z_i = (R mu_i + t)_z, the camera depth of its
+    centre, and n_i = R (t_u x t_v) / |t_u x t_v|, its unit normal in camera
+    coordinates, turned to face the camera (negated where n . x_c > 0; an
+    edge-on surfel keeps its sign). Returns [N, 4] = (z, n_x, n_y, n_z).
+    Blended with the compositing weights like any dense feature, the columns
+    give the expected depth sum_j omega_j z_j and normal sum_j omega_j n_j
+    maps of the 2D-surfel model (Sec. 3.1). `plant` > 0 builds a deliberately
+    wrong variant (only the pin test uses it)."""
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    tt = np.asarray(cam.t, np.float64).reshape(3)
+    xc = np.asarray(s.mu, np.float64) @ R.T + tt
+    c = np.cross(np.asarray(s.tu, np.float64), np.asarray(s.tv, np.float64))
+    n = (c / np.linalg.norm(c, axis=1, keepdims=True)) @ R.T
+    if plant != 1:
+        n = np.where((np.sum(n * xc, axis=1) > 0.0)[:, None], -n, n)
+    return np.concatenate([xc[:, 2:3], n], axis=1)
+
+
+def surfel_geometry_grad(s, cam, g, plant: int = 0):
+    """dL/dmu, dL/dt_u, dL/dt_v of L = sum g . surfel_geometry (g [N, 4]),
+    written from the chain rule (the sign choice is piecewise constant)."""
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    tt = np.asarray(cam.t, np.float64).reshape(3)
+    tu = np.asarray(s.tu, np.float64)
+    tv = np.asarray(s.tv, np.float64)
+    g = np.asarray(g, np.float64)
+    xc = np.asarray(s.mu, np.float64) @ R.T + tt
+    c = np.cross(tu, tv)
+    cn = np.linalg.norm(c, axis=1, keepdims=True)
+    nw = c / cn
+    flip = np.sum((nw @ R.T) * xc, axis=1) > 0.0
+    g_mu = g[:, 0:1] * R[2][None, :]                      # z = R[2] . mu + t_z
+    g_nc = np.where(flip[:, None], -g[:, 1:4], g[:, 1:4])
+    g_nw = g_nc @ R                                       # n_c = R n_w
+    g_c = g_nw / cn if plant == 2 else (g_nw - np.sum(g_nw * nw, axis=1, keepdims=True) * nw) / cn
+    return {"mu": g_mu, "tu": np.cross(tv, g_c), "tv": np.cross(g_c, tu)}
+
+
 CHI2_99_2D = -2.0 * np.log(0.01)  # chi-square quantile of 2 DOF at 99 %: the 99 % disc has radius 3.035 sigma
 
 

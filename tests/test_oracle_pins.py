@@ -399,3 +399,65 @@ def test_attention_gradients_central_differences():
             arg = {"Q": "Q_", "WQ": "WQ_", "WK": "WK_", "WV": "WV_", "feat": "f_", "mu": "mu_"}[key]
             fd = (L(**{arg: p}) - L(**{arg: m})) / (2 * h)
             assert abs(fd - g[key][idx]) < 1e-6 * max(1.0, abs(fd)), (key, idx, fd, g[key][idx])
+
+
+# ---------------------------------------------------------------- depth / normal table (2D-surfel geometry)
+def _geometry_closed_forms(plant=0):
+    """Camera-facing surfels: depth z0 and normal (0, 0, -1) whichever way the
+    tangents are ordered; a tilted surfel: the normal from an independent
+    rotation of the plane's spanning vectors."""
+    from .pins import CAM, fronto_surfel
+    a, _ = fronto_surfel(CAM, 0.1, -0.2, 2.5, 0.3, 0.2, 0.8)
+    b = sg.Surfels(a.mu.copy(), a.tv.copy(), a.tu.copy(), a.scale.copy(), a.opacity.copy(), a.rgb.copy())
+    err = 0.0
+    for s in (a, b):
+        G = orc.surfel_geometry(s, CAM, plant=plant)
+        err = max(err, abs(G[0, 0] - 2.5), np.abs(G[0, 1:] - [0.0, 0.0, -1.0]).max())
+    return err
+
+
+def test_geometry_table_closed_forms_and_invariants():
+    assert _geometry_closed_forms() < 1e-6
+    w = sg.dense_box(n=500)
+    cam = w.cameras[0]
+    G = orc.surfel_geometry(w.surfels, cam)
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    xc = w.surfels.mu.astype(np.float64) @ R.T + np.asarray(cam.t, np.float64)
+    assert np.allclose(G[:, 0], xc[:, 2], atol=0, rtol=0)
+    assert np.allclose(np.linalg.norm(G[:, 1:], axis=1), 1.0, atol=1e-12)
+    assert (np.sum(G[:, 1:] * xc, axis=1) <= 0).all()
+    # normal is perpendicular to both camera-space tangents
+    for f in ("tu", "tv"):
+        tc = getattr(w.surfels, f).astype(np.float64) @ R.T
+        assert np.abs(np.sum(tc * G[:, 1:], axis=1)).max() < 1e-6
+
+
+def _geometry_fd_error(plant=0):
+    w = sg.dense_box(n=40)
+    cam = w.cameras[0]
+    s64 = sg.Surfels(*(getattr(w.surfels, f).astype(np.float64) for f in ("mu", "tu", "tv", "scale", "opacity", "rgb")))
+    g = sg.make_upstream(4 * s64.n, 9, 0).reshape(s64.n, 4).astype(np.float64)
+    an = orc.surfel_geometry_grad(s64, cam, g, plant=plant)
+    loss = lambda: float(np.sum(g * orc.surfel_geometry(s64, cam)))
+    worst = 0.0
+    for kind in ("mu", "tu", "tv"):
+        arr = getattr(s64, kind)
+        for i in range(0, s64.n, 7):
+            for c in range(3):
+                x0 = arr[i, c]
+                h = 1e-6
+                arr[i, c] = x0 + h; lp = loss()
+                arr[i, c] = x0 - h; lm = loss()
+                arr[i, c] = x0
+                fd = (lp - lm) / (2 * h)
+                worst = max(worst, abs(fd - an[kind][i, c]) / max(1.0, abs(fd)))
+    return worst
+
+
+def test_geometry_gradient_central_differences():
+    assert _geometry_fd_error() < 1e-6
+
+
+def test_geometry_planted_mistakes_are_caught():
+    assert _geometry_closed_forms(plant=1) > 0.5        # no turn toward the camera
+    assert _geometry_fd_error(plant=2) > 1e-3           # normalisation's projection dropped
