@@ -368,6 +368,23 @@ int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_feat
                               float *g_Q, float *g_WQ, float *g_WK, float *g_WV, const psi_grads *grads,
                               void *workspace, size_t workspace_bytes, psi_stream stream);
 
+/* ---- depth and normal maps (the 2D-surfel geometry of Sec. 3.1) -----------
+ * psi_surfel_geometry writes, per surfel and for one camera (host struct), a
+ * row (z, n_x, n_y, n_z, 0, ...) of ld floats: z = (R mu + t)_z, the camera
+ * depth of the centre, and n = R (t_u x t_v) / |t_u x t_v|, the unit normal in
+ * camera coordinates turned to face the camera (negated where n . x_cam > 0).
+ * Rendered as a dense float32 feature table (dim = ld, top_k = 0, same camera)
+ * it gives the expected depth sum_j omega_j z_j and normal sum_j omega_j n_j
+ * maps. psi_surfel_geometry_bwd ADDS dL/dmu, dL/dt_u, dL/dt_v (grads->mu, tu,
+ * tv; others ignored, any may be NULL) given g_table = dL/dtable, e.g. the
+ * feature gradient (grads->feat) of psi_render_bwd for that render.
+ *  table, g_table: [N, ld] float32, 16-byte aligned; ld a multiple of 16 in
+ *  [16, 256]; t_u x t_v must not vanish. */
+int psi_surfel_geometry(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cam, float *table, int ld,
+                        psi_stream stream);
+int psi_surfel_geometry_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cam, const float *g_table, int ld,
+                            const psi_grads *grads, psi_stream stream);
+
 /* ---- quaternion-parameterised tangent frames (2DGS form) ------------------
  * The paper's surfels follow 2DGS (Sec. 3.1), whose tangent frame is a
  * rotation R(q / |q|) of a quaternion q = (w, x, y, z): t_u, t_v are R's first

@@ -634,6 +634,35 @@ int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_feat
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_frustum_attention_bwd", e);
 }
 
+int psi_surfel_geometry(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cam, float *table, int ld,
+                        psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc = check_surfels(ctx, s);
+    if (rc) return rc;
+    if (!cam) return fail(ctx, PSI_ERR_INVALID_ARG, "cam is NULL");
+    if (ld < 16 || ld > 256 || ld % 16 != 0) return fail(ctx, PSI_ERR_INVALID_ARG, "ld must be a multiple of 16 in [16,256]");
+    if (s->n > 0 && (!table || !aligned(table, 16))) return fail(ctx, PSI_ERR_INVALID_ARG, "table must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_geometry(*s, *cam, table, ld, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_surfel_geometry", e);
+}
+
+int psi_surfel_geometry_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cam, const float *g_table, int ld,
+                            const psi_grads *grads, psi_stream stream)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    int rc = check_surfels(ctx, s);
+    if (rc) return rc;
+    if (!cam || !grads) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (ld < 16 || ld > 256 || ld % 16 != 0) return fail(ctx, PSI_ERR_INVALID_ARG, "ld must be a multiple of 16 in [16,256]");
+    if (s->n > 0 && (!g_table || !aligned(g_table, 16)))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "g_table must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_geometry_bwd(*s, *cam, g_table, ld, *grads, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_surfel_geometry_bwd", e);
+}
+
 int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream)
 {
     if (!ctx) return PSI_ERR_INVALID_ARG;

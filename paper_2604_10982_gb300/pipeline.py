@@ -291,6 +291,15 @@ def surfel_logits(ctx, scene: DeviceScene, queries, ld: int | None = None, dtype
     return out
 
 
+def surfel_geometry(ctx, scene: DeviceScene, cam, ld: int = 16, stream=None) -> torch.Tensor:
+    """Per-surfel (depth, normal) table [N, ld] float32 for one camera: rendered
+    with label_scene and top_k = 0 it gives the expected depth (column 0) and
+    normal (columns 1-3) maps."""
+    out = torch.empty(scene.n, ld, dtype=torch.float32, device=scene.mu.device)
+    psi.psi_surfel_geometry(ctx, scene.surfels_struct(), psi.cameras([cam]), out, ld, stream)
+    return out
+
+
 def label_scene(scene: DeviceScene, labels: torch.Tensor) -> DeviceScene:
     """The same surfels with the label table as their feature table, so a
     Renderer composites the label mixture of Eq. 8."""

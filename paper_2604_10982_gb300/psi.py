@@ -118,6 +118,10 @@ def lib():
                                                 ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P,
                                                 ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_quat_frames.argtypes = [_P, _P, _i64, _P, _P, _P]
+        L.psi_surfel_geometry.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiCamera), _P, ctypes.c_int,
+                                          _P]
+        L.psi_surfel_geometry_bwd.argtypes = [_P, ctypes.POINTER(PsiSurfels), ctypes.POINTER(PsiCamera), _P,
+                                              ctypes.c_int, ctypes.POINTER(PsiGrads), _P]
         L.psi_quat_frames_bwd.argtypes = [_P, _P, _i64, _P, _P, _P, _P]
         L.psi_surfel_regularisers.argtypes = [_P, ctypes.POINTER(PsiSurfels), _P, _P, _P, _i64, ctypes.c_float,
                                                ctypes.c_float, ctypes.c_float, _P, ctypes.POINTER(PsiGrads), _P]
@@ -371,6 +375,17 @@ def psi_frustum_attention_bwd(ctx, s, feats, Q, n_q, WQ, WK, WV, d, g_out, g_Q, 
                                               _ptr(g_WK), _ptr(g_WV), ctypes.byref(grads), _ptr(workspace),
                                               workspace.numel() * workspace.element_size(), _stream(stream)),
               "psi_frustum_attention_bwd")
+
+
+def psi_surfel_geometry(ctx, s, cam_arr, table, ld, stream=None):
+    """cam_arr: a one-camera array from cameras([cam])."""
+    ctx.check(lib().psi_surfel_geometry(ctx.handle, ctypes.byref(s), cam_arr, _ptr(table), int(ld), _stream(stream)),
+              "psi_surfel_geometry")
+
+
+def psi_surfel_geometry_bwd(ctx, s, cam_arr, g_table, ld, grads: PsiGrads, stream=None):
+    ctx.check(lib().psi_surfel_geometry_bwd(ctx.handle, ctypes.byref(s), cam_arr, _ptr(g_table), int(ld),
+                                            ctypes.byref(grads), _stream(stream)), "psi_surfel_geometry_bwd")
 
 
 def psi_quat_frames(ctx, q, n, tu, tv, stream=None):
