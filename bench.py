@@ -703,6 +703,51 @@ def run_psi(args):
         regs = {"ms": float(reg_ms), "surfels": scene.n, "priors": n_nodes,
                 "hbm_frac": reg_bytes / (reg_ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
 
+    # ---- 2DGS compatibility over all surfels, one 1080p view: quaternion
+    # tangent frames and their adjoint; the depth/normal table, its dense
+    # composite (K = 0), the composite's adjoint and the table's adjoint
+    geo = None
+    if args.label_frames > 0:
+        def timed(fn, reps=3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fn()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+        rng = np.random.default_rng(7)
+        qd = torch.from_numpy(rng.normal(size=(scene.n, 4)).astype(np.float32)).to(dev)
+        tu_o, tv_o = torch.empty(scene.n, 3, device=dev), torch.empty(scene.n, 3, device=dev)
+        gq = torch.zeros(scene.n, 4, device=dev)
+        fr_ms = timed(lambda: psi.psi_quat_frames(ctx, qd, scene.n, tu_o, tv_o))
+        frb_ms = timed(lambda: psi.psi_quat_frames_bwd(ctx, qd, scene.n, grads["tu"], grads["tv"], gq))
+        cam_arr = psi.cameras([cams[0]])
+        Gt = pl.surfel_geometry(ctx, scene, cams[0])
+        gsc = pl.label_scene(scene, Gt)
+        go = psi.default_opts(mode=psi.EXACT, top_k=0, opacity_radius=1)
+        rg = pl.Renderer(ctx, scene.n, [cams[0]], go, r.capacity, D=16, F_dtype=psi.F32, device=dev)
+        rg.project(gsc)
+        rg.intersect()
+        rg.sort()
+        tab_ms = timed(lambda: psi.psi_surfel_geometry(ctx, scene.surfels_struct(), cam_arr, Gt, 16))
+        ren_ms = timed(lambda: rg.render(gsc))
+        gFg = torch.randn(rg.n_pix, 16, device=dev)
+        gg = {k: torch.zeros_like(v) for k, v in grads.items() if k != "feat"}
+        gg["feat"] = torch.zeros(scene.n, 16, device=dev)
+        bwd_ms = timed(lambda: rg.backward(gsc, gC, gFg, gT, grads=gg))
+        gsg = psi.PsiGrads(psi._ptr(gg["mu"]), psi._ptr(gg["tu"]), psi._ptr(gg["tv"]), None, None, None, None)
+        tbwd_ms = timed(lambda: psi.psi_surfel_geometry_bwd(ctx, scene.surfels_struct(), cam_arr, gg["feat"], 16, gsg))
+        geo = {"quat_frames_ms": float(fr_ms), "quat_frames_bwd_ms": float(frb_ms),
+               "depth_normal_table_ms": float(tab_ms), "depth_normal_render_ms": float(ren_ms),
+               "depth_normal_render_bwd_ms": float(bwd_ms), "depth_normal_table_bwd_ms": float(tbwd_ms),
+               "form": "3M surfels, one 1920x1080 view; the [N, 16] FP32 depth/normal table composited densely "
+                       "(K = 0, EXACT) by the compositing kernels; adjoint of that composite (saved state) and of "
+                       "the table"}
+        del rg, gg, Gt
+
     # ---- frustum-constrained cross-attention (Sec. 4.1) over all surfels
     # for one view: 100 queries, C = d = 128 (FP32 GEMMs)
     attn = None
@@ -787,7 +832,7 @@ def run_psi(args):
         "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)}, "kernel_ms": kernel_ms,
         "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
-        "autotune": tuned, "plain_fp32": plain, "ablation": ablation, "labels": labels, "regularisers": regs, "attention": attn, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "autotune": tuned, "plain_fp32": plain, "ablation": ablation, "labels": labels, "regularisers": regs, "compat_2dgs": geo, "attention": attn, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),
         "clocks": clk, "paper_context": PAPER_CONTEXT, "setup_s": setup_s,
     }
