@@ -11,7 +11,9 @@
  *    comment says "host". The library never frees caller memory.
  *  - Work is enqueued asynchronously on the caller's stream `stream`
  *    (a cudaStream_t; NULL = legacy default stream). No entry point
- *    synchronises the host, so a whole frame can be captured in a CUDA graph.
+ *    synchronises the host except psi_status_fetch and the launch-shape
+ *    tuners psi_tune_render_fwd / psi_tune_render_bwd, so a whole frame of
+ *    the other calls can be captured in a CUDA graph.
  *  - Return value: PSI_OK or an error code; psi_last_error(ctx) then holds a
  *    readable message. Host-side argument checks return PSI_ERR_INVALID_ARG
  *    (or PSI_ERR_UNSUPPORTED) before anything is enqueued.
