@@ -5,6 +5,7 @@
 #include <new>
 
 #include <cublas_v2.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 
@@ -22,6 +23,15 @@ struct psi_ctx {
 };
 
 namespace {
+
+// One NVTX range per entry point that enqueues GPU work, named after it, so
+// that a profiler's timeline groups each call's kernels (no-op without one).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 int fail(psi_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -237,6 +247,7 @@ int psi_project_surfels(psi_ctx *ctx, const psi_surfels *s, const psi_camera *ca
                         const psi_render_opts *o, void *records, void *bin_records, uint32_t *tiles_touched,
                         psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc;
     if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o)) || (rc = check_surfels(ctx, s))) return rc;
@@ -257,6 +268,7 @@ int psi_intersect_tiles(psi_ctx *ctx, const psi_camera *cams, int n_views, const
                         uint32_t *vals, int64_t capacity, int64_t *d_num_pairs, void *workspace,
                         size_t workspace_bytes, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc;
     if ((rc = check_opts(ctx, o)) || (rc = check_cams(ctx, cams, n_views, o))) return rc;
@@ -282,6 +294,7 @@ int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d
                   int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *workspace,
                   size_t workspace_bytes, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (begin_bit < 0 || end_bit > 64 || begin_bit >= end_bit)
         return fail(ctx, PSI_ERR_INVALID_ARG, "need 0 <= begin_bit < end_bit <= 64");
@@ -301,6 +314,7 @@ int psi_sort_keys_noalloc(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const in
                           int64_t capacity, int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total,
                           psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (begin_bit < 0 || end_bit > 64 || begin_bit >= end_bit)
         return fail(ctx, PSI_ERR_INVALID_ARG, "need 0 <= begin_bit < end_bit <= 64");
@@ -431,6 +445,7 @@ int psi_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, con
                    const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
                    const psi_render_opts *o, const psi_fwd_out *out, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     psi::FrameParams fp;
     psi::FeatView fv;
@@ -448,6 +463,7 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
                    const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
                    psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     psi::FrameParams fp;
     psi::FeatView fv;
@@ -468,6 +484,7 @@ int psi_tune_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records
                         const psi_render_opts *o, const psi_fwd_out *out, int reps, float *ms, int *best,
                         psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (reps < 1 || !ms || !best) return fail(ctx, PSI_ERR_INVALID_ARG, "need reps >= 1, ms and best");
     psi::FrameParams fp;
@@ -492,6 +509,7 @@ int psi_tune_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *
                         const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
                         int reps, float *ms, int *best, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (reps < 1 || !ms || !best) return fail(ctx, PSI_ERR_INVALID_ARG, "need reps >= 1, ms and best");
     psi::FrameParams fp;
@@ -553,6 +571,7 @@ int psi_ctx_get_render_shape(psi_ctx *ctx, int which, const psi_render_opts *o, 
 int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const void *Q, int n_q, const float *T,
                        int32_t *ids, void *logits, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (n_pix < 0 || n_pix >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "n_pix out of range");
     if (D != 64 && D != 128) return fail(ctx, PSI_ERR_UNSUPPORTED, "D must be 64 or 128");
@@ -581,6 +600,7 @@ int psi_frustum_attention(psi_ctx *ctx, const psi_surfels *s, const psi_features
                           float z_near, const float *Q, int n_q, const float *W_Q, const float *W_K, const float *W_V,
                           int d, float *out, void *workspace, size_t workspace_bytes, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc;
     if ((rc = check_surfels(ctx, s))) return rc;
@@ -613,6 +633,7 @@ int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_feat
                               float *g_Q, float *g_WQ, float *g_WK, float *g_WV, const psi_grads *grads,
                               void *workspace, size_t workspace_bytes, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc;
     if ((rc = check_surfels(ctx, s))) return rc;
@@ -637,6 +658,7 @@ int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_feat
 int psi_surfel_geometry(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cam, float *table, int ld,
                         psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc = check_surfels(ctx, s);
     if (rc) return rc;
@@ -651,6 +673,7 @@ int psi_surfel_geometry(psi_ctx *ctx, const psi_surfels *s, const psi_camera *ca
 int psi_surfel_geometry_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_camera *cam, const float *g_table, int ld,
                             const psi_grads *grads, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc = check_surfels(ctx, s);
     if (rc) return rc;
@@ -665,6 +688,7 @@ int psi_surfel_geometry_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_camera
 
 int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && (!q || !tu || !tv))) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument or n < 0");
     if (!aligned(q, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "q must be 16-byte aligned");
@@ -676,6 +700,7 @@ int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *t
 int psi_quat_frames_bwd(psi_ctx *ctx, const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
                         psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && (!q || !g_q))) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument or n < 0");
     if (!aligned(q, 16) || !aligned(g_q, 16)) return fail(ctx, PSI_ERR_INVALID_ARG, "q and g_q must be 16-byte aligned");
@@ -688,6 +713,7 @@ int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *n
                             const float *node_n, int64_t n_nodes, float lambda_n, float w_geo, float w_iso,
                             double *losses, const psi_grads *grads, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     int rc;
     if ((rc = check_surfels(ctx, s))) return rc;
@@ -704,6 +730,7 @@ int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *n
 int psi_surfel_logits(psi_ctx *ctx, const psi_features *f, int64_t n, const void *Q, int n_q, void *table,
                       int table_dtype, int ld, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (n < 0 || n >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "n out of range");
     if (!f || !f->data) return fail(ctx, PSI_ERR_INVALID_ARG, "features are required");
@@ -728,6 +755,7 @@ int psi_surfel_logits(psi_ctx *ctx, const psi_features *f, int64_t n, const void
 int psi_surfel_labels(psi_ctx *ctx, const psi_features *f, const float *centres, int64_t n, const void *Q, int n_q,
                       const float *q_mu, const float *q_cov, void *labels, int labels_dtype, int ld, psi_stream stream)
 {
+    NvtxRange nvtx_range(__func__);
     if (!ctx) return PSI_ERR_INVALID_ARG;
     if (n < 0 || n >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "n out of range");
     if (!f || !f->data) return fail(ctx, PSI_ERR_INVALID_ARG, "features are required");
