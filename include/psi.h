@@ -154,7 +154,9 @@ typedef struct {
 /* ---- context ---------------------------------------------------------- */
 
 /* Create a context on CUDA device `device` (allocates a 16-byte device status
- * word). *out receives the handle. */
+ * word). *out receives the handle (NULL on failure): PSI_ERR_INVALID_ARG if
+ * `device` is not a CUDA device of this machine, PSI_ERR_CUDA if an
+ * allocation fails. */
 int psi_ctx_create(psi_ctx **out, int device);
 void psi_ctx_destroy(psi_ctx *ctx);
 /* Message of the last failing call on ctx (never NULL; "" if none). */

@@ -68,3 +68,14 @@ def test_render_shape_calls_check_arguments(lib):
     assert lib.psi_ctx_set_render_shape(None, 0, ctypes.byref(o), psi.F32, 0, 1) == psi.PSI_ERR_INVALID_ARG
     assert lib.psi_ctx_get_render_shape(None, 1, ctypes.byref(o), psi.F32, 1, ctypes.byref(v)) == psi.PSI_ERR_INVALID_ARG
     assert psi.RENDER_SHAPES == 4
+
+
+def test_context_creation_without_a_device_fails_cleanly(lib):
+    """On a machine without a CUDA device the library still loads and a
+    context request returns an error code instead of crashing."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p(None)
+    rc = lib.psi_ctx_create(ctypes.byref(h), 0)
+    assert rc == psi.PSI_ERR_INVALID_ARG and not h.value  # device 0 does not exist
