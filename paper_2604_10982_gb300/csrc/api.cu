@@ -8,6 +8,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
+#include "geometry.cuh"
 
 struct psi_ctx {
     int device;

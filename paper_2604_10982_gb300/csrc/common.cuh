@@ -231,9 +231,6 @@ cudaError_t launch_attention_bwd(void *cublas, int64_t N, int C, int n_q, const 
                                  float *gWK, float *gWV, const float *mu, float *g_feat, float *g_mu, void *ws,
                                  cudaStream_t st, const char **why);
 cudaError_t launch_frames(const float *q, int64_t n, float *tu, float *tv, cudaStream_t st);
-cudaError_t launch_geometry(const psi_surfels &s, const psi_camera &cam, float *table, int ld, cudaStream_t st);
-cudaError_t launch_geometry_bwd(const psi_surfels &s, const psi_camera &cam, const float *g_table, int ld,
-                                const psi_grads &g, cudaStream_t st);
 cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
                               cudaStream_t st);
 cudaError_t launch_regularisers(const psi_surfels &s, const int32_t *node_of, const float *node_mu, const float *node_n,

@@ -9,7 +9,7 @@
 // depth sum_j omega_j z_j and normal sum_j omega_j n_j maps; the adjoint of
 // that render gives dL/dtable (its feature gradient), which the second kernel
 // takes to mu, t_u and t_v. One thread per surfel.
-#include "common.cuh"
+#include "geometry.cuh"
 
 namespace psi {
 namespace {
