@@ -55,6 +55,18 @@
 
 enum { OR_SPHERE = 0, OR_AABB = 1, OR_EXACT = 2 };
 
+/* OR_PLANT selects a deliberately wrong variant, built only by the test that
+ * checks that the pins catch it: 1 drops the 1/2 in the Gaussian, 2 updates T
+ * before taking the weight, 3 keeps the K smallest weights, 4 flips the sign
+ * of the centre gradient, 5 mirrors the exact-test chord, 6 drops the factor 2
+ * of the low-pass term, 7 flips the sign of its centre gradient, 8 tests only
+ * the centre's depth against the near plane, 9 takes the smaller eigenvalue
+ * for the SPHERE radius, 10 tests the unit disc instead of the binning disc
+ * against the near plane. 0 = correct. */
+#ifndef OR_PLANT
+#define OR_PLANT 0
+#endif
+
 static float f_bits_to_float(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
 static uint32_t f_float_to_bits(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
 
@@ -124,7 +136,9 @@ static void disc_surfel(const float *mu, const float *tu, const float *tv, float
     const float w = xc[2];
     const float nab = sqrtf(fmaf(uu[2], uu[2], vv[2] * vv[2]));
     const float rb = sqrtf(r2b);
-    const float zmin = fmaf(-rb, nab, w);
+    float zmin = fmaf(-rb, nab, w);
+    if (OR_PLANT == 8) zmin = w;            /* planted: centre-only near test */
+    if (OR_PLANT == 10) zmin = w - nab;     /* planted: unit disc instead of the binning disc */
     if (!(zmin > znear)) return;
 
     /* pixel-homogeneous columns, shifted so the projected centre is the origin */
@@ -161,7 +175,8 @@ static void disc_surfel(const float *mu, const float *tu, const float *tv, float
     if (mode == OR_SPHERE) {
         const float mid = 0.5f * (A00 + A11);
         const float dd = 0.5f * (A00 - A11);
-        const float lam = mid + sqrtf(fmaf(dd, dd, A01 * A01));
+        const float lam = (OR_PLANT == 9) ? mid - sqrtf(fmaf(dd, dd, A01 * A01))  /* planted: lambda_min */
+                                          : mid + sqrtf(fmaf(dd, dd, A01 * A01));
         float Rs = sqrtf(fmaxf(lam, 0.0f));
         Rs = fmaxf(Rs, fmaxf(hx, hy));
         extx = Rs;
@@ -336,15 +351,6 @@ float or_rho_opacity(float o) { return rho_opacity(o); }
 /* ------------------------------------------------------------------ */
 /* (2) value path, float64                                             */
 /* ------------------------------------------------------------------ */
-
-/* OR_PLANT selects a deliberately wrong variant, built only by the test that
- * checks that the pins catch it: 1 drops the 1/2 in the Gaussian, 2 updates T
- * before taking the weight, 3 keeps the K smallest weights, 4 flips the sign
- * of the centre gradient, 5 mirrors the exact-test chord, 6 drops the factor 2
- * of the low-pass term, 7 flips the sign of its centre gradient. 0 = correct. */
-#ifndef OR_PLANT
-#define OR_PLANT 0
-#endif
 
 #define OR_ALPHA_MIN (1.0 / 255.0)
 #define OR_ALPHA_MAX 0.99

@@ -72,6 +72,7 @@ def normal(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
 _S_PLANE, _S_A, _S_B, _S_OFF, _S_AXIS, _S_TILT, _S_PSI, _S_SU, _S_SV, _S_OP, _S_RGB, _S_FEAT, _S_QUERY = range(13)
 _S_GRAD = 40
 _S_CAMJIT = 60
+_S_NEAR = 70  # streams 70..77: the near-plane scene
 
 
 @dataclass
@@ -269,6 +270,28 @@ def dense_box(seed: int = 1, n: int = 6000, d: int = 32, width: int = 150, heigh
     s = make_surfels(n, box_planes(), seed, scale_median=scale_median)
     cam = look_camera((0.0, -6.0, 1.5), 0.0, width, height, 0.86 * width)
     return Workload(f"densebox-{n}-{width}x{height}-D{d}-K{top_k}", s, [cam], d, top_k, make_features(n, d, seed))
+
+
+def near_plane(seed: int = 11, n: int = 400, d: int = 16) -> Workload:
+    """Surfels close to the box camera of ``tiny`` (128x128, f=110) at random
+    tilts: centres in camera space at depth U[0.21, 0.9] m inside the central
+    60 % of the image, normals uniform on the sphere, scales log-uniform in
+    [5 mm, 25 cm], opacity 0.9. The near plane z=0.2 m cuts the support disc
+    of many of them while their centres lie beyond it."""
+    cam = look_camera((0.0, -6.0, 1.5), 0.0, 128, 128, 110.0)
+    u = lambda k, m: uniform(seed, _S_NEAR + k, m)
+    z = 0.21 + 0.69 * u(0, n)
+    xc = np.stack([(0.6 * u(1, n) - 0.3) * z, (0.6 * u(2, n) - 0.3) * z, z], 1)
+    nrm = normal(seed, _S_NEAR + 3, 3 * n).reshape(n, 3)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    a = np.cross(nrm, normal(seed, _S_NEAR + 4, 3 * n).reshape(n, 3))
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    b = np.cross(nrm, a)
+    sc = np.exp(math.log(0.005) + (math.log(0.25) - math.log(0.005)) * u(5, 2 * n)).reshape(n, 2)
+    R, t = cam.R, cam.t
+    f32 = lambda x: np.ascontiguousarray(x, dtype=np.float32)
+    s = Surfels(f32((xc - t) @ R), f32(a @ R), f32(b @ R), f32(sc), f32(np.full(n, 0.9)), f32(u(6, 3 * n).reshape(n, 3)))
+    return Workload(f"nearplane-{n}-128x128", s, [cam], d, 8, make_features(n, d, seed))
 
 
 def street(seed: int = 0, n: int = 200_000, d: int = 64) -> Workload:

@@ -377,3 +377,72 @@ def fd_check(w, params_per_kind=12, seed=0, h_rel=1e-5, tol_rel=1e-6, tol_abs=2e
             checked += 1
     assert checked >= 4 * params_per_kind, checked
     return checked, worst
+
+
+def _disc_boundary(s, i, r, cam, samples):
+    """Points of surfel i's disc of radius r (in (u, v) units) at `samples`
+    angles, in camera space (FP64, by hand)."""
+    R, t, *_ = _cam_f64(cam)
+    th = np.linspace(0, 2 * np.pi, samples, endpoint=False)
+    mu, tu, tv = (getattr(s, f)[i].astype(np.float64) for f in ("mu", "tu", "tv"))
+    su, sv = s.scale[i].astype(np.float64)
+    P = mu[None] + (r * np.cos(th) * su)[:, None] * tu[None] + (r * np.sin(th) * sv)[:, None] * tv[None]
+    return P @ R.T + t
+
+
+def pin_near_plane(s=None, margin=1e-4, samples=8192):
+    """Near-plane cull (reading: a surfel is culled unless its whole binning
+    disc lies beyond z_near): brute force over the sampled boundary of the
+    disc of radius r_b = sqrt(r^2 (1 + 2^-10)) -- a disc's nearest point is on
+    its boundary -- decides visibility; straddles within `margin` of z_near
+    are excused. The scene must contain surfels whose centre is beyond the
+    plane while their disc crosses it, and surfels wholly beyond it."""
+    s = s if s is not None else sg.near_plane().surfels
+    opts = orc.Opts(mode=orc.AABB)
+    b = orc.bin_view(s, CAM, opts)
+    rb = math.sqrt(opts.chi2 * (1.0 + 1.0 / 1024.0))
+    crossing = beyond = 0
+    for i in range(s.n):
+        Xc = _disc_boundary(s, i, rb, CAM, samples)
+        zmin = Xc[:, 2].min()
+        if abs(zmin - opts.z_near) < margin:
+            continue
+        if zmin < opts.z_near:
+            assert not b["visible"][i], (i, zmin)
+            centre_z = (_cam_f64(CAM)[0] @ s.mu[i].astype(np.float64) + _cam_f64(CAM)[1])[2]
+            crossing += int(centre_z > opts.z_near)
+        else:
+            # wholly beyond the plane, centred in the image: must be kept
+            assert b["visible"][i], (i, zmin)
+            beyond += 1
+    assert crossing >= 20 and beyond >= 20, (crossing, beyond)
+    return crossing, beyond
+
+
+def pin_sphere_radius(s=None, samples=4096, n_max=300):
+    """SPHERE mode (the paper's isotropic bounding sphere): the square's
+    half-width is the radius of the smallest circle about the ellipse centre
+    that holds the projected binning disc, i.e. its semi-major axis. Checked
+    against hand-projected boundary points: the centre is the midpoint of their
+    x and y extremes, the radius their largest distance from it."""
+    s = s if s is not None else concat(sg.near_plane(seed=12, n=200).surfels, sg.dense_box(n=3000).surfels)
+    cam = CAM
+    R, t, fx, fy, cx, cy = _cam_f64(cam)
+    opts = orc.Opts(mode=orc.SPHERE)
+    b = orc.bin_view(s, cam, opts)
+    rb = math.sqrt(opts.chi2 * (1.0 + 1.0 / 1024.0))
+    vis = np.nonzero(b["visible"])[0][:n_max]
+    rotated = 0
+    for i in vis:
+        Xc = _disc_boundary(s, i, rb, cam, samples)
+        x = fx * Xc[:, 0] / Xc[:, 2] + cx
+        y = fy * Xc[:, 1] / Xc[:, 2] + cy
+        ex, ey = 0.5 * (x.min() + x.max()), 0.5 * (y.min() + y.max())
+        semi = np.sqrt((x - ex) ** 2 + (y - ey) ** 2).max()
+        hx, hy, extx, exty = (float(v) for v in b["ell"][i][5:9])
+        assert extx == exty, i
+        tol = 2e-3 * max(1.0, semi)
+        assert abs(extx - semi) <= tol, (i, extx, semi, hx, hy)
+        rotated += int(semi > max(hx, hy) * 1.01 + tol)
+    assert len(vis) >= 100 and rotated >= 20, (len(vis), rotated)
+    return len(vis), rotated

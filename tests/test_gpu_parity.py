@@ -59,6 +59,34 @@ def test_project_counts_and_bounds_bitexact(ctx, box, mode, oprad):
 
 
 @pytest.mark.parametrize("mode", [orc.SPHERE, orc.AABB, orc.EXACT])
+def test_project_near_plane_straddles_bitexact(ctx, mode):
+    """Surfels whose support disc crosses the near plane while the centre is
+    beyond it (the pinned near-plane cull), at random tilts: counts, ellipse
+    and rectangle bit for bit, emitted keys in emission order."""
+    w = sg.near_plane(seed=21, n=600)
+    cam = w.cameras[0]
+    o = orc.Opts(mode=mode)
+    scene, r = _renderer(ctx, w, [cam], o)
+    r.project(scene)
+    r.intersect()
+    torch.cuda.synchronize()
+    n = w.surfels.n
+    b = orc.bin_view(w.surfels, cam, o)
+    counts = r.counts.cpu().numpy().view(np.uint32)[:n]
+    assert np.array_equal(counts, b["count"]), int((counts != b["count"]).sum())
+    assert 0 < int((b["count"] > 0).sum()) < n
+    bins = r.bins.cpu().numpy()[: n * 32].view(np.uint32).reshape(n, 8)
+    vis = b["count"] > 0
+    ell = b["ell"][vis].view(np.uint32)
+    assert np.array_equal(bins[vis][:, :5], ell[:, :5])
+    P = int(r.num_pairs.item())
+    ek, ev = orc.emit_pairs(w.surfels, [cam], o)
+    assert P == len(ek)
+    assert np.array_equal(r.keys[:P].cpu().numpy().view(np.uint64), ek)
+    assert np.array_equal(r.vals[:P].cpu().numpy().view(np.uint32), ev)
+
+
+@pytest.mark.parametrize("mode", [orc.SPHERE, orc.AABB, orc.EXACT])
 def test_keys_sort_ranges_bitexact(ctx, box, mode):
     cams = multi_cams()
     o = orc.Opts(mode=mode, opacity_radius=(mode == orc.EXACT))
@@ -181,7 +209,6 @@ def test_topk_large_k_equals_dense_bitwise(ctx, box):
     o_d = orc.Opts(mode=orc.EXACT, top_k=0)
     o_k = orc.Opts(mode=orc.EXACT, top_k=32)
     ref = orc.render(box.surfels, cams[0], orc.Opts(top_k=0))
-    assert ref["ncontrib"].max() <= 32 or True
     scene, rd = _renderer(ctx, box, cams, o_d, D=32)
     rd.frame(scene)
     _, rk = _renderer(ctx, box, cams, o_k, D=32)

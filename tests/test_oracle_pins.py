@@ -77,6 +77,16 @@ def test_fd_gradients_lowpass(oracle_lib):
     assert checked >= 32
 
 
+def test_near_plane_cull_bruteforce(oracle_lib):
+    crossing, beyond = pins.pin_near_plane()
+    assert crossing >= 20 and beyond >= 20
+
+
+def test_sphere_radius_semi_major(oracle_lib):
+    n, rotated = pins.pin_sphere_radius()
+    assert n >= 100 and rotated >= 20
+
+
 def test_tiny_config_shape(oracle_lib):
     w = sg.tiny()
     assert w.surfels.n == 2000 and w.cameras[0].width == 128 and w.features.shape == (2000, 16)
@@ -86,6 +96,7 @@ def test_tiny_config_shape(oracle_lib):
 
 @pytest.mark.parametrize("plant,check", [
     (1, "fronto"), (2, "two"), (3, "topk"), (4, "fd"), (5, "coverage"), (6, "lowpass"), (7, "fd_lowpass"),
+    (8, "near"), (9, "sphere"), (10, "near"),
 ])
 def test_planted_mistake_is_caught(plant, check):
     """A deliberately wrong oracle build fails the pin aimed at that mistake."""
@@ -98,6 +109,8 @@ def test_planted_mistake_is_caught(plant, check):
         "lowpass": pins.pin_lowpass,
         "fd_lowpass": lambda: pins.fd_check(sg.crop_scene(n=300, d=8, size=48, scale_median=0.08),
                                             params_per_kind=6, lowpass=True),
+        "near": pins.pin_near_plane,
+        "sphere": pins.pin_sphere_radius,
     }[check]
     orc.use_variant(plant)
     try:
