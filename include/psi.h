@@ -169,6 +169,19 @@ const char *psi_last_error(const psi_ctx *ctx);
  * clears the word. */
 int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *detail);
 
+/* Failure detection (no counterpart in the paper): every wait of the
+ * kernels' copy and MMA pipelines gives up after the context's wait limit
+ * (default 1 s), raises PSI_ERR_TIMEOUT with its wait site in the status word
+ * and lets the kernel return; the copies and MMA groups it had started are
+ * still awaited (with the fixed 1 s limit) before its shared memory and TMEM
+ * are released. psi_ctx_set_wait_limit_ns sets the limit for kernels launched
+ * after it returns (0 restores 1 s; at most PSI_WAIT_LIMIT_MAX_NS, else
+ * PSI_ERR_INVALID_ARG). A limit shorter than a kernel's normal waits makes
+ * its outputs invalid: it exists to exercise the give-up path. Synchronous
+ * copy to the device: not inside a stream capture. */
+#define PSI_WAIT_LIMIT_MAX_NS 10000000000ull
+int psi_ctx_set_wait_limit_ns(psi_ctx *ctx, uint64_t ns);
+
 /* Kernels psi_ctx_time_kernel can bracket: those that share an entry point
  * with other kernels (psi_render_bwd launches the feature kernel, the list
  * walk and the chain kernel). */
@@ -233,6 +246,9 @@ int psi_intersect_tiles(psi_ctx *ctx, const psi_camera *cams, int n_views, const
  * tiles of similar length is arbitrary and never changes a result). The
  * tile_ranges buffer therefore holds 3*n_tiles_total uint32.
  * Pass begin_bit=0, end_bit=32+ceil(log2(n_tiles_total)) for the full order.
+ * If *d_num_pairs exceeds capacity, only the first capacity pairs are sorted
+ * and ranged, and PSI_ERR_CAPACITY (detail: *d_num_pairs) is raised on the
+ * device; nothing is read or written past capacity.
  *  workspace: psi_sort_workspace_size(capacity) bytes. */
 int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity,
                   int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *workspace,
@@ -240,21 +256,27 @@ int psi_sort_keys(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d
 
 /* ---- a3 without caller scratch (no counterpart in the paper) ------------
  * Same result as psi_sort_keys, for callers that cannot allocate device memory
- * for a workspace: code recorded into a CUDA graph whose capture forbids
- * allocation, real-time loops that must not stall on an allocator, or plug-ins
- * running under a host framework that owns every device allocation. The
- * scratch is a fixed array inside the library (PSI_SORT_NOALLOC_SCRATCH_BYTES
- * per device, reserved when the library's module loads on that device and held
- * until the process exits); this call allocates and frees nothing.
+ * for a workspace: real-time loops that must not stall on an allocator, or
+ * plug-ins running under a host framework that owns every device allocation
+ * and hands them only their inputs and outputs. The scratch is a fixed array
+ * inside the library (PSI_SORT_NOALLOC_SCRATCH_BYTES per device, reserved when
+ * the library's module loads on that device and held until the process
+ * exits); this call allocates and frees nothing.
  *  - capacity must be <= PSI_SORT_NOALLOC_MAX_PAIRS, else PSI_ERR_INVALID_ARG.
+ *  - Devices 0 .. PSI_SORT_NOALLOC_MAX_DEVICES-1 only (PSI_ERR_INVALID_ARG
+ *    beyond).
  *  - The first call on a device (with that device current) looks up the
- *    array's device address; make that first call before any stream capture.
+ *    array's device address and keeps it for the life of the process; make
+ *    that first call before any stream capture. After cudaDeviceReset the
+ *    kept address is stale: do not call this entry point again in that
+ *    process.
  *  - All calls on a device share the one array and it keeps the previous
  *    call's contents (the sort needs nothing zeroed in it): calls that overlap
  *    on the GPU (different streams, or concurrent host threads) race and give
  *    wrong results. Serialise them on one stream. */
 #define PSI_SORT_NOALLOC_MAX_PAIRS (1 << 20)
 #define PSI_SORT_NOALLOC_SCRATCH_BYTES (13 << 20)
+#define PSI_SORT_NOALLOC_MAX_DEVICES 64
 int psi_sort_keys_noalloc(psi_ctx *ctx, uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs,
                           int64_t capacity, int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total,
                           psi_stream stream);
@@ -294,6 +316,11 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
                    const psi_render_opts *o, const float *g_rgb, const float *g_F, const float *g_T,
                    const psi_fwd_out *saved, const psi_grads *grads, void *workspace, size_t workspace_bytes,
                    psi_stream stream);
+
+/* Zero every non-NULL member of *grads ([n, 3], [n, 2], [n], [n, dim] floats
+ * as laid out in psi_grads) on `stream` with asynchronous memsets, before an
+ * accumulating psi_render_bwd. No counterpart in the paper. */
+int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi_stream stream);
 
 /* ---- launch-shape autotuner for a4 and a5 (no counterpart in the paper) ---
  * The compositing kernels are compiled in PSI_RENDER_SHAPES launch shapes:
@@ -415,6 +442,18 @@ int psi_quat_frames_bwd(psi_ctx *ctx, const float *q, int64_t n, const float *g_
 int psi_surfel_regularisers(psi_ctx *ctx, const psi_surfels *s, const int32_t *node_of, const float *node_mu,
                             const float *node_n, int64_t n_nodes, float lambda_n, float w_geo, float w_iso,
                             double *losses, const psi_grads *grads, psi_stream stream);
+
+/* ---- storage form of the feature table (precision of the features) -------
+ * The paper keeps FP32 features; their stored precision is a reading: BF16 is
+ * round-to-nearest-even of each value; FP8-E4M3 uses a per-channel scale
+ * scale[c] = max(amax_c, 1e-30) / 448 (amax_c = max over surfels of |f[., c]|,
+ * 448 = largest finite E4M3) and q = RNE(f / scale[c]) saturated to +-448, so
+ * that f ~= q * scale[c] (psi_features.scale). Accumulation is FP32 always.
+ *  f: [n, dim] float32; q: [n, dim] in dtype (PSI_BF16 or PSI_FP8_E4M3);
+ *  scale: [dim] float32, written for FP8 (ignored for BF16, may be NULL);
+ *  dim a multiple of 16 in [16, 256]; f, q, scale 16-byte aligned. */
+int psi_quantize_features(psi_ctx *ctx, const float *f, int64_t n, int dim, int dtype, void *q, float *scale,
+                          psi_stream stream);
 
 /* ---- per-surfel query logits: the decode fused into compositing ----------
  * table[g, q] = f_q^T f_g for every surfel (tensor cores, BF16 in, FP32

@@ -136,7 +136,9 @@ int psi_ctx_create(psi_ctx **out, int device)
     c->err[0] = 0;
     DeviceGuard g(device);
     cudaError_t e = cudaMalloc(&c->status, sizeof(psi::DevStatus));
-    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(psi::DevStatus));
+    psi::DevStatus init{};
+    init.wait_limit_ns = psi::kWaitLimitNs;
+    if (e == cudaSuccess) e = cudaMemcpy(c->status, &init, sizeof(init), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (c->status) cudaFree(c->status);
         delete c;
@@ -159,6 +161,19 @@ void psi_ctx_destroy(psi_ctx *ctx)
 
 const char *psi_last_error(const psi_ctx *ctx) { return ctx ? ctx->err : "NULL context"; }
 
+int psi_ctx_set_wait_limit_ns(psi_ctx *ctx, uint64_t ns)
+{
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (ns > PSI_WAIT_LIMIT_MAX_NS)
+        return fail(ctx, PSI_ERR_INVALID_ARG, "wait limit %llu ns above %llu", static_cast<unsigned long long>(ns),
+                    static_cast<unsigned long long>(PSI_WAIT_LIMIT_MAX_NS));
+    DeviceGuard g(ctx->device);
+    const unsigned long long v = ns ? ns : psi::kWaitLimitNs;
+    cudaError_t e = cudaMemcpy(reinterpret_cast<char *>(ctx->status) + offsetof(psi::DevStatus, wait_limit_ns), &v,
+                               sizeof(v), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_ctx_set_wait_limit_ns", e);
+}
+
 int psi_ctx_time_kernel(psi_ctx *ctx, int kernel, void *ev_begin, void *ev_end)
 {
     if (!ctx) return PSI_ERR_INVALID_ARG;
@@ -178,9 +193,9 @@ int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64
     psi::DevStatus h{};
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(ctx, "psi_status_fetch", e);
-    e = cudaMemcpy(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(&h, ctx->status, psi::kDevStatusReportBytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, "psi_status_fetch", e);
-    e = cudaMemset(ctx->status, 0, sizeof(h));
+    e = cudaMemset(ctx->status, 0, psi::kDevStatusReportBytes);
     if (e != cudaSuccess) return cuda_fail(ctx, "psi_status_fetch", e);
     int code = PSI_OK;
     // report the most severe: timeout, then capacity, then invalid argument
@@ -685,6 +700,41 @@ int psi_surfel_geometry_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_camera
     DeviceGuard g(ctx->device);
     cudaError_t e = psi::launch_geometry_bwd(*s, *cam, g_table, ld, *grads, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_surfel_geometry_bwd", e);
+}
+
+int psi_quantize_features(psi_ctx *ctx, const float *f, int64_t n, int dim, int dtype, void *q, float *scale,
+                          psi_stream stream)
+{
+    NvtxRange nvtx_range(__func__);
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (n < 0 || dim < 16 || dim > 256 || dim % 16) return fail(ctx, PSI_ERR_INVALID_ARG, "need n >= 0, dim in [16, 256] a multiple of 16");
+    if (dtype != PSI_BF16 && dtype != PSI_FP8_E4M3) return fail(ctx, PSI_ERR_INVALID_ARG, "dtype must be PSI_BF16 or PSI_FP8_E4M3");
+    if (n > 0 && (!f || !q)) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (dtype == PSI_FP8_E4M3 && !scale) return fail(ctx, PSI_ERR_INVALID_ARG, "FP8 needs a scale buffer");
+    if (!aligned(f, 16) || !aligned(q, 16) || !aligned(scale, 16))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "f, q and scale must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = psi::launch_quantize(f, n, dim, dtype, q, scale, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_quantize_features", e);
+}
+
+int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi_stream stream)
+{
+    NvtxRange nvtx_range(__func__);
+    if (!ctx) return PSI_ERR_INVALID_ARG;
+    if (!grads || n < 0 || dim < 0) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL grads or negative size");
+    DeviceGuard g(ctx->device);
+    auto st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t N = static_cast<size_t>(n);
+    struct { float *p; size_t w; } parts[] = {{grads->mu, 3},    {grads->tu, 3},      {grads->tv, 3},
+                                              {grads->scale, 2}, {grads->opacity, 1}, {grads->rgb, 3},
+                                              {grads->feat, static_cast<size_t>(dim)}};
+    for (const auto &pt : parts) {
+        if (!pt.p || pt.w == 0 || N == 0) continue;
+        cudaError_t e = cudaMemsetAsync(pt.p, 0, N * pt.w * sizeof(float), st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "psi_grads_zero", e);
+    }
+    return PSI_OK;
 }
 
 int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream)

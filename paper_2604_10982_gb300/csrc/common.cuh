@@ -12,12 +12,16 @@ namespace psi {
 
 // Device status word layout (see psi_status_fetch): [0] OR of error codes as
 // bits (1 << code), [1] code of the first bounded wait that gave up,
-// [2..3] int64 pairs required on overflow.
+// [2..3] int64 pairs required on overflow (these 16 bytes are read and
+// cleared by psi_status_fetch); then the context's wait limit in ns
+// (psi_ctx_set_wait_limit_ns), kept across fetches.
 struct DevStatus {
     int32_t flags;
     int32_t wait_site;
     unsigned long long required_pairs;
+    unsigned long long wait_limit_ns;
 };
+constexpr size_t kDevStatusReportBytes = 16;
 
 __device__ __forceinline__ void raise_status(DevStatus *st, int code)
 {
@@ -70,8 +74,19 @@ __device__ __forceinline__ int view_of_tile(const FrameParams &fp, uint32_t t)
 }
 
 // ---------------------------------------------------------------- waits
-// Every spin in this library is bounded by wall time read from %globaltimer.
+// Every spin in this library is bounded by wall time read from %globaltimer:
+// by the context's limit (1 s unless psi_ctx_set_wait_limit_ns changed it) for
+// the waits of the pipelines, and always by the fixed 1 s for the drains that
+// let in-flight copies and MMA groups land after a give-up, so that a short
+// limit can never release shared memory or TMEM that a copy still writes.
 constexpr unsigned long long kWaitLimitNs = 1000000000ull; // 1 s
+
+__device__ __forceinline__ unsigned long long wait_limit(const DevStatus *st)
+{
+    if (!st) return kWaitLimitNs;
+    const unsigned long long l = *reinterpret_cast<const volatile unsigned long long *>(&st->wait_limit_ns);
+    return l ? l : kWaitLimitNs;
+}
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -129,9 +144,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DevStatus *st, int site = 0)
 {
     if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long limit = site == kSiteDrain ? kWaitLimitNs : wait_limit(st);
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit) {
             if (st) {
                 atomicCAS(&st->wait_site, 0, site);
                 raise_status(st, PSI_ERR_TIMEOUT);
@@ -176,7 +192,7 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pai
                         int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total, void *ws, DevStatus *status,
                         cudaStream_t st);
 
-constexpr int PSI_MAX_DEVICES_NOALLOC = 64;
+constexpr int PSI_MAX_DEVICES_NOALLOC = PSI_SORT_NOALLOC_MAX_DEVICES;
 cudaError_t launch_sort_noalloc(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity,
                                 int begin_bit, int end_bit, uint32_t *tile_ranges, int64_t n_tiles_total,
                                 DevStatus *status, cudaStream_t st, const char **why);
@@ -230,6 +246,7 @@ cudaError_t launch_attention_bwd(void *cublas, int64_t N, int C, int n_q, const 
                                  const float *WK, const float *WV, int d, const float *G, float *gQ, float *gWQ,
                                  float *gWK, float *gWV, const float *mu, float *g_feat, float *g_mu, void *ws,
                                  cudaStream_t st, const char **why);
+cudaError_t launch_quantize(const float *f, int64_t n, int dim, int dtype, void *q, float *scale, cudaStream_t st);
 cudaError_t launch_frames(const float *q, int64_t n, float *tu, float *tv, cudaStream_t st);
 cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
                               cudaStream_t st);

@@ -255,6 +255,7 @@ __device__ __forceinline__ bool pipe_produce(Pipe &P, const uint32_t *__restrict
     const int nb = (n + kPB - 1) / kPB;
     int issued = 0, done = 0; // batches issued / transformed
     unsigned long long t_idle = 0;
+    const unsigned long long limit = wait_limit(st);
     bool ok = true;
     while (done < nb) {
         if (vload(P.alive) == 0 || vload(P.abort)) break;
@@ -298,7 +299,7 @@ __device__ __forceinline__ bool pipe_produce(Pipe &P, const uint32_t *__restrict
             const unsigned long long now = global_ns();
             if (t_idle == 0) {
                 t_idle = now;
-            } else if (now - t_idle > kWaitLimitNs) {
+            } else if (now - t_idle > limit) {
                 if (lane == 0 && st) {
                     atomicCAS(&st->wait_site, 0, site);
                     raise_status(st, PSI_ERR_TIMEOUT);
@@ -329,6 +330,7 @@ __device__ __forceinline__ bool pipe_wait_ready(Pipe &P, int b, DevStatus *st, i
     const uint32_t par = (b / kPS) & 1;
     bool ready = mbar_try_wait(&P.ready[s], par);
     if (!ready) {
+        const unsigned long long limit = wait_limit(st);
         const unsigned long long t0 = global_ns();
         while (true) {
             if (mbar_try_wait(&P.ready[s], par)) {
@@ -336,7 +338,7 @@ __device__ __forceinline__ bool pipe_wait_ready(Pipe &P, int b, DevStatus *st, i
                 break;
             }
             if (vload(P.abort) || vload(P.alive) == 0) break;
-            if (global_ns() - t0 > kWaitLimitNs) {
+            if (global_ns() - t0 > limit) {
                 if (st) {
                     atomicCAS(&st->wait_site, 0, site);
                     raise_status(st, PSI_ERR_TIMEOUT);

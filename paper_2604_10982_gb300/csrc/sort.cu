@@ -22,15 +22,28 @@ constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems; // 4096 pairs per block
 constexpr int kBins = 256;
 
+// Pair count of the call: *d_n clamped to the buffers' capacity (more pairs
+// than the buffers hold is a capacity error, raised once by the first pass).
+__device__ __forceinline__ int64_t clamped_count(const int64_t *d_n, int64_t cap)
+{
+    const int64_t n = *d_n;
+    return n < 0 ? 0 : (n > cap ? cap : n);
+}
+
 __global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *__restrict__ keys,
-                                                           const int64_t *__restrict__ d_n, int shift, int bits,
-                                                           uint32_t *__restrict__ hist, int nblk)
+                                                           const int64_t *__restrict__ d_n, int64_t cap, int shift,
+                                                           int bits, uint32_t *__restrict__ hist, int nblk,
+                                                           DevStatus *status)
 {
     __shared__ uint32_t h[kWarps][kBins];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < kWarps * kBins; k += kThreads) (&h[0][0])[k] = 0;
     __syncthreads();
-    const int64_t n = *d_n;
+    const int64_t n = clamped_count(d_n, cap);
+    if (status && blockIdx.x == 0 && threadIdx.x == 0 && *d_n > cap) {
+        raise_status(status, PSI_ERR_CAPACITY);
+        atomicMax(&status->required_pairs, static_cast<unsigned long long>(*d_n));
+    }
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + wid * (32 * kItems);
     const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
     if (static_cast<int64_t>(blockIdx.x) * kTile < n) {
@@ -62,13 +75,14 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *__res
                                                            const uint32_t *__restrict__ vals_in,
                                                            uint64_t *__restrict__ keys_out,
                                                            uint32_t *__restrict__ vals_out,
-                                                           const int64_t *__restrict__ d_n, int shift, int bits,
-                                                           const unsigned long long *__restrict__ offs, int nblk)
+                                                           const int64_t *__restrict__ d_n, int64_t cap, int shift,
+                                                           int bits, const unsigned long long *__restrict__ offs,
+                                                           int nblk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t n = *d_n;
+    const int64_t n = clamped_count(d_n, cap);
     const int64_t blk0 = static_cast<int64_t>(blockIdx.x) * kTile;
     if (blk0 >= n) return;
     const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
@@ -155,9 +169,10 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *__res
 }
 
 __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *__restrict__ d_n,
-                                                     uint32_t *__restrict__ ranges, int64_t n_tiles, DevStatus *status)
+                                                     int64_t cap, uint32_t *__restrict__ ranges, int64_t n_tiles,
+                                                     DevStatus *status)
 {
-    const int64_t n = *d_n;
+    const int64_t n = clamped_count(d_n, cap);
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t t = keys[i] >> 32;
@@ -251,19 +266,19 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pai
         int shift = begin_bit + ps * dbits;
         const int bits = std::max(0, std::min(dbits, end_bit - shift));
         if (bits == 0) shift = 0; // identity pass (keeps the pass count even)
-        upsweep_kernel<<<static_cast<unsigned>(nblk), kThreads, 0, st>>>(kin, d_num_pairs, shift, bits, hist,
-                                                                         static_cast<int>(nblk));
+        upsweep_kernel<<<static_cast<unsigned>(nblk), kThreads, 0, st>>>(
+            kin, d_num_pairs, cap, shift, bits, hist, static_cast<int>(nblk), ps == 0 ? status : nullptr);
         cudaError_t e = launch_scan_u32(hist, offs, nh, scan_total, scan_ws, st);
         if (e != cudaSuccess) return e;
         scatter_kernel<<<static_cast<unsigned>(nblk), kThreads, sizeof(ScatterSmem), st>>>(
-            kin, vin, kout, vout, d_num_pairs, shift, bits, offs, static_cast<int>(nblk));
+            kin, vin, kout, vout, d_num_pairs, cap, shift, bits, offs, static_cast<int>(nblk));
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
     if (tile_ranges && n_tiles_total > 0) {
         cudaError_t e = cudaMemsetAsync(tile_ranges, 0, static_cast<size_t>(n_tiles_total) * 8, st);
         if (e != cudaSuccess) return e;
-        ranges_kernel<<<static_cast<unsigned>((cap + 255) / 256), 256, 0, st>>>(keys, d_num_pairs, tile_ranges,
+        ranges_kernel<<<static_cast<unsigned>((cap + 255) / 256), 256, 0, st>>>(keys, d_num_pairs, cap, tile_ranges,
                                                                                n_tiles_total, status);
         tile_order_kernel<<<1, 1024, 0, st>>>(tile_ranges, n_tiles_total, tile_ranges + 2 * n_tiles_total);
     }
@@ -279,7 +294,8 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pai
 // device address is looked up once per device with cudaGetSymbolAddress.
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(13) << 20; // 13 MiB: sort scratch for 2^20 pairs
+constexpr size_t kNoAllocScratchBytes = PSI_SORT_NOALLOC_SCRATCH_BYTES; // 13 MiB: sort scratch for 2^20 pairs
+static_assert(kNoAllocScratchBytes >= 12u * PSI_SORT_NOALLOC_MAX_PAIRS, "scratch must hold the alternate key and value buffers");
 static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocScratchBytes];
 
 std::mutex g_scratch_mu;

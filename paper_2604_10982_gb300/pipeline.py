@@ -13,23 +13,31 @@ import torch
 from . import psi
 
 
-def quantize_features(f: torch.Tensor, dtype: int):
-    """Storage form of an [N, D] float32 feature table.
+_quant_ctx = {}
 
-    F32: as is. BF16: round to nearest even. FP8-E4M3: per-channel scale
-    amax_c / 448 and q = RNE(f / scale) (saturated to +-448), so that
-    f ~= q * scale[c]. Returns (q, scale or None)."""
+
+def quantize_features(f: torch.Tensor, dtype: int, ctx=None):
+    """Storage form of an [N, D] float32 feature table on the device, computed
+    by psi_quantize_features: F32 as is; BF16 round to nearest even;
+    FP8-E4M3 with the per-channel scale amax_c / 448 and q = RNE(f / scale)
+    saturated to +-448, so that f ~= q * scale[c]. Returns (q, scale or None)."""
     f = f.contiguous()
     if dtype == psi.F32:
         return f, None
+    if dtype not in (psi.BF16, psi.FP8_E4M3):
+        raise ValueError(f"unknown feature dtype {dtype}")
+    if ctx is None:
+        dev = f.device.index if f.device.index is not None else torch.cuda.current_device()
+        ctx = _quant_ctx.get(dev) or _quant_ctx.setdefault(dev, psi.Context(dev))
+    n, d = f.shape
     if dtype == psi.BF16:
-        return f.to(torch.bfloat16).contiguous(), None
-    if dtype == psi.FP8_E4M3:
-        amax = f.abs().amax(0).clamp_min(1e-30)
-        scale = (amax / 448.0).float().contiguous()
-        q = (f / scale).clamp(-448.0, 448.0).to(torch.float8_e4m3fn).contiguous()
-        return q, scale
-    raise ValueError(f"unknown feature dtype {dtype}")
+        q = torch.empty(n, d, dtype=torch.bfloat16, device=f.device)
+        psi.psi_quantize_features(ctx, f, n, d, dtype, q, None)
+        return q, None
+    q = torch.empty(n, d, dtype=torch.float8_e4m3fn, device=f.device)
+    scale = torch.empty(d, dtype=torch.float32, device=f.device)
+    psi.psi_quantize_features(ctx, f, n, d, dtype, q, scale)
+    return q, scale
 
 
 def dequantize(q: torch.Tensor, scale, dtype: int) -> np.ndarray:
@@ -132,7 +140,7 @@ class Renderer:
         nbits = max(self.key_bits, 1)
         passes = max(2, (nbits + 7) // 8)
         passes += passes & 1
-        n += passes * 5 + 1                                # upsweep + scan(3) + scatter per pass, ranges
+        n += passes * 5 + 2                                # upsweep + scan(3) + scatter per pass, ranges, tile order
         K = int(self.opts.top_k)
         D = self.D
         ch = 32 if D % 32 == 0 else 16

@@ -98,6 +98,9 @@ def lib():
                                      ctypes.POINTER(PsiCamera), ctypes.c_int, ctypes.POINTER(PsiRenderOpts), _P, _P, _P,
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.psi_ctx_set_wait_limit_ns.argtypes = [_P, ctypes.c_uint64]
+        L.psi_quantize_features.argtypes = [_P, _P, _i64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+        L.psi_grads_zero.argtypes = [_P, ctypes.POINTER(PsiGrads), _i64, ctypes.c_int, _P]
         L.psi_tune_render_fwd.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _P, _P, ctypes.POINTER(PsiCamera),
                                           ctypes.c_int, _i64, ctypes.POINTER(PsiRenderOpts),
                                           ctypes.POINTER(PsiFwdOut), ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
@@ -341,6 +344,21 @@ def psi_ctx_get_render_shape(ctx, which, opts, feat_dtype, saved):
     ctx.check(lib().psi_ctx_get_render_shape(ctx.handle, int(which), ctypes.byref(opts), int(feat_dtype), int(saved),
                                              ctypes.byref(v)), "psi_ctx_get_render_shape")
     return int(v.value)
+
+
+def psi_quantize_features(ctx, f, n, dim, dtype, q, scale=None, stream=None):
+    ctx.check(lib().psi_quantize_features(ctx.handle, _ptr(f), int(n), int(dim), int(dtype), _ptr(q), _ptr(scale),
+                                          _stream(stream)), "psi_quantize_features")
+
+
+def psi_grads_zero(ctx, grads: "PsiGrads", n, dim, stream=None):
+    ctx.check(lib().psi_grads_zero(ctx.handle, ctypes.byref(grads), int(n), int(dim), _stream(stream)),
+              "psi_grads_zero")
+
+
+def psi_ctx_set_wait_limit_ns(ctx, ns):
+    """Limit of the kernels' bounded waits on this context (0 = the default 1 s)."""
+    ctx.check(lib().psi_ctx_set_wait_limit_ns(ctx.handle, int(ns)), "psi_ctx_set_wait_limit_ns")
 
 
 def psi_ctx_time_kernel(ctx, kernel, ev_begin, ev_end):

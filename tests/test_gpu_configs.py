@@ -114,21 +114,54 @@ def test_batch_16_views_one_launch_and_graph(ctx, dtype):
 
 
 def test_panoptic_full_size_sampled(ctx):
-    """3M surfels, 1920x1080, D=128 BF16, K=8, Q=100: sampled pixels of the
-    rendered frame and of the decoded ids against the oracle."""
+    """3M surfels, 1920x1080, D=128 BF16, K=8, Q=100: 2048 sampled pixels of
+    the rendered frame against the oracle -- colour and T to 1e-4, the BF16
+    feature map to 2e-2 relative, the Top-K id sets equal -- on every pixel
+    that is not excused; the excused shares (threshold straddles,
+    ill-conditioned pixels, near ties) are reported with the largest error over
+    them, and held to their own bounds. Decoded ids on 4096 pixels against an
+    FP64 matmul of the GPU's own feature map."""
     from paper_2604_10982_gb300 import pipeline as pl, psi
+    from .gpu_common import GROSS, cond_bound, flags
     w = sg.panoptic_scene(frames=2)
     cam = w.cameras[0]
     o = orc.Opts(mode=orc.EXACT, top_k=8, opacity_radius=True)
     scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.BF16)
-    r = pl.make_renderer(ctx, scene, [cam], opts_of(o), D=128, F_dtype=psi.BF16)
+    r = pl.make_renderer(ctx, scene, [cam], opts_of(o), D=128, F_dtype=psi.BF16, want_topk_ids=True)
     r.frame(scene)
     Q = torch.from_numpy(w.queries).cuda().to(torch.bfloat16)
     ids = torch.empty(r.n_pix, dtype=torch.int32, device="cuda")
     psi.psi_decode_queries(ctx, r.F, r.n_pix, 128, Q, 100, r.T, ids)
     torch.cuda.synchronize()
+    assert ctx.status_fetch()[0] == 0
     deq = pl.dequantize(scene.q, None, psi.BF16)
-    _sampled_parity(r, w, [cam], o, deq, n_per_view=128, bf16_rel=2e-2)
+    idx = np.random.default_rng(11).choice(r.n_pix, 2048, replace=False)
+    ref = orc.render(w.surfels, cam, o, feat=deq, pixels=orc.all_pixels(cam)[idx])
+    rgb = r.rgb.cpu().numpy().astype(np.float64)[:, idx].T
+    T = r.T.cpu().numpy().astype(np.float64)[idx]
+    F = r.F.float().cpu().numpy().astype(np.float64)[idx]
+    tk = r.topk_ids.cpu().numpy()[idx]
+    st, ic, nt = flags(ref, cam)
+    strict = ~(st | ic)
+    e_px = np.maximum(np.abs(rgb - ref["rgb"]).max(1), np.abs(T - ref["T"]))
+    relF = np.abs(F - ref["F"]).max(1) / (np.abs(ref["F"]).max(1) + 1e-3)
+    same = np.array([set(tk[p][tk[p] >= 0].tolist()) == set(ref["topk"][p][ref["topk"][p] >= 0].tolist())
+                     for p in range(len(idx))])
+    icm = ic & ~st
+    report = dict(pixels=len(idx), straddle=float(st.mean()), ill_conditioned=float(icm.mean()),
+                  near_tie=float(nt.mean()), max_err_strict=float(e_px[strict].max(initial=0)),
+                  max_err_ill_conditioned=float(e_px[icm].max(initial=0)),
+                  max_err_straddle=float(e_px[st].max(initial=0)),
+                  topk_set_mismatch_strict=int((strict & ~nt & ~same).sum()),
+                  topk_set_mismatch_excused=int((~(strict & ~nt) & ~same).sum()),
+                  max_relF_strict=float(relF[strict & ~nt].max(initial=0)))
+    print("panoptic 1080p parity:", report)
+    assert report["max_err_strict"] < 1e-4, report
+    assert report["max_relF_strict"] < 2e-2, report
+    assert report["topk_set_mismatch_strict"] == 0, report
+    assert (e_px[icm] < cond_bound(ref, cam)[icm]).all(), report
+    assert e_px.max() < GROSS, report
+    assert (~strict).mean() <= 0.25, report
     # decode of the GPU's own feature map on sampled pixels (FP64 matmul)
     idx = np.random.default_rng(7).choice(r.n_pix, 4096, replace=False)
     Fs = r.F.float().cpu().numpy()[idx].astype(np.float64)

@@ -146,6 +146,38 @@ def test_sort_random_keys_vs_stable_argsort(ctx):
         assert np.array_equal(vv[:n].cpu().numpy().view(np.uint32), vals[perm])
 
 
+def test_sort_count_beyond_capacity_is_clamped(ctx):
+    """*d_num_pairs larger than the buffers: the first `capacity` pairs are
+    sorted and ranged, PSI_ERR_CAPACITY is raised with the requested count,
+    and nothing past capacity is touched."""
+    from paper_2604_10982_gb300 import psi
+    rng = np.random.default_rng(9)
+    cap, bits = 70_001, 40
+    keys = (rng.integers(0, 1 << (bits - 32), cap, dtype=np.uint64) << np.uint64(32)) | \
+        rng.integers(0, 1 << 20, cap, dtype=np.uint64)
+    vals = np.arange(cap, dtype=np.uint32)
+    guard = 4096
+    kk = torch.full((cap + guard,), -7, dtype=torch.int64, device="cuda")
+    vv = torch.full((cap + guard,), -7, dtype=torch.int32, device="cuda")
+    kk[:cap] = torch.from_numpy(keys.view(np.int64)).cuda()
+    vv[:cap] = torch.from_numpy(vals.view(np.int32)).cuda()
+    npairs = torch.tensor([cap + 5], dtype=torch.int64, device="cuda")
+    ws = torch.empty(psi.sort_workspace_size(cap), dtype=torch.uint8, device="cuda")
+    nt = 1 << (bits - 32)
+    ranges = torch.empty(nt * 3, dtype=torch.int32, device="cuda")
+    ctx.status_fetch()
+    psi.psi_sort_keys(ctx, kk, vv, npairs, cap, 0, bits, ranges, nt, ws)
+    st, detail = ctx.status_fetch()
+    assert st == psi.PSI_ERR_CAPACITY and detail == cap + 5, (st, detail)
+    perm = np.argsort(keys, kind="stable")
+    assert np.array_equal(kk[:cap].cpu().numpy().view(np.uint64), keys[perm])
+    assert np.array_equal(vv[:cap].cpu().numpy().view(np.uint32), vals[perm])
+    assert (kk[cap:] == -7).all() and (vv[cap:] == -7).all()
+    rg = ranges[: 2 * nt].cpu().numpy().view(np.uint32).reshape(nt, 2).astype(np.int64)
+    cnt = np.bincount((keys >> np.uint64(32)).astype(np.int64), minlength=nt)
+    assert np.array_equal(rg[:, 1] - rg[:, 0], cnt)
+
+
 def _compare_render(r, scene, w, cams, o, D, feat64, bf16_out=False):
     rgb = r.rgb.cpu().numpy().astype(np.float64)
     T = r.T.cpu().numpy().astype(np.float64)

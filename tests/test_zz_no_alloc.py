@@ -1,10 +1,9 @@
 """psi_sort_keys_noalloc: the sort for callers that cannot allocate device
 memory (needs a GPU).
 
-Some callers cannot hand the library a workspace: a loop recorded into a CUDA
-graph where allocation is not allowed, a real-time control thread that must
-not wait on an allocator, or a plug-in whose host framework owns all device
-memory. For them the sort has an entry point whose scratch is a fixed array
+Some callers cannot hand the library a workspace: a real-time control thread
+that must not wait on an allocator, or a plug-in whose host framework owns all
+device memory and passes it only inputs and outputs. For them the sort has an entry point whose scratch is a fixed array
 inside the library. Its results must equal those of psi_sort_keys with a
 caller workspace, call after call, since every call reuses the same array.
 
