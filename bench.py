@@ -785,26 +785,45 @@ def run_psi(args):
         del rg, gg, Gt
 
     # ---- frustum-constrained cross-attention (Sec. 4.1) over all surfels
-    # for one view: 100 queries, C = d = 128 (FP32 GEMMs)
+    # for one view: 100 queries, C = d = 128, BF16 features; forward and adjoint
     attn = None
     if args.label_frames > 0:
         rng = np.random.default_rng(6)
         Wa = [torch.from_numpy((rng.normal(size=(D, D)) / np.sqrt(D)).astype(np.float32)).to(dev) for _ in range(3)]
         Qa = torch.from_numpy(rng.normal(size=(nq, D)).astype(np.float32)).to(dev)
+        Ga = torch.from_numpy(rng.normal(size=(nq, D)).astype(np.float32)).to(dev)
         outa = torch.empty(nq, D, device=dev)
+        gQa, gW = torch.empty(nq, D, device=dev), [torch.empty(D, D, device=dev) for _ in range(3)]
         wsa = torch.empty(psi.attention_workspace_size(scene.n, D, D, nq), dtype=torch.uint8, device=dev)
+        gsa = psi.PsiGrads(psi._ptr(grads["mu"]), None, None, None, None, None, psi._ptr(grads["feat"]))
         ca = psi.cameras([cams[0]])
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        for rep in range(3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fw, bw = [], []
+        for rep in range(4):
             ev[0].record()
             psi.psi_frustum_attention(ctx, scene.surfels_struct(), scene.features_struct(), ca[0], 0.2, Qa, nq,
                                       Wa[0], Wa[1], Wa[2], D, outa, wsa)
             ev[1].record()
+            psi.psi_frustum_attention_bwd(ctx, scene.surfels_struct(), scene.features_struct(), Qa, nq, Wa[0], Wa[1],
+                                          Wa[2], D, Ga, gQa, gW[0], gW[1], gW[2], gsa, wsa)
+            ev[2].record()
             torch.cuda.synchronize()
-        flops = 2.0 * scene.n * D * D * 2 + 2.0 * nq * scene.n * D * 2  # K and V projections, scores, output
-        attn = {"ms": float(ev[0].elapsed_time(ev[1])), "surfels": scene.n, "queries": nq, "C": D, "d": D,
-                "tflops_fp32": flops / (ev[0].elapsed_time(ev[1]) / 1000.0) / 1e12,
-                "form": "mask + K, V rows (kernel), FP32 cuBLAS projections and products, masked softmax (kernel)"}
+            if rep > 0:
+                fw.append(ev[0].elapsed_time(ev[1]))
+                bw.append(ev[1].elapsed_time(ev[2]))
+        st, _ = ctx.status_fetch()
+        assert st == 0, f"device status {st}"
+        fms, bms = float(np.median(fw)), float(np.median(bw))
+        flops = 4.0 * nq * scene.n * D  # scores and the weighted sum over the surfels (folded form)
+        fbytes = scene.n * (2.0 * D + 20.0)  # BF16 feature row, centre and scales per surfel
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+        attn = {"fwd_ms": fms, "bwd_ms": bms, "surfels": scene.n, "queries": nq, "C": D, "d": D,
+                "fwd_tflops": flops / (fms / 1000.0) / 1e12,
+                "fwd_tflops_frac_of_bf16": flops / (fms / 1000.0) / 1e12 / bf16_peak,
+                "fwd_hbm_frac": fbytes / (fms / 1000.0) / 1e9 / hbm_peak,
+                "form": "tcgen05 kernels, BF16 operands / FP32 accumulation: per 128-surfel tile S = qh [f|psi]^T, "
+                        "online masked softmax, O += P f; queries folded qh = (Q W_Q) W_K^T / sqrt(d), output O W_V. "
+                        "Adjoint: P recomputed per tile, dqh, dK, dV on the tensor cores"}
         del wsa
 
     # ---- the paper's Table 3 rows on this GPU: tile test x feature selection,

@@ -379,21 +379,31 @@ int psi_decode_queries(psi_ctx *ctx, const void *F, int64_t n_pix, int D, const 
  *   Q'_i = softmax_j((Q_i W_Q)(K_j W_K)^T / sqrt(d)) (V_j W_V).
  * psi: channel c encodes axis c mod 3 with sin (t = c/3 even) or cos (t odd)
  * at frequency 10000^(-6k/C), k = t/2 (the paper leaves psi open).
- * Products are FP32 cuBLAS GEMMs (the context creates its handle on first
- * use) over all n surfels with the inactive ones masked in the softmax (no
- * host synchronisation). An empty active set gives Q' = 0.
- *  f: the feature table (any dtype, dim C); Q: [n_q, C]; W_Q, W_K, W_V:
- *  [C, d]; out: [n_q, d]; all float32 row-major, device.
- *  workspace: psi_attention_workspace_size(n, C, d, n_q) bytes. */
+ * Computed as e_ij = qh_i . K_j with qh = (Q W_Q) W_K^T / sqrt(d) and Q' =
+ * (sum_j P_ij V_j) W_V (associativity), so per surfel only the two
+ * contractions with qh and with P run, on the tensor cores: BF16 operands
+ * (qh, f, psi(mu), P rounded to BF16), FP32 accumulation, online softmax in
+ * FP32; the feature table is read once. Inactive surfels are masked (weight
+ * 0); no host synchronisation. An empty active set gives Q' = 0.
+ *  f: BF16 feature table without scale, dim C in {64, 128} (other tables:
+ *  PSI_ERR_UNSUPPORTED; psi_quantize_features makes one); n < 2^31 surfels;
+ *  Q: [n_q, C] float32, 1 <= n_q <= 128; W_Q, W_K, W_V: [C, d] float32,
+ *  1 <= d <= 256; out: [n_q, d] float32; all row-major, device.
+ *  workspace: psi_attention_workspace_size(n, C, d, n_q) bytes (it keeps the
+ *  view, the per-query softmax statistics and the attended values for the
+ *  adjoint). */
 int psi_attention_workspace_size(int64_t n, int C, int d, int n_q, size_t *bytes);
 int psi_frustum_attention(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const psi_camera *cam,
                           float z_near, const float *Q, int n_q, const float *W_Q, const float *W_K, const float *W_V,
                           int d, float *out, void *workspace, size_t workspace_bytes, psi_stream stream);
 /* Its adjoint for L = <g_out, Q'> ([n_q, d]), reusing the workspace exactly as
- * the preceding psi_frustum_attention left it (same surfels, features and
- * weights): writes g_Q [n_q, C], g_WQ / g_WK / g_WV [C, d] (each may be
- * NULL) and ADDS dL/df (grads->feat, w.r.t. the dequantised values) and
- * dL/dmu through psi (grads->mu) for the active surfels. */
+ * the preceding psi_frustum_attention left it (same surfels, features,
+ * queries and weights; the view is taken from the workspace): writes g_Q
+ * [n_q, C], g_WQ / g_WK / g_WV [C, d] (each may be NULL) and ADDS dL/df
+ * (grads->feat, [n, C] float32, 16-byte aligned) and dL/dmu through psi
+ * (grads->mu) for the active surfels. The softmax weights are recomputed per
+ * tile of surfels from the forward's per-query maximum and sum; the same BF16
+ * operand rounding as the forward. */
 int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, const float *Q, int n_q,
                               const float *W_Q, const float *W_K, const float *W_V, int d, const float *g_out,
                               float *g_Q, float *g_WQ, float *g_WK, float *g_WV, const psi_grads *grads,

@@ -4,7 +4,6 @@
 #include <cstring>
 #include <new>
 
-#include <cublas_v2.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
@@ -14,7 +13,6 @@ struct psi_ctx {
     int device;
     psi::DevStatus *status;
     char err[512];
-    void *cublas; // created on first use by psi_frustum_attention
     // armed kernel-timing events per psi_kernel_id: [id][0] begin, [id][1] end
     cudaEvent_t time_ev[3][2];
     // launch shape of the compositing kernels per (K class, feature dtype,
@@ -154,7 +152,6 @@ void psi_ctx_destroy(psi_ctx *ctx)
     {
         DeviceGuard g(ctx->device);
         if (ctx->status) cudaFree(ctx->status);
-        if (ctx->cublas) cublasDestroy(static_cast<cublasHandle_t>(ctx->cublas));
     }
     delete ctx;
 }
@@ -623,23 +620,21 @@ int psi_frustum_attention(psi_ctx *ctx, const psi_surfels *s, const psi_features
     psi::FeatView fv;
     if ((rc = check_feat(ctx, f, fv))) return rc;
     if (!fv.data) return fail(ctx, PSI_ERR_INVALID_ARG, "features are required");
+    if (fv.dtype != PSI_BF16 || fv.scale || (fv.dim != 64 && fv.dim != 128))
+        return fail(ctx, PSI_ERR_UNSUPPORTED, "psi_frustum_attention: BF16 features without scale, dim 64 or 128 "
+                                              "(convert with psi_quantize_features)");
     if (!cam || cam->width < 1 || cam->height < 1) return fail(ctx, PSI_ERR_INVALID_ARG, "bad camera");
-    if (s->n >= (int64_t(1) << 31) || static_cast<int64_t>(n_q) * s->n >= (int64_t(1) << 40))
-        return fail(ctx, PSI_ERR_INVALID_ARG, "too many surfels");
-    if (n_q < 1 || d < 1 || !Q || !W_Q || !W_K || !W_V || !out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (s->n >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "too many surfels");
+    if (n_q < 1 || n_q > 128 || d < 1 || d > 256) return fail(ctx, PSI_ERR_INVALID_ARG, "need 1 <= n_q <= 128, 1 <= d <= 256");
+    if (!Q || !W_Q || !W_K || !W_V || !out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
     const size_t need = psi::attention_workspace_bytes(s->n, fv.dim, d, n_q);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
         return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
     if (s->n == 0) return fail(ctx, PSI_ERR_INVALID_ARG, "no surfels to attend to");
     DeviceGuard g(ctx->device);
-    if (!ctx->cublas) {
-        cublasHandle_t h = nullptr;
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return fail(ctx, PSI_ERR_CUDA, "cublasCreate failed");
-        ctx->cublas = h;
-    }
     const char *why = nullptr;
-    cudaError_t e = psi::launch_attention(ctx->cublas, *s, fv.data, fv.scale, fv.dtype, fv.dim, *cam, z_near, Q, n_q,
-                                          W_Q, W_K, W_V, d, out, workspace, reinterpret_cast<cudaStream_t>(stream), &why);
+    cudaError_t e = psi::launch_attention(*s, fv.data, fv.dim, *cam, z_near, Q, n_q, W_Q, W_K, W_V, d, out, workspace,
+                                          ctx->status, reinterpret_cast<cudaStream_t>(stream), &why);
     if (why) return fail(ctx, PSI_ERR_CUDA, "psi_frustum_attention: %s", why);
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_frustum_attention", e);
 }
@@ -656,17 +651,21 @@ int psi_frustum_attention_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_feat
     psi::FeatView fv;
     if ((rc = check_feat(ctx, f, fv))) return rc;
     if (!fv.data || s->n == 0) return fail(ctx, PSI_ERR_INVALID_ARG, "features and surfels are required");
-    if (n_q < 1 || d < 1 || !Q || !W_Q || !W_K || !W_V || !g_out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (fv.dtype != PSI_BF16 || fv.scale || (fv.dim != 64 && fv.dim != 128))
+        return fail(ctx, PSI_ERR_UNSUPPORTED, "psi_frustum_attention_bwd: BF16 features without scale, dim 64 or 128");
+    if (s->n >= (int64_t(1) << 31)) return fail(ctx, PSI_ERR_INVALID_ARG, "too many surfels");
+    if (n_q < 1 || n_q > 128 || d < 1 || d > 256) return fail(ctx, PSI_ERR_INVALID_ARG, "need 1 <= n_q <= 128, 1 <= d <= 256");
+    if (!Q || !W_Q || !W_K || !W_V || !g_out) return fail(ctx, PSI_ERR_INVALID_ARG, "NULL argument");
+    if (grads && grads->feat && !aligned(grads->feat, 16))
+        return fail(ctx, PSI_ERR_INVALID_ARG, "grads->feat must be 16-byte aligned");
     const size_t need = psi::attention_workspace_bytes(s->n, fv.dim, d, n_q);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
         return fail(ctx, PSI_ERR_INVALID_ARG, "workspace must be >= %zu bytes, 256-byte aligned", need);
-    if (!ctx->cublas) return fail(ctx, PSI_ERR_INVALID_ARG, "run psi_frustum_attention first");
     DeviceGuard g(ctx->device);
     const char *why = nullptr;
-    cudaError_t e = psi::launch_attention_bwd(ctx->cublas, s->n, fv.dim, n_q, Q, W_Q, W_K, W_V, d, g_out, g_Q, g_WQ,
-                                              g_WK, g_WV, s->mu, grads ? grads->feat : nullptr,
-                                              grads ? grads->mu : nullptr, workspace,
-                                              reinterpret_cast<cudaStream_t>(stream), &why);
+    cudaError_t e = psi::launch_attention_bwd(*s, fv.data, fv.dim, Q, n_q, W_Q, W_K, W_V, d, g_out, g_Q, g_WQ, g_WK,
+                                              g_WV, grads ? grads->feat : nullptr, grads ? grads->mu : nullptr,
+                                              workspace, ctx->status, reinterpret_cast<cudaStream_t>(stream), &why);
     if (why) return fail(ctx, PSI_ERR_CUDA, "psi_frustum_attention_bwd: %s", why);
     return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_frustum_attention_bwd", e);
 }

@@ -238,14 +238,13 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
                               DevStatus *status, cudaStream_t st, cudaEvent_t const (*time_ev)[2], int shape);
 
 size_t attention_workspace_bytes(int64_t n, int C, int d, int n_q);
-cudaError_t launch_attention(void *cublas, const psi_surfels &s, const void *feat, const float *fscale, int dtype, int C,
-                             const psi_camera &cam, float z_near, const float *Q, int n_q, const float *WQ,
-                             const float *WK, const float *WV, int d, float *out, void *ws, cudaStream_t st,
-                             const char **why);
-cudaError_t launch_attention_bwd(void *cublas, int64_t N, int C, int n_q, const float *Q, const float *WQ,
-                                 const float *WK, const float *WV, int d, const float *G, float *gQ, float *gWQ,
-                                 float *gWK, float *gWV, const float *mu, float *g_feat, float *g_mu, void *ws,
-                                 cudaStream_t st, const char **why);
+cudaError_t launch_attention(const psi_surfels &s, const void *feat, int C, const psi_camera &cam, float z_near,
+                             const float *Q, int n_q, const float *WQ, const float *WK, const float *WV, int d,
+                             float *out, void *ws, DevStatus *status, cudaStream_t st, const char **why);
+cudaError_t launch_attention_bwd(const psi_surfels &s, const void *feat, int C, const float *Q, int n_q,
+                                 const float *WQ, const float *WK, const float *WV, int d, const float *G_out,
+                                 float *gQ, float *gWQ, float *gWK, float *gWV, float *g_feat, float *g_mu, void *ws,
+                                 DevStatus *status, cudaStream_t st, const char **why);
 cudaError_t launch_quantize(const float *f, int64_t n, int dim, int dtype, void *q, float *scale, cudaStream_t st);
 cudaError_t launch_frames(const float *q, int64_t n, float *tu, float *tv, cudaStream_t st);
 cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,

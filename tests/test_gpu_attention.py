@@ -1,4 +1,16 @@
-"""Frustum-constrained cross-attention (Sec. 4.1) against the oracle (needs a GPU)."""
+"""Frustum-constrained cross-attention (Sec. 4.1) on the tensor cores against the
+oracle (needs a GPU).
+
+The kernels round the folded queries qh = (Q W_Q) W_K^T / sqrt(d), the
+positional encoding and the softmax weights to BF16 (unit roundoff 2^-9) and
+accumulate in FP32; the feature table itself is stored in BF16 and the oracle
+is fed those stored values. A score e = qh . K then carries an error of a few
+2^-9 |qh||K|, a weight a relative error of the same order, and an output --
+a convex combination of feature rows times W_V -- an error of about 2^-9 times
+its scale. The bar is 1e-2 of the largest output (five units of 2^-9 and
+margin), and 5e-3 in relative L2 over all outputs; gradients 2e-2 relative L2
+per tensor. Closed forms hold tighter: W_K = 0 gives the mean value over the
+active set (weights exactly 1), to FP32 rounding."""
 import numpy as np
 import pytest
 
@@ -9,6 +21,10 @@ from paper_2604_10982_gb300 import scenegen as sg
 
 pytestmark = pytest.mark.gpu
 
+BAR_MAX = 1e-2
+BAR_L2 = 5e-3
+BAR_GRAD = 2e-2
+
 
 @pytest.fixture(scope="module")
 def ctx():
@@ -18,44 +34,56 @@ def ctx():
     return psi.Context(0)
 
 
-def _run(ctx, w, cam, dtype, nq, d, seed=1):
-    from paper_2604_10982_gb300 import pipeline as pl, psi
-    C = w.features.shape[1]
+def _weights(C, d, nq, seed):
     rng = np.random.default_rng(seed)
     W = [(rng.normal(size=(C, d)) / np.sqrt(C)).astype(np.float32) for _ in range(3)]
     Q = rng.normal(size=(nq, C)).astype(np.float32)
-    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=dtype)
+    return W, Q
+
+
+def _run(ctx, w, cam, nq, d, seed=1, W=None, Q=None):
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    C = w.features.shape[1]
+    if W is None:
+        W, Q = _weights(C, d, nq, seed)
+    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.BF16)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out = torch.empty(nq, d, device="cuda")
     ws = torch.empty(psi.attention_workspace_size(scene.n, C, d, nq), dtype=torch.uint8, device="cuda")
-    camarr = psi.cameras([cam])
-    psi.psi_frustum_attention(ctx, scene.surfels_struct(), scene.features_struct(), camarr[0], 0.2, dev(Q), nq,
-                              dev(W[0]), dev(W[1]), dev(W[2]), d, out, ws)
+    psi.psi_frustum_attention(ctx, scene.surfels_struct(), scene.features_struct(), psi.cameras([cam])[0], 0.2,
+                              dev(Q), nq, dev(W[0]), dev(W[1]), dev(W[2]), d, out, ws)
     torch.cuda.synchronize()
     assert ctx.status_fetch()[0] == 0
-    feat = pl.dequantize(scene.q, scene.qscale, dtype) if dtype != psi.F32 else w.features.astype(np.float64)
+    feat = pl.dequantize(scene.q, None, psi.BF16)
     ref, act, margin = orc.frustum_attention(w.surfels, feat, cam, 0.2, Q.astype(np.float64), *W)
     return out.cpu().numpy().astype(np.float64), ref, act, margin
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_attention_matches_oracle(ctx, dtype):
-    from paper_2604_10982_gb300 import psi
-    w = sg.dense_box(n=5000, d=64)
+def _check(got, ref):
+    scale = max(1e-3, np.abs(ref).max())
+    err = np.abs(got - ref).max() / scale
+    l2 = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert err <= BAR_MAX and l2 <= BAR_L2, (err, l2)
+    return err, l2
+
+
+@pytest.mark.parametrize("C", [64, 128])
+def test_attention_matches_oracle(ctx, C):
+    w = sg.dense_box(n=5000, d=C)
     cam = w.cameras[0]
-    got, ref, act, margin = _run(ctx, w, cam, psi.F32 if dtype == "f32" else psi.BF16, 7, 32)
+    got, ref, act, margin = _run(ctx, w, cam, 7, 32)
     # the float32 frustum test agrees with the FP64 one away from the planes
     assert np.min(np.abs(margin)) > 1e-4, "a surfel sits on a frustum plane: pick another seed"
     assert 0 < act.sum() < len(act)
-    assert np.abs(got - ref).max() <= 2e-4 * max(1.0, np.abs(ref).max())
+    print("box C=%d" % C, _check(got, ref))
 
 
 def test_attention_street_view(ctx):
-    """200k surfels of the street, one 720p view: most surfels outside the
-    frustum. Surfels within 1e-4 m of a frustum plane (where float32 and FP64
-    may decide differently) are left out of the input, by the oracle's margin."""
+    """200k surfels of the street, one 720p view, 100 queries: many tiles per
+    CTA, most surfels outside the frustum. Surfels within 1e-4 m of a frustum
+    plane (where float32 and FP64 may decide differently) are left out of the
+    input, by the oracle's margin."""
     import dataclasses
-    from paper_2604_10982_gb300 import psi
     w = sg.street()
     cam = w.cameras[0]
     _, margin = orc.frustum_active(w.surfels, cam, 0.2)
@@ -63,21 +91,58 @@ def test_attention_street_view(ctx):
     s = sg.Surfels(*(np.ascontiguousarray(np.asarray(getattr(w.surfels, k))[keep])
                      for k in ("mu", "tu", "tv", "scale", "opacity", "rgb")))
     w2 = dataclasses.replace(w, surfels=s, features=np.ascontiguousarray(w.features[keep]))
-    got, ref, act, _ = _run(ctx, w2, cam, psi.F32, 100, 64)
+    got, ref, act, _ = _run(ctx, w2, cam, 100, 64)
     assert act.mean() < 0.9 and keep.mean() > 0.999
-    assert np.abs(got - ref).max() <= 5e-4 * max(1.0, np.abs(ref).max())
+    print("street", _check(got, ref))
 
 
-def test_attention_gradients_match_oracle(ctx):
-    from paper_2604_10982_gb300 import pipeline as pl, psi
-    w = sg.dense_box(n=4000, d=32)
+def test_attention_zero_wk_is_mean_of_active_values(ctx):
+    """W_K = 0: every active surfel gets the same score, so Q' is the mean of
+    V_j W_V over the active set (ragged surfel count, 3 tiles short of full)."""
+    w = sg.dense_box(n=5000 - 3 * 128 + 17, d=64)
     cam = w.cameras[0]
-    C, d, nq = 32, 16, 6
-    rng = np.random.default_rng(3)
-    W = [(rng.normal(size=(C, d)) / np.sqrt(C)).astype(np.float32) for _ in range(3)]
-    Q = rng.normal(size=(nq, C)).astype(np.float32)
-    G = rng.normal(size=(nq, d)).astype(np.float32)
-    scene = pl.DeviceScene(w.surfels, w.features)
+    C, d, nq = 64, 24, 5
+    W, Q = _weights(C, d, nq, 4)
+    W[1] = np.zeros_like(W[1])
+    got, ref, act, _ = _run(ctx, w, cam, nq, d, W=W, Q=Q)
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.BF16)
+    feat = pl.dequantize(scene.q, None, psi.BF16)
+    mean = feat[act].mean(0) @ W[2].astype(np.float64)
+    assert np.abs(ref - mean[None]).max() < 1e-9
+    assert np.abs(got - mean[None]).max() <= 1e-5 * max(1.0, np.abs(mean).max())
+
+
+def test_attention_empty_active_set_gives_zero(ctx):
+    """A camera looking away from every surfel: no active surfel, Q' = 0."""
+    w = sg.dense_box(n=3000, d=64)
+    cam = sg.look_camera((0.0, -6.0, 1.5), np.pi, 128, 128, 110.0)
+    got, ref, act, _ = _run(ctx, w, cam, 4, 16)
+    assert act.sum() == 0 and np.all(ref == 0)
+    assert np.all(got == 0)
+
+
+def test_attention_rejects_other_tables(ctx):
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    w = sg.dense_box(n=500, d=64)
+    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.F32)
+    ws = torch.empty(psi.attention_workspace_size(500, 64, 8, 2), dtype=torch.uint8, device="cuda")
+    z = torch.zeros(64, 8, device="cuda")
+    with pytest.raises(psi.PsiError):
+        psi.psi_frustum_attention(ctx, scene.surfels_struct(), scene.features_struct(), psi.cameras([w.cameras[0]])[0],
+                                  0.2, torch.zeros(2, 64, device="cuda"), 2, z, z, z, 8, torch.empty(2, 8, device="cuda"),
+                                  ws)
+
+
+@pytest.mark.parametrize("C", [64, 128])
+def test_attention_gradients_match_oracle(ctx, C):
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    w = sg.dense_box(n=4000, d=C)
+    cam = w.cameras[0]
+    d, nq = 16, 6
+    W, Q = _weights(C, d, nq, 3)
+    G = np.random.default_rng(5).normal(size=(nq, d)).astype(np.float32)
+    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.BF16)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out = torch.empty(nq, d, device="cuda")
     ws = torch.empty(psi.attention_workspace_size(scene.n, C, d, nq), dtype=torch.uint8, device="cuda")
@@ -94,8 +159,12 @@ def test_attention_gradients_match_oracle(ctx):
     assert ctx.status_fetch()[0] == 0
     _, margin = orc.frustum_active(w.surfels, cam, 0.2)
     assert np.min(np.abs(margin)) > 1e-4
-    ref = orc.frustum_attention_grad(w.surfels, w.features.astype(np.float64), cam, 0.2, Q, *W, G)
+    feat = pl.dequantize(scene.q, None, psi.BF16)
+    ref = orc.frustum_attention_grad(w.surfels, feat, cam, 0.2, Q, *W, G)
+    rep = {}
     for key, got in (("Q", gQ), ("WQ", gWQ), ("WK", gWK), ("WV", gWV), ("feat", gfeat), ("mu", gmu)):
         g = got.cpu().numpy().astype(np.float64)
         r = ref[key]
-        assert np.linalg.norm(g - r) <= 1e-4 * max(np.linalg.norm(r), 1e-12), key
+        rep[key] = np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-12)
+    print("grad C=%d" % C, rep)
+    assert all(v <= BAR_GRAD for v in rep.values()), rep
