@@ -488,6 +488,8 @@ def frustum_attention(s, feat, cam, z_near, Q, WQ, WK, WV, plant: int = 0):
     f = np.asarray(feat, np.float64)
     active, margin = frustum_active(s, cam, z_near)
     C = f.shape[1]
+    if not active.any():  # reading: an empty active set attends to nothing, Q' = 0
+        return np.zeros((np.asarray(Q).shape[0], np.asarray(WV).shape[1])), active, margin
     K = f + attn_pos_enc(s.mu, C)
     q = np.asarray(Q, np.float64) @ np.asarray(WQ, np.float64)
     k = K[active] @ np.asarray(WK, np.float64)
@@ -516,6 +518,9 @@ def frustum_attention_grad(s, feat, cam, z_near, Q, WQ, WK, WV, G):
     active, _ = frustum_active(s, cam, z_near)
     C = f.shape[1]
     mu = np.asarray(s.mu, np.float64)
+    if not active.any():  # Q' = 0 identically: every gradient vanishes
+        return {"Q": np.zeros_like(Q), "WQ": np.zeros_like(WQ), "WK": np.zeros_like(WK), "WV": np.zeros_like(WV),
+                "feat": np.zeros_like(f), "mu": np.zeros_like(mu)}
     K = f + attn_pos_enc(mu, C)
     Ka, Va = K[active], f[active]
     q, k, v = Q @ WQ, Ka @ WK, Va @ WV

@@ -13,9 +13,12 @@
 // clamped): dL/do = dL/dalpha G, and (u, v) enter via a = dL/dalpha * alpha:
 // with (u, v, 1) ~ M^-1 p the gradient of M is M^-T W, W = sum a (u, v,
 // -d^2)(u, v, 1)^T, so each (pixel, record) adds 7 moments of (u, v).
-// Per-surfel sums are reduced across the warp (a transposing butterfly: 11
-// values in 13 shuffles) and added with one atomic per value per warp; the
-// feature gradient is accumulated warp-cooperatively across channels.
+// Per-record sums (colour, dL/do, moments) go to a per-record slot array:
+// when at most four lanes of the warp contribute, each adds its 11 values with
+// three 16-byte vector reductions; otherwise they are reduced across the warp
+// (a transposing butterfly: 11 values in 13 shuffles) and added with one
+// atomic per value per warp. The feature gradient is accumulated
+// warp-cooperatively across channels.
 // With the 2DGS low-pass filter, a pixel where the screen-space term
 // rho = 2 |x - p0|^2 wins adds dL/dp0 = 2 a (x - p0) (a = dL/dalpha * alpha)
 // instead of the (u, v) moments: 13 sums (16-slot butterfly, 16 shuffles)
@@ -34,9 +37,10 @@ namespace {
 
 using namespace raster;
 
-// per record: dL/do, Suu, Suv, Svv, Su, Sv, Sdu, Sdv; with the low-pass filter
-// also dL/dp0x, dL/dp0y and two padding floats
-__host__ __device__ constexpr int moments_per_record(bool lp) { return lp ? 12 : 8; }
+// per record: dL/dc (3), dL/do, Suu, Suv, Svv, Su, Sv, Sdu, Sdv, padding; with
+// the low-pass filter also dL/dp0x, dL/dp0y and three padding floats -- whole
+// float4s, so that a pixel can add its share with 16-byte vector reductions
+__host__ __device__ constexpr int moments_per_record(bool lp) { return lp ? 16 : 12; }
 
 struct BwdArgs {
     const float4 *records;
@@ -49,7 +53,6 @@ struct BwdArgs {
     const float *g_rgb; // [3][P_total]
     const float *g_F;   // [P_total, D] or NULL
     const float *g_T;   // [P_total] or NULL
-    float *g_col;       // [N,3] or NULL
     float *g_feat;      // [N,D] or NULL
     float *moments;     // [R, moments_per_record]
     DevStatus *status;
@@ -134,9 +137,9 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
     return v[0];
 }
 
-// Up to this many contributing lanes add their values with their own atomics
-// instead of reducing over the warp first.
-constexpr int kDirectLanes = 1;
+// Up to this many contributing lanes add their values with their own 16-byte
+// vector reductions (3 or 4 per lane) instead of reducing over the warp first.
+constexpr int kDirectLanes = 4;
 
 // SAVED: T_final, last and the Top-K ids come from the forward's outputs;
 // otherwise pass A recomputes them. With SAVED and K > 0 the feature terms
@@ -410,17 +413,14 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
                         }
                     }
                     if (__popc(amask) <= kDirectLanes) {
-                        // few contributing lanes add their values directly
+                        // few contributing lanes add their values directly, a
+                        // float4 at a time (the record's slots are 16-byte aligned)
                         if (act) {
+                            float4 *dst = reinterpret_cast<float4 *>(a.moments + static_cast<int64_t>(rid) * kM);
 #pragma unroll
-                            for (int k2 = 0; k2 < kSums; ++k2) {
-                                if (vals[k2] == 0.0f) continue;
-                                if (k2 < 3) {
-                                    if (a.g_col) atomicAdd(a.g_col + 3 * sid + k2, vals[k2]);
-                                } else {
-                                    atomicAdd(a.moments + static_cast<int64_t>(rid) * kM + (k2 - 3), vals[k2]);
-                                }
-                            }
+                            for (int k4 = 0; k4 < kM / 4; ++k4)
+                                atomicAdd(dst + k4, make_float4(vals[4 * k4], vals[4 * k4 + 1], vals[4 * k4 + 2],
+                                                                vals[4 * k4 + 3]));
                         }
                     } else {
                         float tot;
@@ -436,13 +436,7 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
                             idx = ((lane >> 4) & 1) * 6 + ((lane >> 3) & 1) * 3 + g;
                             mine = (lane & 1) == 0 && g < 3;
                         }
-                        if (mine && tot != 0.0f) {
-                            if (idx < 3) {
-                                if (a.g_col) atomicAdd(a.g_col + 3 * sid + idx, tot);
-                            } else {
-                                atomicAdd(a.moments + static_cast<int64_t>(rid) * kM + (idx - 3), tot);
-                            }
-                        }
+                        if (mine && tot != 0.0f) atomicAdd(a.moments + static_cast<int64_t>(rid) * kM + idx, tot);
                     }
                     if (want_feat) {
                         uint32_t selmask = __ballot_sync(0xffffffffu, act && sel);
@@ -510,17 +504,23 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= total) return;
     constexpr int kV = moments_per_record(LP) / 4;
-    const float4 m0 = moments[kV * r], m1 = moments[kV * r + 1];
-    const float2 gp = LP ? make_float2(moments[kV * r + 2].x, moments[kV * r + 2].y) : make_float2(0.0f, 0.0f);
-    if (m0.x == 0.0f && m0.y == 0.0f && m0.z == 0.0f && m0.w == 0.0f && m1.x == 0.0f && m1.y == 0.0f &&
-        m1.z == 0.0f && m1.w == 0.0f && gp.x == 0.0f && gp.y == 0.0f)
+    // slots: dL/dc (3), dL/do, Suu, Suv, Svv, Su, Sv, Sdu, Sdv, pad[, dL/dp0 (2), pad (3)]
+    const float4 q0 = moments[kV * r], q1 = moments[kV * r + 1], q2 = moments[kV * r + 2];
+    const float2 gp = LP ? make_float2(moments[kV * r + 2].w, moments[kV * r + 3].x) : make_float2(0.0f, 0.0f);
+    if (q0.x == 0.0f && q0.y == 0.0f && q0.z == 0.0f && q0.w == 0.0f && q1.x == 0.0f && q1.y == 0.0f &&
+        q1.z == 0.0f && q1.w == 0.0f && q2.x == 0.0f && q2.y == 0.0f && q2.z == 0.0f && gp.x == 0.0f && gp.y == 0.0f)
         return;
     const int v = static_cast<int>(r / fp.n);
     const int64_t i = r - static_cast<int64_t>(v) * fp.n;
     const ViewParams &cam = fp.v[v];
     const float *R = cam.R;
-    if (g.opacity) atomicAdd(g.opacity + i, m0.x);
-    const float Suu = m0.y, Suv = m0.z, Svv = m0.w, Su = m1.x, Sv = m1.y, Sdu = m1.z, Sdv = m1.w;
+    if (g.rgb) {
+        if (q0.x != 0.0f) atomicAdd(g.rgb + 3 * i, q0.x);
+        if (q0.y != 0.0f) atomicAdd(g.rgb + 3 * i + 1, q0.y);
+        if (q0.z != 0.0f) atomicAdd(g.rgb + 3 * i + 2, q0.z);
+    }
+    if (g.opacity) atomicAdd(g.opacity + i, q0.w);
+    const float Suu = q1.x, Suv = q1.y, Svv = q1.z, Su = q1.w, Sv = q2.x, Sdu = q2.y, Sdv = q2.z;
 
     float mu[3], tu[3], tv[3];
     for (int k = 0; k < 3; ++k) {
@@ -696,7 +696,6 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
     a.g_rgb = g_rgb;
     a.g_F = f.data ? g_F : nullptr;
     a.g_T = g_T;
-    a.g_col = g.rgb;
     a.g_feat = f.data ? g.feat : nullptr;
     a.moments = static_cast<float *>(ws);
     a.status = status;

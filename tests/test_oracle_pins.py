@@ -474,3 +474,17 @@ def test_geometry_gradient_central_differences():
 def test_geometry_planted_mistakes_are_caught():
     assert _geometry_closed_forms(plant=1) > 0.5        # no turn toward the camera
     assert _geometry_fd_error(plant=2) > 1e-3           # normalisation's projection dropped
+
+
+def test_attention_empty_active_set_is_zero():
+    """Reading: with no surfel in the frustum nothing is attended, Q' = 0, and
+    every gradient vanishes."""
+    w = sg.dense_box(n=300, d=16)
+    cam = sg.look_camera((0.0, -6.0, 1.5), np.pi, 64, 64, 55.0)
+    rng = np.random.default_rng(0)
+    W = [rng.normal(size=(16, 4)) for _ in range(3)]
+    Q, G = rng.normal(size=(3, 16)), rng.normal(size=(3, 4))
+    out, act, _ = orc.frustum_attention(w.surfels, w.features, cam, 0.2, Q, *W)
+    assert act.sum() == 0 and out.shape == (3, 4) and np.all(out == 0)
+    g = orc.frustum_attention_grad(w.surfels, w.features, cam, 0.2, Q, *W, G)
+    assert all(np.all(v == 0) for v in g.values())
