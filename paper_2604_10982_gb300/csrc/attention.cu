@@ -19,7 +19,9 @@
 // per SM walks a contiguous range of tiles:
 //   warp 0     TMA: the resident qh tile, then the feature tiles (2-stage ring)
 //   warp 1     TMEM allocation; one thread issues the MMAs
-//   warps 2-3  per tile: the frustum mask and the psi tile (BF16, 2 stages)
+//   warps 2, 3, 8, 9  per tile, one surfel per thread: the frustum mask and
+//              the psi row (BF16, 2 stages), one sin/cos pair per (axis,
+//              frequency)
 //   warps 4-7  one query row per thread: online softmax of S (double-buffered
 //              in TMEM), P written to shared memory as the A operand of the
 //              P f product, the O accumulator rescaled in TMEM when the row
@@ -48,7 +50,7 @@ constexpr float kChi2_99 = 9.21034037198f; // -2 ln 0.01
 constexpr float kLnB = 9.21034037198f;     // ln 10000
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kAT = 128;         // surfels per tile
-constexpr int kAThreads = 256;   // 8 warps
+constexpr int kAThreads = 320;   // 10 warps: TMA, MMA, 4 softmax, 4 psi (warps 2, 3, 8, 9)
 constexpr uint32_t kAtom = 128u * 128u; // bytes of one 128-row x 128-byte swizzle atom column
 
 struct AttnCam {
@@ -99,16 +101,35 @@ __device__ __forceinline__ float ex2f(float x)
     return y;
 }
 
-// psi channel values c0..c0+7 of one centre; w: frequency per k
-__device__ __forceinline__ void psi8(const float m[3], int c0, const float *w, float v[8])
+// psi row of one centre as a row of a swizzled BF16 tile: channels 6k..6k+5
+// are sin(m_x w_k), sin(m_y w_k), sin(m_z w_k), cos(m_x w_k), cos(m_y w_k),
+// cos(m_z w_k) (t = c / 3, axis = c mod 3, k = t / 2), one sin/cos pair per
+// (axis, k); w: frequency per k
+template <int C>
+__device__ __forceinline__ void psi_row(uint32_t tile, int row, float mx, float my, float mz, const float *w)
 {
+    float v[C];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int c = c0 + e, t = c / 3, axis = c - 3 * t;
-        const float arg = m[axis] * w[t >> 1];
-        v[e] = (t & 1) ? __cosf(arg) : __sinf(arg);
+    for (int k = 0; 6 * k < C; ++k) {
+        float sn[3], cs[3];
+        __sincosf(mx * w[k], &sn[0], &cs[0]);
+        __sincosf(my * w[k], &sn[1], &cs[1]);
+        __sincosf(mz * w[k], &sn[2], &cs[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (6 * k + a < C) v[6 * k + a] = sn[a];
+            if (6 * k + 3 + a < C) v[6 * k + 3 + a] = cs[a];
+        }
     }
+#pragma unroll
+    for (int ch = 0; ch < C / 8; ++ch)
+        st_shared_v4(tile + tile_off(row, ch), pack_bf16(v[8 * ch], v[8 * ch + 1]), pack_bf16(v[8 * ch + 2], v[8 * ch + 3]),
+                     pack_bf16(v[8 * ch + 4], v[8 * ch + 5]), pack_bf16(v[8 * ch + 6], v[8 * ch + 7]));
 }
+
+// the transform warps (2, 3, 8, 9) -> index 0..3 (the 32-row group of the tile they handle)
+__device__ __forceinline__ int psi_warp_index(int wid) { return wid < 4 ? wid - 2 : wid - 6; }
+__device__ __forceinline__ bool is_psi_warp(int wid) { return wid == 2 || wid == 3 || wid == 8 || wid == 9; }
 
 // Shared-memory matrix descriptor for an MN-major operand in the 128-byte
 // swizzle layout: 64-element (128-byte) rows along MN, 8 rows along K per
@@ -219,12 +240,12 @@ __global__ void __launch_bounds__(kAThreads, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&f_full[i], 1);
             mbar_init(&f_empty[i], 1);
-            mbar_init(&psi_full[i], 2);
+            mbar_init(&psi_full[i], 4);
             mbar_init(&psi_empty[i], 1);
             mbar_init(&s_full[i], 1);
             mbar_init(&s_empty[i], 4);
         }
-        for (int i = 0; i < 4; ++i) mbar_init(&m_full[i], 2);
+        for (int i = 0; i < 4; ++i) mbar_init(&m_full[i], 4);
         mbar_init(&o_full, 1);
         mbar_init(&p_full, 4);
         mbar_init(&q_bar, 1);
@@ -309,41 +330,22 @@ __global__ void __launch_bounds__(kAThreads, 1)
             mma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0, st, kSiteDrain);
         }
-    } else if (wid < 4) {
-        // ---------------- frustum mask and psi tiles
-        const int tt = tid - 64; // 0..63: rows tt and tt + 64
+    } else if (is_psi_warp(wid)) {
+        // ---------------- frustum mask and psi tiles, one surfel per thread
+        const int gq = psi_warp_index(wid), row = gq * 32 + lane;
         for (int t = 0; t < nt; ++t) {
             const int b = t & 1;
             if (t >= 2 && !await_warp(&psi_empty[b], ((t >> 1) - 1) & 1, st, kSiteDecodeMma, &abort_flag)) break;
-            float m[2][3];
-            bool act[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t j = static_cast<int64_t>(t0 + t) * kAT + tt + 64 * h;
-                const bool valid = j < p.n;
-                m[h][0] = valid ? p.mu[3 * j] : 0.f;
-                m[h][1] = valid ? p.mu[3 * j + 1] : 0.f;
-                m[h][2] = valid ? p.mu[3 * j + 2] : 0.f;
-                act[h] = valid && frustum_active(cam_s, m[h][0], m[h][1], m[h][2], p.scale[2 * j], p.scale[2 * j + 1]);
-            }
-            const uint32_t w0 = __ballot_sync(0xffffffffu, act[0]), w1 = __ballot_sync(0xffffffffu, act[1]);
-            if (lane == 0) {
-                mask[t & 3][wid - 2] = w0;     // rows 0..31 / 32..63
-                mask[t & 3][wid - 2 + 2] = w1; // rows 64..95 / 96..127
-            }
+            const int64_t j = static_cast<int64_t>(t0 + t) * kAT + row;
+            const bool valid = j < p.n;
+            const float mx = valid ? p.mu[3 * j] : 0.f, my = valid ? p.mu[3 * j + 1] : 0.f;
+            const float mz = valid ? p.mu[3 * j + 2] : 0.f;
+            const bool act = valid && frustum_active(cam_s, mx, my, mz, p.scale[2 * j], p.scale[2 * j + 1]);
+            const uint32_t word = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) mask[t & 3][gq] = word;
             __syncwarp();
             if (lane == 0) mbar_arrive(&m_full[t & 3]);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = tt + 64 * h;
-#pragma unroll 1
-                for (int ch = 0; ch < C / 8; ++ch) {
-                    float v[8];
-                    psi8(m[h], ch * 8, wk, v);
-                    st_shared_v4(sb + L::PSI + b * L::TILE + tile_off(row, ch), pack_bf16(v[0], v[1]),
-                                 pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-                }
-            }
+            psi_row<C>(sb + L::PSI + b * L::TILE, row, mx, my, mz, wk);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&psi_full[b]);
@@ -364,20 +366,18 @@ __global__ void __launch_bounds__(kAThreads, 1)
 #pragma unroll
             for (int k = 0; k < 4; ++k) mw[k] = mask[t & 3][k];
             tc_fence_after();
-            uint32_t s[kAT];
-#pragma unroll
-            for (int c0 = 0; c0 < kAT; c0 += 16) tmem_ld16_async(tmem + lane_bits + b * kAT + c0, s + c0);
-            tmem_wait_ld();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s_empty[b]);
-            // scores in log2 units; inactive surfels excluded
+            // pass 1 over the row: the maximum of the active scores (log2 units)
             float mt = -__int_as_float(0x7f800000);
+#pragma unroll 1
+            for (int c0 = 0; c0 < kAT; c0 += 32) {
+                uint32_t s[32];
+                tmem_ld16_async(tmem + lane_bits + b * kAT + c0, s);
+                tmem_ld16_async(tmem + lane_bits + b * kAT + c0 + 16, s + 16);
+                tmem_wait_ld();
+                const uint32_t mword = mw[c0 >> 5];
 #pragma unroll
-            for (int j = 0; j < kAT; ++j) {
-                const float x = __uint_as_float(s[j]) * kLog2e;
-                s[j] = __float_as_uint(x);
-                if ((mw[j >> 5] >> (j & 31)) & 1u) mt = fmaxf(mt, x);
+                for (int jj = 0; jj < 32; ++jj)
+                    if ((mword >> jj) & 1u) mt = fmaxf(mt, __uint_as_float(s[jj]) * kLog2e);
             }
             const float m_new = fmaxf(m_run, mt);
             // P f of the previous tile has landed: the P buffer is free, O may be rescaled
@@ -386,14 +386,14 @@ __global__ void __launch_bounds__(kAThreads, 1)
                 if (!ok) break;
                 tc_fence_after();
                 if (__any_sync(0xffffffffu, m_new > m_run)) {
-                    const float alpha = (m_new > m_run) ? ex2f(m_run - m_new) : 1.0f;
+                    const float scale_o = (m_new > m_run) ? ex2f(m_run - m_new) : 1.0f;
 #pragma unroll 1
                     for (int c0 = 0; c0 < C; c0 += 16) {
                         uint32_t o[16];
                         tmem_ld16_async(tmem + lane_bits + 256 + c0, o);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) o[e] = __float_as_uint(__uint_as_float(o[e]) * alpha);
+                        for (int e = 0; e < 16; ++e) o[e] = __float_as_uint(__uint_as_float(o[e]) * scale_o);
                         tmem_st16(tmem + lane_bits + 256 + c0, o);
                     }
                     tmem_wait_st();
@@ -401,22 +401,33 @@ __global__ void __launch_bounds__(kAThreads, 1)
             }
             const float alpha = (m_new > m_run) ? ex2f(m_run - m_new) : 1.0f;
             const bool any = m_new > -__int_as_float(0x7f800000);
+            // pass 2: the weights, rounded to BF16 as the A operand of P f
             float psum = 0.0f;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kAT; c0 += 32) {
+                uint32_t s[32];
+                tmem_ld16_async(tmem + lane_bits + b * kAT + c0, s);
+                tmem_ld16_async(tmem + lane_bits + b * kAT + c0 + 16, s + 16);
+                tmem_wait_ld();
+                const uint32_t mword = any ? mw[c0 >> 5] : 0u;
 #pragma unroll
-            for (int ch = 0; ch < kAT / 8; ++ch) {
-                uint32_t w[4];
+                for (int ch = 0; ch < 4; ++ch) {
+                    uint32_t w[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int j0 = ch * 8 + 2 * e, j1 = j0 + 1;
-                    const bool a0 = (mw[j0 >> 5] >> (j0 & 31)) & 1u, a1 = (mw[j1 >> 5] >> (j1 & 31)) & 1u;
-                    const float p0 = (a0 && any) ? ex2f(__uint_as_float(s[j0]) - m_new) : 0.0f;
-                    const float p1 = (a1 && any) ? ex2f(__uint_as_float(s[j1]) - m_new) : 0.0f;
-                    w[e] = pack_bf16(p0, p1);
-                    // the sum of the values the tensor cores see
-                    psum += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xFFFF0000u);
+                    for (int e = 0; e < 4; ++e) {
+                        const int j0 = ch * 8 + 2 * e, j1 = j0 + 1;
+                        const float p0 = ((mword >> j0) & 1u) ? ex2f(__uint_as_float(s[j0]) * kLog2e - m_new) : 0.0f;
+                        const float p1 = ((mword >> j1) & 1u) ? ex2f(__uint_as_float(s[j1]) * kLog2e - m_new) : 0.0f;
+                        w[e] = pack_bf16(p0, p1);
+                        // the sum of the values the tensor cores see
+                        psum += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xFFFF0000u);
+                    }
+                    st_shared_v4(sb + L::P + tile_off(row, (c0 >> 3) + ch), w[0], w[1], w[2], w[3]);
                 }
-                st_shared_v4(sb + L::P + tile_off(row, ch), w[0], w[1], w[2], w[3]);
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_empty[b]);
             l_run = l_run * alpha + psum;
             m_run = m_new;
             fence_proxy_async_smem();
@@ -499,13 +510,13 @@ __global__ void __launch_bounds__(kAThreads, 1)
             mbar_init(&f_full[i], 1);
             mbar_init(&f_empty[i], 1);
         }
-        mbar_init(&psi_full, 2);
+        mbar_init(&psi_full, 4);
         mbar_init(&psi_empty, 1);
         mbar_init(&s_full, 1);
         mbar_init(&pe_full, 4);
         mbar_init(&x_full, 1);
         mbar_init(&x_empty, 4);
-        for (int i = 0; i < 4; ++i) mbar_init(&m_full[i], 2);
+        for (int i = 0; i < 4; ++i) mbar_init(&m_full[i], 4);
         mbar_init(&q_bar, 1);
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
@@ -603,40 +614,21 @@ __global__ void __launch_bounds__(kAThreads, 1)
             mma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0, st, kSiteDrain);
         }
-    } else if (wid < 4) {
-        // ---------------- frustum mask and psi tile
-        const int tt = tid - 64;
+    } else if (is_psi_warp(wid)) {
+        // ---------------- frustum mask and psi tile, one surfel per thread
+        const int gq = psi_warp_index(wid), row = gq * 32 + lane;
         for (int t = 0; t < nt; ++t) {
             if (t >= 1 && !await_warp(&psi_empty, (t - 1) & 1, st, kSiteDecodeMma, &abort_flag)) break;
-            float m[2][3];
-            bool act[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t j = static_cast<int64_t>(t0 + t) * kAT + tt + 64 * h;
-                const bool valid = j < p.n;
-                m[h][0] = valid ? p.mu[3 * j] : 0.f;
-                m[h][1] = valid ? p.mu[3 * j + 1] : 0.f;
-                m[h][2] = valid ? p.mu[3 * j + 2] : 0.f;
-                act[h] = valid && frustum_active(cam_s, m[h][0], m[h][1], m[h][2], p.scale[2 * j], p.scale[2 * j + 1]);
-            }
-            const uint32_t w0 = __ballot_sync(0xffffffffu, act[0]), w1 = __ballot_sync(0xffffffffu, act[1]);
-            if (lane == 0) {
-                mask[t & 3][wid - 2] = w0;
-                mask[t & 3][wid - 2 + 2] = w1;
-            }
+            const int64_t j = static_cast<int64_t>(t0 + t) * kAT + row;
+            const bool valid = j < p.n;
+            const float mx = valid ? p.mu[3 * j] : 0.f, my = valid ? p.mu[3 * j + 1] : 0.f;
+            const float mz = valid ? p.mu[3 * j + 2] : 0.f;
+            const bool act = valid && frustum_active(cam_s, mx, my, mz, p.scale[2 * j], p.scale[2 * j + 1]);
+            const uint32_t word = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) mask[t & 3][gq] = word;
             __syncwarp();
             if (lane == 0) mbar_arrive(&m_full[t & 3]);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = tt + 64 * h;
-#pragma unroll 1
-                for (int ch = 0; ch < C / 8; ++ch) {
-                    float v[8];
-                    psi8(m[h], ch * 8, wk, v);
-                    st_shared_v4(sb + L::PSI + tile_off(row, ch), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
-                                 pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-                }
-            }
+            psi_row<C>(sb + L::PSI, row, mx, my, mz, wk);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&psi_full);
@@ -699,39 +691,46 @@ __global__ void __launch_bounds__(kAThreads, 1)
             tc_fence_after();
             const int64_t j = static_cast<int64_t>(t0 + t) * kAT + row;
             const bool act = (mw[row >> 5] >> (row & 31)) & 1u;
-            float gm[3] = {0.f, 0.f, 0.f};
             float mj[3] = {0.f, 0.f, 0.f};
             if (act) {
                 mj[0] = p.mu[3 * j];
                 mj[1] = p.mu[3 * j + 1];
                 mj[2] = p.mu[3 * j + 2];
             }
-#pragma unroll 1
+            // dK row in registers; dL/dmu_a = sum over k of w_k (dK[6k+a] cos(m_a w_k)
+            // - dK[6k+3+a] sin(m_a w_k)) (the derivative of the psi row)
+            uint32_t dk[C];
+#pragma unroll
+            for (int c0 = 0; c0 < C; c0 += 16) tmem_ld16_async(tmem + lane_bits + c0, dk + c0);
+            tmem_wait_ld();
+            float gm[3] = {0.f, 0.f, 0.f};
+            if (act && p.g_mu) {
+#pragma unroll
+                for (int k = 0; 6 * k < C; ++k) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        float sn, cs;
+                        __sincosf(mj[a] * wk[k], &sn, &cs);
+                        if (6 * k + a < C) gm[a] = fmaf(__uint_as_float(dk[6 * k + a]) * wk[k], cs, gm[a]);
+                        if (6 * k + 3 + a < C) gm[a] = fmaf(-__uint_as_float(dk[6 * k + 3 + a]) * wk[k], sn, gm[a]);
+                    }
+                }
+            }
+#pragma unroll
             for (int c0 = 0; c0 < C; c0 += 16) {
-                uint32_t dk[16], dv[16];
-                tmem_ld16_async(tmem + lane_bits + c0, dk);
+                uint32_t dv[16];
                 tmem_ld16_async(tmem + lane_bits + 128 + c0, dv);
                 tmem_wait_ld();
-                if (act) {
-                    if (p.g_feat) {
-                        float4 *gf = reinterpret_cast<float4 *>(p.g_feat + j * C + c0);
+                if (act && p.g_feat) {
+                    float4 *gf = reinterpret_cast<float4 *>(p.g_feat + j * C + c0);
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            float4 v = gf[e];
-                            v.x += __uint_as_float(dk[4 * e]) + __uint_as_float(dv[4 * e]);
-                            v.y += __uint_as_float(dk[4 * e + 1]) + __uint_as_float(dv[4 * e + 1]);
-                            v.z += __uint_as_float(dk[4 * e + 2]) + __uint_as_float(dv[4 * e + 2]);
-                            v.w += __uint_as_float(dk[4 * e + 3]) + __uint_as_float(dv[4 * e + 3]);
-                            gf[e] = v;
-                        }
-                    }
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int c = c0 + e, tq = c / 3, axis = c - 3 * tq;
-                        const float w = wk[tq >> 1];
-                        const float arg = mj[axis] * w;
-                        const float dpsi = ((tq & 1) ? -__sinf(arg) : __cosf(arg)) * w;
-                        gm[axis] += __uint_as_float(dk[e]) * dpsi;
+                    for (int e = 0; e < 4; ++e) {
+                        float4 v = gf[e];
+                        v.x += __uint_as_float(dk[c0 + 4 * e]) + __uint_as_float(dv[4 * e]);
+                        v.y += __uint_as_float(dk[c0 + 4 * e + 1]) + __uint_as_float(dv[4 * e + 1]);
+                        v.z += __uint_as_float(dk[c0 + 4 * e + 2]) + __uint_as_float(dv[4 * e + 2]);
+                        v.w += __uint_as_float(dk[c0 + 4 * e + 3]) + __uint_as_float(dv[4 * e + 3]);
+                        gf[e] = v;
                     }
                 }
             }
