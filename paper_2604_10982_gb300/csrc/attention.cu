@@ -292,40 +292,67 @@ __global__ void __launch_bounds__(kAThreads, 1)
             const uint32_t idesc_s = idesc_bf16(128, kAT);
             const uint32_t idesc_o = idesc_bf16(128, C) | (1u << 16); // B (the feature tile) MN-major
             bool ok = await(&q_bar, 0, st, kSiteDecodeQ, &abort_flag);
-            auto issue_pv = [&](int u) -> bool {
-                if (!await(&p_full, u & 1, st, kSiteDecodeMma, &abort_flag)) return false;
-                tc_fence_after();
-                const uint32_t fs = sb + L::F + (u & 1) * L::TILE;
+            // issue whichever product is ready: S of the next tile (its feature
+            // and psi tiles landed, its S buffer released) or P f of the oldest
+            // tile whose weights are written; bounded by the wait limit of the
+            // context while nothing is ready
+            int s_next = 0, pv_next = 0;
+            const unsigned long long limit = wait_limit(st);
+            unsigned long long t_idle = 0;
+            while (ok && pv_next < nt) {
+                bool progressed = false;
+                if (s_next < nt) {
+                    const int t = s_next, b = t & 1;
+                    if (mbar_try_wait(&f_full[b], (t >> 1) & 1) && mbar_try_wait(&psi_full[b], (t >> 1) & 1) &&
+                        (t < 2 || mbar_try_wait(&s_empty[b], ((t >> 1) - 1) & 1))) {
+                        tc_fence_after();
+                        const uint32_t d = tmem + b * kAT;
 #pragma unroll 1
-                for (int k = 0; k < kAT / 16; ++k) {
-                    const uint64_t a = sw128_desc(sb + L::P + (k >> 2) * kAtom + (k & 3) * 32);
-                    const uint64_t b = sw128_desc_mn(fs + k * 2048, kAtom, 1024);
-                    mma_bf16(tmem + 256, a, b, idesc_o, (u > 0 || k > 0) ? 1u : 0u);
+                        for (int k = 0; k < C / 16; ++k) {
+                            const uint32_t off = (k >> 2) * kAtom + (k & 3) * 32;
+                            const uint64_t a = sw128_desc(sb + L::Q + off);
+                            mma_bf16(d, a, sw128_desc(sb + L::F + b * L::TILE + off), idesc_s, k > 0 ? 1u : 0u);
+                            mma_bf16(d, a, sw128_desc(sb + L::PSI + b * L::TILE + off), idesc_s, 1u);
+                        }
+                        mma_commit(&s_full[b]);
+                        mma_commit(&psi_empty[b]);
+                        ++s_next;
+                        progressed = true;
+                    }
                 }
-                mma_commit(&o_full);
-                mma_commit(&f_empty[u & 1]);
-                return true;
-            };
-            for (int t = 0; t < nt && ok; ++t) {
-                const int b = t & 1;
-                ok = await(&f_full[b], (t >> 1) & 1, st, kSiteDecodeLoad, &abort_flag) &&
-                     await(&psi_full[b], (t >> 1) & 1, st, kSiteDecodeMma, &abort_flag) &&
-                     (t < 2 || await(&s_empty[b], ((t >> 1) - 1) & 1, st, kSiteDecodeMma, &abort_flag));
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t d = tmem + b * kAT;
+                if (pv_next < s_next && mbar_try_wait(&p_full, pv_next & 1)) {
+                    const int u = pv_next;
+                    tc_fence_after();
+                    const uint32_t fs = sb + L::F + (u & 1) * L::TILE;
 #pragma unroll 1
-                for (int k = 0; k < C / 16; ++k) {
-                    const uint32_t off = (k >> 2) * kAtom + (k & 3) * 32;
-                    const uint64_t a = sw128_desc(sb + L::Q + off);
-                    mma_bf16(d, a, sw128_desc(sb + L::F + b * L::TILE + off), idesc_s, k > 0 ? 1u : 0u);
-                    mma_bf16(d, a, sw128_desc(sb + L::PSI + b * L::TILE + off), idesc_s, 1u);
+                    for (int k = 0; k < kAT / 16; ++k) {
+                        const uint64_t a = sw128_desc(sb + L::P + (k >> 2) * kAtom + (k & 3) * 32);
+                        const uint64_t b = sw128_desc_mn(fs + k * 2048, kAtom, 1024);
+                        mma_bf16(tmem + 256, a, b, idesc_o, (u > 0 || k > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&o_full);
+                    mma_commit(&f_empty[u & 1]);
+                    ++pv_next;
+                    progressed = true;
                 }
-                mma_commit(&s_full[b]);
-                mma_commit(&psi_empty[b]);
-                if (t >= 1) ok = issue_pv(t - 1);
+                if (progressed) {
+                    t_idle = 0;
+                } else if (*reinterpret_cast<volatile int *>(&abort_flag)) {
+                    ok = false;
+                } else {
+                    const unsigned long long now = global_ns();
+                    if (t_idle == 0) {
+                        t_idle = now;
+                    } else if (now - t_idle > limit) {
+                        if (st) {
+                            atomicCAS(&st->wait_site, 0, kSiteDecodeMma);
+                            raise_status(st, PSI_ERR_TIMEOUT);
+                        }
+                        atomicExch(&abort_flag, 1);
+                        ok = false;
+                    }
+                }
             }
-            if (ok) issue_pv(nt - 1);
             // let every issued MMA group complete before TMEM is released
             mma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0, st, kSiteDrain);
@@ -333,14 +360,24 @@ __global__ void __launch_bounds__(kAThreads, 1)
     } else if (is_psi_warp(wid)) {
         // ---------------- frustum mask and psi tiles, one surfel per thread
         const int gq = psi_warp_index(wid), row = gq * 32 + lane;
+        // this thread's centre and scales, loaded one tile ahead
+        auto fetch = [&](int t, float *m5) {
+            const int64_t j = static_cast<int64_t>(t0 + t) * kAT + row;
+            const bool valid = t < nt && j < p.n;
+            m5[0] = valid ? p.mu[3 * j] : 0.f;
+            m5[1] = valid ? p.mu[3 * j + 1] : 0.f;
+            m5[2] = valid ? p.mu[3 * j + 2] : 0.f;
+            m5[3] = valid ? p.scale[2 * j] : -1.f;
+            m5[4] = valid ? p.scale[2 * j + 1] : -1.f;
+        };
+        float nx[5];
+        fetch(0, nx);
         for (int t = 0; t < nt; ++t) {
             const int b = t & 1;
+            const float mx = nx[0], my = nx[1], mz = nx[2], su = nx[3], sv = nx[4];
+            fetch(t + 1, nx);
             if (t >= 2 && !await_warp(&psi_empty[b], ((t >> 1) - 1) & 1, st, kSiteDecodeMma, &abort_flag)) break;
-            const int64_t j = static_cast<int64_t>(t0 + t) * kAT + row;
-            const bool valid = j < p.n;
-            const float mx = valid ? p.mu[3 * j] : 0.f, my = valid ? p.mu[3 * j + 1] : 0.f;
-            const float mz = valid ? p.mu[3 * j + 2] : 0.f;
-            const bool act = valid && frustum_active(cam_s, mx, my, mz, p.scale[2 * j], p.scale[2 * j + 1]);
+            const bool act = su >= 0.f && frustum_active(cam_s, mx, my, mz, su, sv);
             const uint32_t word = __ballot_sync(0xffffffffu, act);
             if (lane == 0) mask[t & 3][gq] = word;
             __syncwarp();
@@ -617,13 +654,22 @@ __global__ void __launch_bounds__(kAThreads, 1)
     } else if (is_psi_warp(wid)) {
         // ---------------- frustum mask and psi tile, one surfel per thread
         const int gq = psi_warp_index(wid), row = gq * 32 + lane;
-        for (int t = 0; t < nt; ++t) {
-            if (t >= 1 && !await_warp(&psi_empty, (t - 1) & 1, st, kSiteDecodeMma, &abort_flag)) break;
+        auto fetch = [&](int t, float *m5) {
             const int64_t j = static_cast<int64_t>(t0 + t) * kAT + row;
-            const bool valid = j < p.n;
-            const float mx = valid ? p.mu[3 * j] : 0.f, my = valid ? p.mu[3 * j + 1] : 0.f;
-            const float mz = valid ? p.mu[3 * j + 2] : 0.f;
-            const bool act = valid && frustum_active(cam_s, mx, my, mz, p.scale[2 * j], p.scale[2 * j + 1]);
+            const bool valid = t < nt && j < p.n;
+            m5[0] = valid ? p.mu[3 * j] : 0.f;
+            m5[1] = valid ? p.mu[3 * j + 1] : 0.f;
+            m5[2] = valid ? p.mu[3 * j + 2] : 0.f;
+            m5[3] = valid ? p.scale[2 * j] : -1.f;
+            m5[4] = valid ? p.scale[2 * j + 1] : -1.f;
+        };
+        float nx[5];
+        fetch(0, nx);
+        for (int t = 0; t < nt; ++t) {
+            const float mx = nx[0], my = nx[1], mz = nx[2], su = nx[3], sv = nx[4];
+            fetch(t + 1, nx);
+            if (t >= 1 && !await_warp(&psi_empty, (t - 1) & 1, st, kSiteDecodeMma, &abort_flag)) break;
+            const bool act = su >= 0.f && frustum_active(cam_s, mx, my, mz, su, sv);
             const uint32_t word = __ballot_sync(0xffffffffu, act);
             if (lane == 0) mask[t & 3][gq] = word;
             __syncwarp();
@@ -722,22 +768,20 @@ __global__ void __launch_bounds__(kAThreads, 1)
                 tmem_ld16_async(tmem + lane_bits + 128 + c0, dv);
                 tmem_wait_ld();
                 if (act && p.g_feat) {
+                    // added with 16-byte reductions: no load of the row to wait for
                     float4 *gf = reinterpret_cast<float4 *>(p.g_feat + j * C + c0);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        float4 v = gf[e];
-                        v.x += __uint_as_float(dk[c0 + 4 * e]) + __uint_as_float(dv[4 * e]);
-                        v.y += __uint_as_float(dk[c0 + 4 * e + 1]) + __uint_as_float(dv[4 * e + 1]);
-                        v.z += __uint_as_float(dk[c0 + 4 * e + 2]) + __uint_as_float(dv[4 * e + 2]);
-                        v.w += __uint_as_float(dk[c0 + 4 * e + 3]) + __uint_as_float(dv[4 * e + 3]);
-                        gf[e] = v;
-                    }
+                    for (int e = 0; e < 4; ++e)
+                        atomicAdd(gf + e, make_float4(__uint_as_float(dk[c0 + 4 * e]) + __uint_as_float(dv[4 * e]),
+                                                      __uint_as_float(dk[c0 + 4 * e + 1]) + __uint_as_float(dv[4 * e + 1]),
+                                                      __uint_as_float(dk[c0 + 4 * e + 2]) + __uint_as_float(dv[4 * e + 2]),
+                                                      __uint_as_float(dk[c0 + 4 * e + 3]) + __uint_as_float(dv[4 * e + 3])));
                 }
             }
             if (act && p.g_mu) {
-                p.g_mu[3 * j] += gm[0];
-                p.g_mu[3 * j + 1] += gm[1];
-                p.g_mu[3 * j + 2] += gm[2];
+                atomicAdd(p.g_mu + 3 * j, gm[0]);
+                atomicAdd(p.g_mu + 3 * j + 1, gm[1]);
+                atomicAdd(p.g_mu + 3 * j + 2, gm[2]);
             }
             tc_fence_before();
             __syncwarp();
