@@ -106,7 +106,9 @@ typedef struct {
     float chi2;             /* squared support radius in (u,v) units (paper: "e.g. 3 sigma" -> 9) */
     float z_near;           /* near plane; the whole support disc must lie beyond it */
     int32_t opacity_radius; /* 1: shrink the radius to where o*exp(-d^2/2) reaches 1/255 */
-    int32_t tile_w, tile_h; /* tile size in pixels (16x16 supported) */
+    int32_t tile_w, tile_h; /* tile size in pixels: 16x16, or 16x8 (top_k in 1..8, no low-pass
+                               filter): smaller tiles give shorter lists per CTA for more
+                               (tile, surfel) pairs; which is faster depends on the frame */
     float t_eps;            /* stop a pixel after the surfel that takes T below this */
     int32_t lowpass;        /* 1: the 2DGS object-space low-pass filter (Sec. 3.1 surfels
                                follow 2DGS): the Gaussian argument is min(u^2+v^2, 2|x-c|^2),
@@ -328,7 +330,12 @@ int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi
  * per SM (top_k <= 8: forward 3 -> 4, adjoint 4 -> 3 with saved state and
  * 3 -> 4 without; larger K and dense features: 2 -> 1), i.e. registers per
  * thread against occupancy; bit 1 composites dense features
- * (top_k = 0, dim a multiple of 32) 16 channels per pass instead of 32.
+ * (top_k = 0, dim a multiple of 32) 16 channels per pass instead of 32;
+ * bit 2 is the persistent launch: a few CTAs per SM, each taking tiles
+ * (of all views) longest list first from a work counter kept in the context
+ * (the last CTA resets it, so compositing calls through one context must not
+ * overlap on the GPU). With 16x8 tiles (psi_render_opts.tile_h = 8) the
+ * kernels have one occupancy and bit 0 changes nothing.
  * Every shape computes the same result: the forward bit for bit, the adjoint
  * up to the order of its float32 atomic additions. Which one is fastest
  * depends on K, the feature dtype, the scene and the resolution, so it is
@@ -348,7 +355,7 @@ int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi
  * psi_ctx_set_render_shape / psi_ctx_get_render_shape write or read the
  * stored shape directly: which = 0 forward, 1 adjoint; feat_dtype a
  * psi_dtype, or -1 without features; saved 0/1 (adjoint only). */
-#define PSI_RENDER_SHAPES 4
+#define PSI_RENDER_SHAPES 8
 int psi_tune_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
                         const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
                         const psi_render_opts *o, const psi_fwd_out *out, int reps, float *ms, int *best,

@@ -54,9 +54,11 @@ int check_opts(psi_ctx *ctx, const psi_render_opts *o)
 {
     if (!o) return fail(ctx, PSI_ERR_INVALID_ARG, "opts is NULL");
     if (o->mode < PSI_ISECT_SPHERE || o->mode > PSI_ISECT_EXACT) return fail(ctx, PSI_ERR_INVALID_ARG, "bad mode %d", o->mode);
-    if (o->tile_w != 16 || o->tile_h != 16)
-        return fail(ctx, PSI_ERR_UNSUPPORTED, "tile %dx%d unsupported (16x16 only)", o->tile_w, o->tile_h);
+    if (o->tile_w != 16 || (o->tile_h != 16 && o->tile_h != 8))
+        return fail(ctx, PSI_ERR_UNSUPPORTED, "tile %dx%d unsupported (16x16 or 16x8)", o->tile_w, o->tile_h);
     if (o->top_k < 0 || o->top_k > PSI_MAX_TOPK) return fail(ctx, PSI_ERR_INVALID_ARG, "top_k %d out of [0,32]", o->top_k);
+    if (o->tile_h == 8 && (o->top_k < 1 || o->top_k > 8 || o->lowpass))
+        return fail(ctx, PSI_ERR_UNSUPPORTED, "16x8 tiles need 1 <= top_k <= 8 and no low-pass filter");
     if (!(o->chi2 > 0.0f) || !(o->chi2 < 1e4f)) return fail(ctx, PSI_ERR_INVALID_ARG, "chi2 must be in (0, 1e4)");
     if (!(o->z_near > 0.0f)) return fail(ctx, PSI_ERR_INVALID_ARG, "z_near must be > 0");
     if (!(o->t_eps >= 0.0f) || !(o->t_eps < 1.0f)) return fail(ctx, PSI_ERR_INVALID_ARG, "t_eps must be in [0,1)");

@@ -20,6 +20,7 @@ struct DevStatus {
     int32_t wait_site;
     unsigned long long required_pairs;
     unsigned long long wait_limit_ns;
+    unsigned int work[4]; // persistent compositing: tile counter and finished-CTA count (forward, adjoint)
 };
 constexpr size_t kDevStatusReportBytes = 16;
 
@@ -207,11 +208,13 @@ struct FeatView {
 // Launch shapes of the compositing kernels (a4, a5), picked per workload by
 // the autotuner: bit 0 builds the kernel for the alternative number of CTAs
 // per SM (registers per thread against occupancy), bit 1 composites dense
-// features (K = 0) 16 channels per pass instead of 32. Every shape computes
-// the same result.
+// features (K = 0) 16 channels per pass instead of 32, bit 2 launches the
+// persistent form (a few CTAs per SM fetching tiles from a counter). Every
+// shape computes the same result.
 constexpr int kShapeAltOcc = 1;
 constexpr int kShapeAltChunk = 2;
-constexpr int kShapes = 4;
+constexpr int kShapePersistent = 4;
+constexpr int kShapes = 8;
 // channels per pass of the dense feature path for this shape
 inline int render_channel_chunk(int D, int K, int shape)
 {

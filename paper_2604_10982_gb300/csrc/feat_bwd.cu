@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
     const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
     int lxi, lyi;
     pixel_of_thread(tid, lxi, lyi);
-    const int px = tx * kTile + lxi, py = ty * kTile + lyi;
+    const int px = tx * kTile + lxi, py = ty * fp.tile_h + lyi; // blockDim = 16 x tile height
     const bool inside = px < cam.W && py < cam.H;
     const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
     const int K = fp.top_k;
@@ -159,9 +159,9 @@ cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FeatBwdArgs
 {
     const unsigned grid = static_cast<unsigned>(fp.n_tiles_total);
     switch (f.dtype) {
-    case PSI_BF16: feat_bwd_kernel<KMAX, PSI_BF16><<<grid, 256, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: feat_bwd_kernel<KMAX, PSI_FP8_E4M3><<<grid, 256, 0, st>>>(fp, a); break;
-    default: feat_bwd_kernel<KMAX, PSI_F32><<<grid, 256, 0, st>>>(fp, a); break;
+    case PSI_BF16: feat_bwd_kernel<KMAX, PSI_BF16><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: feat_bwd_kernel<KMAX, PSI_FP8_E4M3><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+    default: feat_bwd_kernel<KMAX, PSI_F32><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
 }

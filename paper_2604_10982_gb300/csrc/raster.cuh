@@ -9,7 +9,7 @@
 namespace psi {
 namespace raster {
 
-constexpr int kTile = 16;    // 16x16 pixels per CTA, one thread per pixel
+constexpr int kTile = 16;    // tile width in pixels (16x16 or 16x8 tiles), one thread per pixel
 constexpr int kRecF4 = 5;    // render record: 80 bytes = 5 float4
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
@@ -169,17 +169,21 @@ struct TopK {
 
 // ------------------------------------------------------------ decoupled pipeline
 // A tile's list is streamed through kPS shared-memory stages of kPB records. A
-// dedicated producer warp (warp 8) fills a stage with one TMA bulk copy per
-// record (completion on full[s]), transforms the records for the tile once
-// (ready[s]), and refills the stage after all eight pixel warps released it
-// (empty[s], 8 arrivals). Pixel warps only wait for ready stages, so a warp
+// dedicated producer warp (the last warp) fills a stage with one TMA bulk copy
+// per record (completion on full[s]), transforms the records for the tile once
+// (ready[s]), and refills the stage after all pixel warps (8 for a 16x16 tile,
+// 4 for 16x8) released it (empty[s], one arrival per pixel warp). Pixel warps only wait for ready stages, so a warp
 // with little work in a batch runs ahead instead of waiting at a CTA barrier.
 // Every wait is bounded; `alive` counts pixel warps with pixels still
 // compositing (the producer stops when it reaches zero).
 constexpr int kPS = 4;            // stages
 constexpr int kPB = 128;          // records per stage (four 32-bit hit words per warp)
-constexpr int kPixelWarps = 8;
-constexpr int kPipeThreads = 32 * (kPixelWarps + 1);
+// pixel warps of a 16 x TH tile (8x4-pixel blocks, two per block row) and the
+// CTA size with the producer warp
+__host__ __device__ constexpr int pixel_warps(int TH) { return TH / 2; }
+__host__ __device__ constexpr int pipe_threads(int TH) { return 32 * (pixel_warps(TH) + 1); }
+constexpr int kPixelWarps = pixel_warps(16);
+constexpr int kPipeThreads = pipe_threads(16);
 
 struct Pipe {
     float4 rec[kPS][kPB][kRecF4];
@@ -191,17 +195,38 @@ struct Pipe {
 
 __device__ __forceinline__ int vload(const int &x) { return *reinterpret_cast<const volatile int *>(&x); }
 
-// thread 0; the caller synchronises the CTA afterwards
+// thread 0; the caller synchronises the CTA afterwards. alive = the number of
+// pixel warps (each releases every stage once per batch)
 __device__ __forceinline__ void pipe_init(Pipe &P, int alive)
 {
     for (int s = 0; s < kPS; ++s) {
         mbar_init(&P.full[s], 1);
         mbar_init(&P.ready[s], 1);
-        mbar_init(&P.empty[s], kPixelWarps);
+        mbar_init(&P.empty[s], alive);
     }
     P.alive = alive;
     P.abort = 0;
     fence_mbar_init();
+}
+
+// thread 0, between two tiles of a persistent CTA (after a CTA barrier):
+// retire the barriers so that pipe_init may initialise them again
+__device__ __forceinline__ void pipe_inval(Pipe &P)
+{
+    for (int s = 0; s < kPS; ++s) {
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.full[s])) : "memory");
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.ready[s])) : "memory");
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.empty[s])) : "memory");
+    }
+}
+
+// Grid of a persistent compositing launch: occ CTAs per SM, at most one per tile.
+inline unsigned persistent_grid(uint32_t n_tiles, int occ)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return static_cast<unsigned>(std::min<int64_t>(n_tiles, static_cast<int64_t>(occ) * sms));
 }
 
 // Batch b of a walk over n list entries (forward: from the front; reverse:

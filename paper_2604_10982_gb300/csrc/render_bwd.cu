@@ -61,6 +61,7 @@ struct BwdArgs {
     const int32_t *saved_last; // [P_total]
     const int32_t *saved_topk; // [P_total, K] surfel ids in list order, -1 padded
     const float *kd_saved;     // [P_total, K] <gF, f_j> of the saved set (feat_bwd.cu), or NULL
+    unsigned int *work;        // persistent launch: the context's adjoint tile counter pair; NULL: one tile per CTA
 };
 
 // Sum 12 per-lane values over the warp (a transposing butterfly, 13
@@ -145,19 +146,17 @@ constexpr int kDirectLanes = 4;
 // otherwise pass A recomputes them. With SAVED and K > 0 the feature terms
 // (<gF, f_j> and dL/df) come from the per-pixel feature kernel instead of this
 // walk. CH (channel chunk) matters only for K = 0.
-// OCC: CTAs per SM the kernel is built for (the launch shape the autotuner picks)
-template <int KMAX, int DT, int CH, bool SAVED, bool LP, int OCC>
-__global__ void __launch_bounds__(kPipeThreads, OCC)
-    render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
+// One tile (the whole CTA; P freshly initialised by thread 0 below).
+template <int KMAX, int DT, int CH, bool SAVED, bool LP, int TH>
+__device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a, Pipe &P, int &s_maxlast,
+                                         uint32_t tile)
 {
+    constexpr int PW = pixel_warps(TH);
     constexpr int kM = moments_per_record(LP);
     constexpr int kSums = LP ? 13 : 11; // colour (3), dL/do, moments
     constexpr int kSlots = LP ? 16 : 12;
-    __shared__ __align__(128) Pipe P;
-    __shared__ int s_maxlast;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const bool producer = wid == kPixelWarps;
-    const uint32_t tile = a.ranges[2 * fp.n_tiles_total + blockIdx.x]; // longest lists first
+    const bool producer = wid == PW;
     const int v = view_of_tile(fp, tile);
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);
@@ -166,16 +165,20 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
     const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
     const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
     const int K = KMAX > 0 ? fp.top_k : 0;
-    const int tileX = tx * kTile, tileY = ty * kTile;
+    // a 16x8 tile plays the upper or lower half of its 16x16 tile (see the
+    // forward kernel): same folded records, same per-pixel float32 sequence
+    const int oy = (ty * TH) & 15;
+    const int vw = wid + (oy ? pixel_warps(16) / 2 : 0);
+    const int tileX = tx * kTile, tileY = ty * TH - oy;
     int lxi = 0, lyi = 0;
-    if (!producer) pixel_of_thread(tid, lxi, lyi);
+    if (!producer) pixel_of_thread(vw * 32 + lane, lxi, lyi);
     const int px = tileX + lxi, py = tileY + lyi;
     const bool inside = !producer && px < cam.W && py < cam.H;
     const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
     const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
 
     if (tid == 0) {
-        pipe_init(P, kPixelWarps);
+        pipe_init(P, PW);
         s_maxlast = 0;
     }
     __syncthreads();
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
             const int lo = batch_range(b, n, false, cnt);
             if (!wdone) {
                 uint32_t hw[kPB / 32];
-                pipe_hit_words(P, st, cnt, wid, hw);
+                pipe_hit_words(P, st, cnt, vw, hw);
                 bool all_done = false;
 #pragma unroll 1
                 for (int q = 0; q < kPB / 32 && !all_done; ++q)
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
                 asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.ready[s])) : "memory");
                 asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.empty[s])) : "memory");
             }
-            pipe_init(P, kPixelWarps);
+            pipe_init(P, PW);
         }
         __syncthreads();
     }
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
         const int limit = min(cnt, warp_last - lo); // entries [0, limit) of the batch can matter
         if (limit > 0) {
             uint32_t hw[kPB / 32];
-            pipe_hit_words(P, st, cnt, wid, hw);
+            pipe_hit_words(P, st, cnt, vw, hw);
 #pragma unroll 1
             for (int q = kPB / 32 - 1; q >= 0; --q) {
                 uint32_t bits = q == 0 ? hw[0] : q == 1 ? hw[1] : q == 2 ? hw[2] : hw[3];
@@ -494,6 +497,38 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
     }
 }
 
+// OCC: CTAs per SM the kernel is built for (the launch shape the autotuner
+// picks). Tiles longest list first; the persistent launch (a.work set) fetches
+// further tiles from the context's counter as the forward kernel does.
+template <int KMAX, int DT, int CH, bool SAVED, bool LP, int OCC, int TH = 16>
+__global__ void __launch_bounds__(pipe_threads(TH), OCC)
+    render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
+{
+    __shared__ __align__(128) Pipe P;
+    __shared__ int s_maxlast;
+    __shared__ uint32_t s_next;
+    uint32_t i = blockIdx.x;
+    while (true) {
+        bwd_tile<KMAX, DT, CH, SAVED, LP, TH>(fp, a, P, s_maxlast, a.ranges[2 * fp.n_tiles_total + i]);
+        if (!a.work) break;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_next = vload(P.abort) ? 0xffffffffu : gridDim.x + atomicAdd(&a.work[0], 1u);
+            pipe_inval(P);
+        }
+        __syncthreads();
+        i = s_next;
+        if (i >= fp.n_tiles_total) break;
+    }
+    if (a.work && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.work[1], 1u) == gridDim.x - 1) {
+            a.work[0] = 0u;
+            a.work[1] = 0u;
+        }
+    }
+}
+
 // Per record: dL/dM = T^T M'^-T W (M' = T M is the map shifted to the projected
 // centre), then through M = [K R s_u t_u | K R s_v t_v | K (R mu + t)].
 template <bool LP>
@@ -606,19 +641,25 @@ __global__ void __launch_bounds__(256) chain_kernel(const __grid_constant__ Fram
     }
 }
 
-template <int KMAX, int CH, bool SAVED, bool LP, int OCC>
+template <int KMAX, int CH, bool SAVED, bool LP, int OCC, int TH = 16>
 cudaError_t launch_kcslo(const FrameParams &fp, const FeatView &f, const BwdArgs &a, cudaStream_t st)
 {
-    const unsigned grid = fp.n_tiles_total;
+    unsigned grid = fp.n_tiles_total;
+    if (a.work) grid = persistent_grid(fp.n_tiles_total, OCC);
+    constexpr int nt = pipe_threads(TH);
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED, LP, OCC, TH><<<grid, nt, 0, st>>>(fp, a); break;
     case PSI_FP8_E4M3:
-        render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH, SAVED, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a);
+        render_bwd_kernel<KMAX, PSI_FP8_E4M3, CH, SAVED, LP, OCC, TH><<<grid, nt, 0, st>>>(fp, a);
         break;
-    default: render_bwd_kernel<KMAX, PSI_F32, CH, SAVED, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    default: render_bwd_kernel<KMAX, PSI_F32, CH, SAVED, LP, OCC, TH><<<grid, nt, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
 }
+
+// 16x8 tiles (Top-K with K <= 8, no low-pass filter): 4 pixel warps, 5 CTAs per SM
+// (shared memory: one pipeline each)
+constexpr int kOccTile8 = 5;
 
 template <int KMAX, int CH, bool SAVED, bool LP>
 cudaError_t launch_kcsl(const FrameParams &fp, const FeatView &f, const BwdArgs &a, bool alt, cudaStream_t st)
@@ -716,8 +757,12 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
     const int K = fp.top_k;
     const int ch = render_channel_chunk(f.dim, K, shape);
     const bool alt = shape & kShapeAltOcc;
+    a.work = (shape & kShapePersistent) ? status->work + 2 : nullptr;
     mark(PSI_KERNEL_BWD_WALK, 0);
-    if (K == 0)
+    if (fp.tile_h == 8)
+        e = a.saved_T ? launch_kcslo<8, 16, true, false, kOccTile8, 8>(fp, f, a, st)
+                      : launch_kcslo<8, 16, false, false, kOccTile8, 8>(fp, f, a, st);
+    else if (K == 0)
         e = launch_k<0>(fp, f, a, ch, alt, st);
     else if (K <= 8)
         e = launch_k<8>(fp, f, a, ch, alt, st);

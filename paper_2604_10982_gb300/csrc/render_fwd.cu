@@ -38,16 +38,16 @@ struct FwdArgs {
     float *topk_w;
     int32_t *argmax;
     DevStatus *status;
+    unsigned int *work; // persistent launch: the context's tile counter pair; NULL: one tile per CTA
 };
 
-// OCC: CTAs per SM the kernel is built for (the launch shape the autotuner picks)
-template <int KMAX, int DT, int CH, bool LP, int OCC>
-__global__ void __launch_bounds__(kPipeThreads, OCC)
-    render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
+// One tile of the frame (the whole CTA; P freshly initialised by thread 0
+// below). TH: tile height (16x16 or 16x8 tiles).
+template <int KMAX, int DT, int CH, bool LP, int TH>
+__device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a, Pipe &P, uint32_t tile)
 {
-    __shared__ __align__(128) Pipe P;
+    constexpr int PW = pixel_warps(TH);
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const uint32_t tile = a.ranges[2 * fp.n_tiles_total + blockIdx.x]; // longest lists first
     const int v = view_of_tile(fp, tile);
     const ViewParams &cam = fp.v[v];
     const int local = static_cast<int>(tile - cam.tile_base);
@@ -56,16 +56,22 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
     const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
     const int nb = (n + kPB - 1) / kPB;
 
-    if (tid == 0) pipe_init(P, kPixelWarps);
+    // A 16x8 tile is the upper or lower half of the 16x16 tile it lies in:
+    // records are folded at that 16x16 tile's origin and its pixel warps play
+    // warps 0-3 or 4-7 of it, so every pixel evaluates exactly the float32
+    // sequence of the 16x16 launch (same results bit for bit).
+    const int oy = (ty * TH) & 15;
+    const int vw = wid + (oy ? pixel_warps(16) / 2 : 0); // warp of the 16x16 tile this warp plays
+    if (tid == 0) pipe_init(P, PW);
     __syncthreads();
-    if (wid == kPixelWarps) {
-        pipe_produce(P, a.vals, list0, n, false, a.records, tx * kTile, ty * kTile, a.status, kSiteRenderFwd);
+    if (wid == PW) {
+        pipe_produce(P, a.vals, list0, n, false, a.records, tx * kTile, ty * TH - oy, a.status, kSiteRenderFwd);
         return;
     }
 
     int lxi, lyi;
-    pixel_of_thread(tid, lxi, lyi);
-    const int px = tx * kTile + lxi, py = ty * kTile + lyi;
+    pixel_of_thread(vw * 32 + lane, lxi, lyi);
+    const int px = tx * kTile + lxi, py = ty * TH - oy + lyi;
     const bool inside = px < cam.W && py < cam.H;
     const float lx = static_cast<float>(lxi), ly = static_cast<float>(lyi);
     const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
         if (!wdone) {
             // only the records that touch this warp's pixel block, in list order
             uint32_t hw[kPB / 32];
-            pipe_hit_words(P, st, cnt, wid, hw);
+            pipe_hit_words(P, st, cnt, vw, hw);
             bool all_done = false;
 #pragma unroll 1
             for (int q = 0; q < kPB / 32 && !all_done; ++q)
@@ -201,17 +207,56 @@ __global__ void __launch_bounds__(kPipeThreads, OCC)
     }
 }
 
-template <int KMAX, int CH, bool LP, int OCC>
+// OCC: CTAs per SM the kernel is built for (the launch shape the autotuner
+// picks). Tiles are taken longest list first: CTA b starts with entry b of the
+// launch order; in the persistent launch (a.work set, grid of a few CTAs per
+// SM) each CTA then fetches the next entry from the context's counter until
+// the order is exhausted, and the last CTA to finish resets the counter pair
+// for the next launch (launches through one context must not overlap).
+template <int KMAX, int DT, int CH, bool LP, int OCC, int TH = 16>
+__global__ void __launch_bounds__(pipe_threads(TH), OCC)
+    render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
+{
+    __shared__ __align__(128) Pipe P;
+    __shared__ uint32_t s_next;
+    uint32_t i = blockIdx.x;
+    while (true) {
+        fwd_tile<KMAX, DT, CH, LP, TH>(fp, a, P, a.ranges[2 * fp.n_tiles_total + i]);
+        if (!a.work) break;
+        __syncthreads(); // every warp is done with this tile's pipeline
+        if (threadIdx.x == 0) {
+            s_next = vload(P.abort) ? 0xffffffffu : gridDim.x + atomicAdd(&a.work[0], 1u);
+            pipe_inval(P);
+        }
+        __syncthreads();
+        i = s_next;
+        if (i >= fp.n_tiles_total) break;
+    }
+    if (a.work && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.work[1], 1u) == gridDim.x - 1) {
+            a.work[0] = 0u;
+            a.work[1] = 0u;
+        }
+    }
+}
+
+template <int KMAX, int CH, bool LP, int OCC, int TH = 16>
 cudaError_t launch_kclo(const FrameParams &fp, const FeatView &f, const FwdArgs &a, cudaStream_t st)
 {
-    const unsigned grid = fp.n_tiles_total;
+    unsigned grid = fp.n_tiles_total;
+    if (a.work) grid = persistent_grid(fp.n_tiles_total, OCC);
+    constexpr int nt = pipe_threads(TH);
     switch (f.data ? f.dtype : PSI_F32) {
-    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
-    default: render_fwd_kernel<KMAX, PSI_F32, CH, LP, OCC><<<grid, kPipeThreads, 0, st>>>(fp, a); break;
+    case PSI_BF16: render_fwd_kernel<KMAX, PSI_BF16, CH, LP, OCC, TH><<<grid, nt, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: render_fwd_kernel<KMAX, PSI_FP8_E4M3, CH, LP, OCC, TH><<<grid, nt, 0, st>>>(fp, a); break;
+    default: render_fwd_kernel<KMAX, PSI_F32, CH, LP, OCC, TH><<<grid, nt, 0, st>>>(fp, a); break;
     }
     return cudaGetLastError();
 }
+
+// 16x8 tiles (Top-K with K <= 8, no low-pass filter): 4 pixel warps, up to 5 CTAs per SM
+constexpr int kOccTile8 = 5;
 
 template <int KMAX, int CH, bool LP>
 cudaError_t launch_kcl(const FrameParams &fp, const FeatView &f, const FwdArgs &a, bool alt, cudaStream_t st)
@@ -267,6 +312,7 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
     const int K = fp.top_k;
     const int ch = render_channel_chunk(f.dim, K, shape);
     const bool alt = shape & kShapeAltOcc;
+    a.work = (shape & kShapePersistent) ? status->work : nullptr;
     if (K == 0) {
         // dense: one pass per chunk of channels (the first also writes rgb/T)
         cudaError_t e = launch_k<0>(fp, f, a, ch, alt, st);
@@ -277,6 +323,7 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
         }
         return e;
     }
+    if (fp.tile_h == 8) return launch_kclo<8, 16, false, kOccTile8, 8>(fp, f, a, st);
     if (K <= 8) return launch_k<8>(fp, f, a, ch, alt, st);
     if (K <= 16) return launch_k<16>(fp, f, a, ch, alt, st);
     return launch_k<32>(fp, f, a, ch, alt, st);

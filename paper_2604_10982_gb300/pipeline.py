@@ -320,6 +320,49 @@ def label_scene(scene: DeviceScene, labels: torch.Tensor) -> DeviceScene:
     return ls
 
 
+def tune_tile_height(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, g_rgb=None, g_F=None, g_T=None,
+                     grads=None, reps: int = 3, stream=None):
+    """The tile-shape half of the autotuner: time one whole frame (project,
+    intersect, sort, render and, with upstream gradients, the adjoint) with
+    16x16 and with 16x8 tiles (the latter exists for 1 <= top_k <= 8 without
+    the low-pass filter) on the caller's frame, CUDA events on the stream,
+    one untimed run each, and return (opts with the faster tile height,
+    {tile height: ms per frame}). Both tile shapes give the same frame bit for
+    bit; the launch shapes of each are tuned with Renderer.tune."""
+    import copy
+    heights = [16]
+    if 1 <= int(opts.top_k) <= 8 and not int(opts.lowpass):
+        heights.append(8)
+    ms = {}
+    for th in heights:
+        o = copy.copy(opts)
+        o.tile_h = th
+        r = make_renderer(ctx, scene, cams, o, D=D, F_dtype=F_dtype)
+        s = stream if stream is not None else torch.cuda.current_stream()
+
+        def one():
+            r.frame(scene, stream=s)
+            if g_rgb is not None:
+                if grads is not None:
+                    psi.psi_grads_zero(ctx, psi.PsiGrads(*(psi._ptr(grads[k]) for k in
+                                                            ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat"))),
+                                       scene.n, scene.D, s)
+                r.backward(scene, g_rgb, g_F, g_T, grads=grads, stream=s)
+        one()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            one()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms[th] = e0.elapsed_time(e1) / reps
+        del r
+    best = min(ms, key=ms.get)
+    o = copy.copy(opts)
+    o.tile_h = best
+    return o, ms
+
+
 def make_renderer(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, want_topk_ids=True, headroom=1.25,
                   min_capacity=1024):
     """Renderer whose key buffer fits this scene and these cameras."""

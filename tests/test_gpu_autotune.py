@@ -50,7 +50,7 @@ def _outputs(r):
 
 
 def _valid(K, D=32):
-    return [s for s in range(4) if not (s & 2) or (K == 0 and D % 32 == 0)]
+    return [s for s in range(8) if not (s & 2) or (K == 0 and D % 32 == 0)]
 
 
 @pytest.mark.parametrize("K,lowpass", [(0, False), (8, False), (16, False), (8, True)])
@@ -94,7 +94,7 @@ def test_tuner_stores_fastest_and_zeroes_grads(ctx, box, K):
         ms, best = rep[key]
         valid = _valid(K)
         assert best in valid
-        assert all(ms[s] > 0 for s in valid) and all(ms[s] == -1 for s in range(4) if s not in valid)
+        assert all(ms[s] > 0 for s in valid) and all(ms[s] == -1 for s in range(8) if s not in valid)
         assert ms[best] == min(ms[s] for s in valid)
         assert psi.psi_ctx_get_render_shape(ctx, which, r.opts, psi.F32, saved) == best
     for k in KEYS:
