@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--ablation-frames", type=int, default=6, help="frames per Table-3 row (0: skip)")
     ap.add_argument("--label-frames", type=int, default=8, help="frames of the instance-label path (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=16)
+    ap.add_argument("--batch-reps", type=int, default=10, help="replays of the 16-view batch graph (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -317,6 +318,17 @@ def run_psi(args):
     gC, gF, gT = gC_h.to(dev), gF_h.to(dev), gT_h.to(dev)
 
     opts = psi.default_opts(mode=psi.EXACT, top_k=K, opacity_radius=1)
+    grads = dict(mu=torch.zeros(scene.n, 3, device=dev), tu=torch.zeros(scene.n, 3, device=dev),
+                 tv=torch.zeros(scene.n, 3, device=dev), scale=torch.zeros(scene.n, 2, device=dev),
+                 opacity=torch.zeros(scene.n, device=dev), rgb=torch.zeros(scene.n, 3, device=dev),
+                 feat=torch.zeros(scene.n, D, device=dev))
+    grads_struct = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
+    # the tile shape (16x16 or 16x8) of the autotuner: a whole frame with each, on frame 0
+    tile_ms = None
+    if not args.no_tune:
+        opts, tile_ms = pl.tune_tile_height(ctx, scene, [cams[0]], opts, D=D, F_dtype=psi.BF16, g_rgb=gC, g_F=gF,
+                                            g_T=gT, grads=grads)
+        torch.cuda.synchronize()
     r = pl.Renderer(ctx, scene.n, [cams[0]], opts, 1024, D=D, F_dtype=psi.BF16, device=dev)
     need = 0
     for c in cams:
@@ -324,11 +336,6 @@ def run_psi(args):
         need = max(need, r.required_pairs(scene))
     r.set_capacity(int(need * 1.15) + 1024)
     ids = torch.empty(r.n_pix, dtype=torch.int32, device=dev)
-    grads = dict(mu=torch.zeros(scene.n, 3, device=dev), tu=torch.zeros(scene.n, 3, device=dev),
-                 tv=torch.zeros(scene.n, 3, device=dev), scale=torch.zeros(scene.n, 2, device=dev),
-                 opacity=torch.zeros(scene.n, device=dev), rgb=torch.zeros(scene.n, 3, device=dev),
-                 feat=torch.zeros(scene.n, D, device=dev))
-    grads_struct = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
 
     def stage_fns(f):
         def proj():
@@ -372,10 +379,12 @@ def run_psi(args):
     tuned = None
     if not args.no_tune:
         tr = r.tune(scene, gC, gF, gT, grads=grads, reps=3)
-        tuned = {"forward": {"ms_per_shape": [round(x, 4) for x in tr["fwd"][0]], "shape": tr["fwd"][1]},
+        tuned = {"tile": f"16x{int(opts.tile_h)}", "frame_ms_per_tile_height": tile_ms,
+                 "forward": {"ms_per_shape": [round(x, 4) for x in tr["fwd"][0]], "shape": tr["fwd"][1]},
                  "adjoint": {"ms_per_shape": [round(x, 4) for x in tr["bwd"][0]], "shape": tr["bwd"][1]},
                  "shapes": "bit 0: the other CTAs-per-SM build (K<=8: 3<->4, else 2->1); bit 1: dense 16-channel passes; "
-                           "-1: shape does not apply; timed on frame 0 before the graphs are captured"}
+                           "bit 2: persistent launch (tile counter); -1: shape does not apply; tile height and shapes "
+                           "timed on frame 0 before the graphs are captured"}
     torch.cuda.synchronize()
     use_graph = not args.no_graph
     graphs = None
@@ -784,6 +793,60 @@ def run_psi(args):
                        "the table"}
         del rg, gg, Gt
 
+    # ---- precision plus batching: 1M surfels, 16 views of uneven resolution
+    # (640x360 .. 1920x1080) in one launch per stage, the frame captured as one
+    # CUDA graph; features in BF16, then FP8-E4M3 with per-channel scales;
+    # tile height and launch shapes from the autotuner
+    batch = None
+    batch_frames = {}
+    batch_world = None
+    if args.batch_reps > 0:
+        wb = sg.batch_scene()
+        batch = {"surfels": wb.surfels.n, "views": len(wb.cameras),
+                 "pixels": int(sum(c.width * c.height for c in wb.cameras)), "top_k": 8, "feat_dim": 128}
+        for name, fdt in (("bf16", psi.BF16), ("fp8_e4m3", psi.FP8_E4M3)):
+            sb = pl.DeviceScene(wb.surfels, wb.features, feat_dtype=fdt, device=dev)
+            ob = psi.default_opts(mode=psi.EXACT, top_k=8, opacity_radius=1)
+            ob, tms = pl.tune_tile_height(ctx, sb, wb.cameras, ob, D=D, F_dtype=psi.BF16)
+            rb = pl.make_renderer(ctx, sb, wb.cameras, ob, D=D, F_dtype=psi.BF16)
+            rb.frame(sb)
+            tr = rb.tune(sb, torch.zeros(3, rb.n_pix, device=dev), reps=2)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream(device=dev)
+            with torch.cuda.graph(g, stream=cs, capture_error_mode="relaxed"):
+                rb.frame(sb)
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.batch_reps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            st, _ = ctx.status_fetch()
+            assert st == 0, f"device status {st}"
+            ms = e0.elapsed_time(e1) / args.batch_reps
+            batch[name] = {"ms_per_batch": ms, "views_per_s": len(wb.cameras) * 1000.0 / ms,
+                           "batches_per_s": 1000.0 / ms, "tile": f"16x{int(ob.tile_h)}",
+                           "frame_ms_per_tile_height": tms, "forward_shape": tr["fwd"][1],
+                           "forward_ms_per_shape": [round(x, 4) for x in tr["fwd"][0]],
+                           "pairs": int(rb.num_pairs.item()), "launches_per_batch": rb.kernel_launches()}
+            # 24 sampled pixels of views 2 and 9 for the oracle comparison on the CPU leg
+            rng = np.random.default_rng(2)
+            samp = []
+            for v in (2, 9):
+                cam = wb.cameras[v]
+                idx = rng.choice(cam.width * cam.height, 24, replace=False)
+                p = torch.from_numpy(int(rb.pix_base[v]) + idx).to(dev)
+                samp.append((v, idx, rb.rgb[:, p].T.double().cpu().numpy(), rb.F[p].float().double().cpu().numpy()))
+            batch_frames[name] = (samp, pl.dequantize(sb.q, sb.qscale, fdt))
+            del g, rb, sb
+        batch["form"] = ("project+intersect+sort+render of all 16 views, one launch per stage, replayed as one CUDA "
+                         "graph; EXACT tiles, K=8, FP32 accumulation; ms per batch of 16 views")
+        batch_world = wb
+
     # ---- frustum-constrained cross-attention (Sec. 4.1) over all surfels
     # for one view: 100 queries, C = d = 128, BF16 features; forward and adjoint
     attn = None
@@ -884,6 +947,27 @@ def run_psi(args):
                          f"and forward+gradient+decode of {info['sample_pixels']} random pixels "
                          f"({info['t_pix'] * 1e3:.1f} ms/pixel), extrapolated to {P} pixels"}
         parity = parity_of_sample(info["out"], info["pixels"], cams[0], g_rgb, g_T, g_F, g_tk)
+        if batch is not None:
+            # storage precision of the batch against the FP64 oracle: 24 pixels
+            # of views 2 and 9, the oracle fed the unquantised features (the
+            # storage error) and the stored ones (the arithmetic)
+            from oracle import oracle as orc
+            wb = batch_world
+            ob = orc.Opts(mode=orc.EXACT, top_k=8, opacity_radius=True)
+            f64 = wb.features.astype(np.float64)
+            for name, (samp, deq) in batch_frames.items():
+                e_rgb, e_st, e_q = 0.0, 0.0, 0.0
+                for v, idx, b_rgb, b_F in samp:
+                    cam = wb.cameras[v]
+                    pix = orc.all_pixels(cam)[idx]
+                    ref = orc.render(wb.surfels, cam, ob, feat=f64, pixels=pix)
+                    refq = orc.render(wb.surfels, cam, ob, feat=deq, pixels=pix)
+                    e_rgb = max(e_rgb, float(np.abs(b_rgb - ref["rgb"]).max()))
+                    m = ref["sumw"] > 0.5
+                    e_st = max(e_st, float(np.linalg.norm(b_F[m] - ref["F"][m]) / max(np.linalg.norm(ref["F"][m]), 1e-30)))
+                    e_q = max(e_q, float(np.linalg.norm(b_F[m] - refq["F"][m]) / max(np.linalg.norm(refq["F"][m]), 1e-30)))
+                batch[name]["oracle"] = {"max_abs_err_rgb": e_rgb, "rel_l2_F_vs_unquantised": e_st,
+                                         "rel_l2_F_vs_stored_values": e_q, "pixels": 48}
 
     if rank != 0:
         return
@@ -895,7 +979,7 @@ def run_psi(args):
         "frame_ms_p50": float(np.percentile(frame_ms, 50)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)}, "kernel_ms": kernel_ms,
         "pairs_per_frame": float(np.mean(pairs)), "pairs_per_tile": float(np.mean(pairs) / n_tiles),
-        "autotune": tuned, "plain_fp32": plain, "ablation": ablation, "labels": labels, "regularisers": regs, "compat_2dgs": geo, "attention": attn, "roofline": roof, "cpu_baseline": cpu, "parity": parity, "e2e": e2e,
+        "autotune": tuned, "plain_fp32": plain, "ablation": ablation, "labels": labels, "regularisers": regs, "compat_2dgs": geo, "attention": attn, "roofline": roof, "cpu_baseline": cpu, "parity": parity, "batch16": batch, "e2e": e2e,
         "gpu_launches": int(args.steps * r.kernel_launches(with_decode=True, with_bwd=True)),
         "clocks": clk, "paper_context": PAPER_CONTEXT, "setup_s": setup_s,
     }
