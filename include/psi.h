@@ -167,7 +167,8 @@ const char *psi_last_error(const psi_ctx *ctx);
  * (0 = clean, else a PSI_ERR_* code; TIMEOUT before CAPACITY before
  * INVALID_ARG) and *detail (may be NULL): for PSI_ERR_CAPACITY the pair count
  * the overflowing frame needed, for PSI_ERR_TIMEOUT the code of the first wait
- * that gave up (1 render, 2/3 adjoint passes, 4-6 decode, 7 drain); then
+ * that gave up (1 render, 2/3 adjoint passes, 4-6 decode, 7 drain,
+ * 8 sort); then
  * clears the word. */
 int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64_t *detail);
 

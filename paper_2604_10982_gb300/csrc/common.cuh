@@ -37,7 +37,8 @@ enum WaitSite {
     kSiteDecodeQ = 4,
     kSiteDecodeLoad = 5,
     kSiteDecodeMma = 6,
-    kSiteDrain = 7
+    kSiteDrain = 7,
+    kSiteSort = 8
 };
 
 struct ViewParams {

@@ -1,13 +1,18 @@
 // a3: stable LSD radix sort of (uint64 key, uint32 value) pairs and the
 // per-tile [start, end) ranges of the sorted keys.
 //
-// Each pass sorts one digit with the spin-free reduce-then-scan scheme:
-// per-block digit histograms, one exclusive scan over the digit-major
-// histogram table, then a scatter in which every block ranks its items
+// One kernel reads the keys once and counts the digits of every pass (8-bit
+// digits); a one-block kernel turns the counts into each pass's digit bases.
+// Each pass is then a single kernel with a decoupled look-back: a block takes
+// the next partition of 4096 pairs from a counter (partitions are handed out
+// in launch order, so every predecessor is already running), ranks its items
 // stably (warp match on the digit, per-warp running counters, prefix over
-// warps) and writes them out through shared memory, so runs of one digit leave
-// the block as contiguous, coalesced stores. The number of passes is made even
-// (digit width <= 8 bits) so the result ends in the caller's buffers.
+// warps), publishes its per-digit counts, reads its predecessors' published
+// counts back to the first inclusive prefix (a bounded wait on each flag) to
+// learn where its run of every digit starts, and writes its items out through
+// shared memory so that runs of one digit leave the block as contiguous,
+// coalesced stores. The number of passes is made even so the result ends in
+// the caller's buffers.
 #include <algorithm>
 #include <mutex>
 
@@ -30,37 +35,72 @@ __device__ __forceinline__ int64_t clamped_count(const int64_t *d_n, int64_t cap
     return n < 0 ? 0 : (n > cap ? cap : n);
 }
 
-__global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *__restrict__ keys,
-                                                           const int64_t *__restrict__ d_n, int64_t cap, int shift,
-                                                           int bits, uint32_t *__restrict__ hist, int nblk,
-                                                           DevStatus *status)
+constexpr int kMaxPasses = 8; // 64-bit keys in 8-bit digits
+
+struct PassPlan {
+    int passes;
+    int shift[kMaxPasses];
+    int bits[kMaxPasses];
+};
+
+// Digit counts of every pass in one read of the keys: per block in shared
+// memory, then added to hist[pass][256] (zeroed by the caller).
+__global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t *__restrict__ keys,
+                                                        const int64_t *__restrict__ d_n, int64_t cap, PassPlan plan,
+                                                        uint32_t *__restrict__ hist, DevStatus *status)
 {
-    __shared__ uint32_t h[kWarps][kBins];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < kWarps * kBins; k += kThreads) (&h[0][0])[k] = 0;
+    __shared__ uint32_t h[kMaxPasses][kBins];
+    for (int k = threadIdx.x; k < kMaxPasses * kBins; k += kThreads) (&h[0][0])[k] = 0;
     __syncthreads();
     const int64_t n = clamped_count(d_n, cap);
     if (status && blockIdx.x == 0 && threadIdx.x == 0 && *d_n > cap) {
         raise_status(status, PSI_ERR_CAPACITY);
         atomicMax(&status->required_pairs, static_cast<unsigned long long>(*d_n));
     }
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + wid * (32 * kItems);
-    const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
-    if (static_cast<int64_t>(blockIdx.x) * kTile < n) {
-#pragma unroll 4
-        for (int i = 0; i < kItems; ++i) {
-            const int64_t idx = base + i * 32 + lane;
-            if (idx < n) atomicAdd(&h[wid][static_cast<uint32_t>((keys[idx] >> shift) & mask)], 1u);
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; idx < n;
+         idx += static_cast<int64_t>(gridDim.x) * kThreads) {
+        const uint64_t k = keys[idx];
+        for (int ps = 0; ps < plan.passes; ++ps) {
+            const uint64_t mask = (1ull << plan.bits[ps]) - 1ull;
+            atomicAdd(&h[ps][static_cast<uint32_t>((k >> plan.shift[ps]) & mask)], 1u);
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kBins; d += kThreads) {
-        uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += h[w][d];
-        hist[static_cast<int64_t>(d) * nblk + blockIdx.x] = s;
+    for (int k = threadIdx.x; k < plan.passes * kBins; k += kThreads) {
+        const uint32_t c = (&h[0][0])[k];
+        if (c) atomicAdd(hist + k, c);
     }
 }
+
+// hist[pass][256] -> exclusive prefix per pass, in place (one block)
+__global__ void __launch_bounds__(kBins) digit_scan_kernel(uint32_t *hist, int passes)
+{
+    __shared__ uint32_t wsum[kBins / 32];
+    const int d = threadIdx.x, lane = d & 31, w = d >> 5;
+    for (int ps = 0; ps < passes; ++ps) {
+        const uint32_t c = hist[ps * kBins + d];
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int k = 0; k < w; ++k) before += wsum[k];
+        hist[ps * kBins + d] = before + inc - c;
+        __syncthreads();
+    }
+}
+
+// look-back status word of (partition, digit), one array shared by the passes:
+// flag in bits 62-63, the pass (1-based) in bits 59-61, the count below; a word
+// of an earlier pass reads as not yet published
+constexpr unsigned long long kFlagAgg = 1ull << 62;  // this partition's own count
+constexpr unsigned long long kFlagIncl = 2ull << 62; // count of all partitions up to this one
+constexpr unsigned long long kValueMask = (1ull << 59) - 1ull;
+__device__ __forceinline__ unsigned long long pass_tag(int ps) { return static_cast<unsigned long long>(ps + 1) << 59; }
 
 struct ScatterSmem {
     uint32_t warp_cnt[kWarps][kBins];
@@ -71,23 +111,27 @@ struct ScatterSmem {
     uint32_t xvals[kTile];
 };
 
-__global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *__restrict__ keys_in,
-                                                           const uint32_t *__restrict__ vals_in,
-                                                           uint64_t *__restrict__ keys_out,
-                                                           uint32_t *__restrict__ vals_out,
-                                                           const int64_t *__restrict__ d_n, int64_t cap, int shift,
-                                                           int bits, const unsigned long long *__restrict__ offs,
-                                                           int nblk)
+__global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t *__restrict__ keys_in,
+                                                            const uint32_t *__restrict__ vals_in,
+                                                            uint64_t *__restrict__ keys_out,
+                                                            uint32_t *__restrict__ vals_out,
+                                                            const int64_t *__restrict__ d_n, int64_t cap, int ps,
+                                                            int shift, int bits, const uint32_t *__restrict__ digit_base,
+                                                            unsigned long long *status_words,
+                                                            unsigned int *part_counter, DevStatus *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    __shared__ uint32_t s_part;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_part = atomicAdd(part_counter, 1u);
+    __syncthreads();
+    const int64_t part = s_part;
     const int64_t n = clamped_count(d_n, cap);
-    const int64_t blk0 = static_cast<int64_t>(blockIdx.x) * kTile;
-    if (blk0 >= n) return;
+    const int64_t blk0 = part * kTile;
+    if (blk0 >= n) return; // partitions are handed out in order: no valid one waits for this
     const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
     for (int k = threadIdx.x; k < kWarps * kBins; k += kThreads) (&S.warp_cnt[0][0])[k] = 0;
-    for (int d = threadIdx.x; d < kBins; d += kThreads) S.digit_base[d] = offs[static_cast<int64_t>(d) * nblk + blockIdx.x];
     __syncthreads();
 
     // warp-striped items: item i of lane l is at blk0 + wid*512 + i*32 + l
@@ -123,6 +167,43 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *__res
             run += c;
         }
         cnt = run;
+    }
+    // publish this partition's count of digit d, then read the predecessors'
+    // back to the first inclusive prefix: the block's run of digit d starts at
+    // digit_base[d] + (items of digit d in all earlier partitions)
+    {
+        const int d = threadIdx.x;
+        volatile unsigned long long *row = status_words + part * kBins;
+        unsigned long long excl = 0;
+        const unsigned long long tag = pass_tag(ps);
+        if (part == 0) {
+            row[d] = kFlagIncl | tag | cnt;
+        } else {
+            row[d] = kFlagAgg | tag | cnt;
+            const unsigned long long limit = wait_limit(status);
+            unsigned long long t0 = 0;
+            for (int64_t q = part - 1; q >= 0;) {
+                const unsigned long long w = reinterpret_cast<volatile unsigned long long *>(status_words)[q * kBins + d];
+                if ((w & (kFlagAgg | kFlagIncl)) == 0 || (w & (7ull << 59)) != tag) {
+                    const unsigned long long now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > limit) {
+                        if (status) {
+                            atomicCAS(&status->wait_site, 0, kSiteSort);
+                            raise_status(status, PSI_ERR_TIMEOUT);
+                        }
+                        break;
+                    }
+                    continue;
+                }
+                t0 = 0;
+                excl += w & kValueMask;
+                if (w & kFlagIncl) break;
+                --q;
+            }
+            row[d] = kFlagIncl | tag | (excl + cnt);
+        }
+        S.digit_base[d] = static_cast<unsigned long long>(digit_base[d]) + excl;
     }
     // exclusive scan of the digit counts over the block (256 digits, one per thread)
     uint32_t inc = cnt;
@@ -222,13 +303,17 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t *__rest
 
 } // namespace
 
+namespace {
+int64_t sort_partitions(int64_t capacity) { return (std::max<int64_t>(capacity, 1) + kTile - 1) / kTile; }
+} // namespace
+
+// alternate keys and values, then (zeroed per call) the digit counts of every
+// pass, the partition counters and the look-back status words
 size_t sort_workspace_bytes(int64_t capacity)
 {
     const int64_t cap = std::max<int64_t>(capacity, 1);
-    const int64_t nblk = (cap + kTile - 1) / kTile;
-    const int64_t nh = nblk * kBins;
-    return align_up(cap * 8, 256) + align_up(cap * 4, 256) + align_up(nh * 4, 256) + align_up(nh * 8, 256) +
-           scan_workspace_bytes(nh) + 256;
+    return align_up(cap * 8, 256) + align_up(cap * 4, 256) + align_up(kMaxPasses * kBins * 4 + kMaxPasses * 4, 256) +
+           align_up(sort_partitions(cap) * kBins * 8, 256);
 }
 
 cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pairs, int64_t capacity, int begin_bit,
@@ -236,47 +321,52 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, const int64_t *d_num_pai
                         cudaStream_t st)
 {
     const int64_t cap = std::max<int64_t>(capacity, 1);
-    const int64_t nblk = (cap + kTile - 1) / kTile;
-    const int64_t nh = nblk * kBins;
+    const int64_t nparts = sort_partitions(cap);
     char *p = static_cast<char *>(ws);
     auto *alt_keys = reinterpret_cast<uint64_t *>(p);
     p += align_up(cap * 8, 256);
     auto *alt_vals = reinterpret_cast<uint32_t *>(p);
     p += align_up(cap * 4, 256);
+    char *zero0 = p;
     auto *hist = reinterpret_cast<uint32_t *>(p);
-    p += align_up(nh * 4, 256);
-    auto *offs = reinterpret_cast<unsigned long long *>(p);
-    p += align_up(nh * 8, 256);
-    void *scan_ws = p;
-    p += scan_workspace_bytes(nh);
-    auto *scan_total = reinterpret_cast<unsigned long long *>(p);
+    auto *counters = reinterpret_cast<unsigned int *>(p + kMaxPasses * kBins * 4);
+    p += align_up(kMaxPasses * kBins * 4 + kMaxPasses * 4, 256);
+    auto *status_words = reinterpret_cast<unsigned long long *>(p);
+    p += align_up(nparts * kBins * 8, 256);
+    cudaError_t e = cudaMemsetAsync(zero0, 0, static_cast<size_t>(p - zero0), st);
+    if (e != cudaSuccess) return e;
 
     const int nbits = std::max(end_bit - begin_bit, 1);
-    int passes = std::max(2, (nbits + 7) / 8);
-    if (passes & 1) ++passes;
-    const int dbits = (nbits + passes - 1) / passes;
-    {
-        cudaError_t e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(sizeof(ScatterSmem)));
-        if (e != cudaSuccess) return e;
+    PassPlan plan{};
+    plan.passes = std::max(2, (nbits + 7) / 8);
+    if (plan.passes & 1) ++plan.passes;
+    const int dbits = (nbits + plan.passes - 1) / plan.passes;
+    for (int ps = 0; ps < plan.passes; ++ps) {
+        const int shift = begin_bit + ps * dbits;
+        const int bits = std::max(0, std::min(dbits, end_bit - shift));
+        plan.shift[ps] = bits == 0 ? 0 : shift; // identity pass (keeps the pass count even)
+        plan.bits[ps] = bits;
     }
+    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sizeof(ScatterSmem)));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned hgrid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(nparts * kItems, sms * 8)));
+    hist_kernel<<<hgrid, kThreads, 0, st>>>(keys, d_num_pairs, cap, plan, hist, status);
+    digit_scan_kernel<<<1, kBins, 0, st>>>(hist, plan.passes);
     uint64_t *kin = keys, *kout = alt_keys;
     uint32_t *vin = vals, *vout = alt_vals;
-    for (int ps = 0; ps < passes; ++ps) {
-        int shift = begin_bit + ps * dbits;
-        const int bits = std::max(0, std::min(dbits, end_bit - shift));
-        if (bits == 0) shift = 0; // identity pass (keeps the pass count even)
-        upsweep_kernel<<<static_cast<unsigned>(nblk), kThreads, 0, st>>>(
-            kin, d_num_pairs, cap, shift, bits, hist, static_cast<int>(nblk), ps == 0 ? status : nullptr);
-        cudaError_t e = launch_scan_u32(hist, offs, nh, scan_total, scan_ws, st);
-        if (e != cudaSuccess) return e;
-        scatter_kernel<<<static_cast<unsigned>(nblk), kThreads, sizeof(ScatterSmem), st>>>(
-            kin, vin, kout, vout, d_num_pairs, cap, shift, bits, offs, static_cast<int>(nblk));
+    for (int ps = 0; ps < plan.passes; ++ps) {
+        onesweep_kernel<<<static_cast<unsigned>(nparts), kThreads, sizeof(ScatterSmem), st>>>(
+            kin, vin, kout, vout, d_num_pairs, cap, ps, plan.shift[ps], plan.bits[ps], hist + ps * kBins, status_words,
+            counters + ps, status);
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
     if (tile_ranges && n_tiles_total > 0) {
-        cudaError_t e = cudaMemsetAsync(tile_ranges, 0, static_cast<size_t>(n_tiles_total) * 8, st);
+        e = cudaMemsetAsync(tile_ranges, 0, static_cast<size_t>(n_tiles_total) * 8, st);
         if (e != cudaSuccess) return e;
         ranges_kernel<<<static_cast<unsigned>((cap + 255) / 256), 256, 0, st>>>(keys, d_num_pairs, cap, tile_ranges,
                                                                                n_tiles_total, status);

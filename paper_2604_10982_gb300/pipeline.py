@@ -140,7 +140,7 @@ class Renderer:
         nbits = max(self.key_bits, 1)
         passes = max(2, (nbits + 7) // 8)
         passes += passes & 1
-        n += passes * 5 + 2                                # upsweep + scan(3) + scatter per pass, ranges, tile order
+        n += passes + 4                                    # digit counts, digit scan, one pass each, ranges, tile order
         K = int(self.opts.top_k)
         D = self.D
         ch = 32 if D % 32 == 0 else 16
@@ -321,42 +321,50 @@ def label_scene(scene: DeviceScene, labels: torch.Tensor) -> DeviceScene:
 
 
 def tune_tile_height(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, g_rgb=None, g_F=None, g_T=None,
-                     grads=None, reps: int = 3, stream=None):
+                     grads=None, reps: int = 3, rounds: int = 3, stream=None):
     """The tile-shape half of the autotuner: time one whole frame (project,
     intersect, sort, render and, with upstream gradients, the adjoint) with
     16x16 and with 16x8 tiles (the latter exists for 1 <= top_k <= 8 without
-    the low-pass filter) on the caller's frame, CUDA events on the stream,
-    one untimed run each, and return (opts with the faster tile height,
-    {tile height: ms per frame}). Both tile shapes give the same frame bit for
-    bit; the launch shapes of each are tuned with Renderer.tune."""
+    the low-pass filter) on the caller's frame: CUDA events on the stream,
+    one untimed run each, then `rounds` interleaved rounds of `reps` frames
+    per tile shape, keeping each shape's fastest round. Returns (opts with the
+    faster tile height, {tile height: ms per frame}). Both tile shapes give the
+    same frame bit for bit; the launch shapes of each are tuned with
+    Renderer.tune."""
     import copy
     heights = [16]
     if 1 <= int(opts.top_k) <= 8 and not int(opts.lowpass):
         heights.append(8)
-    ms = {}
+    s = stream if stream is not None else torch.cuda.current_stream()
+    gs = None
+    if g_rgb is not None and grads is not None:
+        gs = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
+    runs = {}
     for th in heights:
         o = copy.copy(opts)
         o.tile_h = th
         r = make_renderer(ctx, scene, cams, o, D=D, F_dtype=F_dtype)
-        s = stream if stream is not None else torch.cuda.current_stream()
 
-        def one():
+        def one(r=r):
             r.frame(scene, stream=s)
             if g_rgb is not None:
-                if grads is not None:
-                    psi.psi_grads_zero(ctx, psi.PsiGrads(*(psi._ptr(grads[k]) for k in
-                                                            ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat"))),
-                                       scene.n, scene.D, s)
+                if gs is not None:
+                    psi.psi_grads_zero(ctx, gs, scene.n, scene.D, s)
                 r.backward(scene, g_rgb, g_F, g_T, grads=grads, stream=s)
         one()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(reps):
-            one()
-        e1.record(s)
-        torch.cuda.synchronize()
-        ms[th] = e0.elapsed_time(e1) / reps
-        del r
+        runs[th] = one
+    torch.cuda.synchronize()
+    ms = {th: float("inf") for th in heights}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(rounds):
+        for th in heights:
+            e0.record(s)
+            for _ in range(reps):
+                runs[th]()
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms[th] = min(ms[th], e0.elapsed_time(e1) / reps)
+    del runs
     best = min(ms, key=ms.get)
     o = copy.copy(opts)
     o.tile_h = best
