@@ -95,12 +95,13 @@ __global__ void __launch_bounds__(kBins) digit_scan_kernel(uint32_t *hist, int p
 }
 
 // look-back status word of (partition, digit), one array shared by the passes:
-// flag in bits 62-63, the pass (1-based) in bits 59-61, the count below; a word
-// of an earlier pass reads as not yet published
+// flag in bits 62-63, the pass (1-based, up to 8) in bits 58-61, the count
+// below; a word of an earlier pass reads as not yet published
 constexpr unsigned long long kFlagAgg = 1ull << 62;  // this partition's own count
 constexpr unsigned long long kFlagIncl = 2ull << 62; // count of all partitions up to this one
-constexpr unsigned long long kValueMask = (1ull << 59) - 1ull;
-__device__ __forceinline__ unsigned long long pass_tag(int ps) { return static_cast<unsigned long long>(ps + 1) << 59; }
+constexpr unsigned long long kTagMask = 15ull << 58;
+constexpr unsigned long long kValueMask = (1ull << 58) - 1ull;
+__device__ __forceinline__ unsigned long long pass_tag(int ps) { return static_cast<unsigned long long>(ps + 1) << 58; }
 
 struct ScatterSmem {
     uint32_t warp_cnt[kWarps][kBins];
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t *__re
             unsigned long long t0 = 0;
             for (int64_t q = part - 1; q >= 0;) {
                 const unsigned long long w = reinterpret_cast<volatile unsigned long long *>(status_words)[q * kBins + d];
-                if ((w & (kFlagAgg | kFlagIncl)) == 0 || (w & (7ull << 59)) != tag) {
+                if ((w & (kFlagAgg | kFlagIncl)) == 0 || (w & kTagMask) != tag) {
                     const unsigned long long now = global_ns();
                     if (t0 == 0) t0 = now;
                     else if (now - t0 > limit) {
