@@ -326,8 +326,9 @@ def tune_tile_height(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, 
     intersect, sort, render and, with upstream gradients, the adjoint) with
     16x16 and with 16x8 tiles (the latter exists for 1 <= top_k <= 8 without
     the low-pass filter) on the caller's frame: CUDA events on the stream,
-    one untimed run each, then `rounds` interleaved rounds of `reps` frames
-    per tile shape, keeping each shape's fastest round. Returns (opts with the
+    one untimed run each, the frame captured as a CUDA graph, then `rounds`
+    interleaved rounds of `reps` replays per tile shape, keeping each shape's
+    fastest round (not inside a stream capture). Returns (opts with the
     faster tile height, {tile height: ms per frame}). Both tile shapes give the
     same frame bit for bit; the launch shapes of each are tuned with
     Renderer.tune."""
@@ -339,32 +340,43 @@ def tune_tile_height(ctx, scene: DeviceScene, cams, opts, D=0, F_dtype=psi.F32, 
     gs = None
     if g_rgb is not None and grads is not None:
         gs = psi.PsiGrads(*(psi._ptr(grads[k]) for k in ("mu", "tu", "tv", "scale", "opacity", "rgb", "feat")))
-    runs = {}
+    # each frame is captured as one CUDA graph, so that the comparison is of the
+    # device work and not of the host's launch rate
+    graphs, keep = {}, []
+    cap = torch.cuda.Stream()
     for th in heights:
         o = copy.copy(opts)
         o.tile_h = th
         r = make_renderer(ctx, scene, cams, o, D=D, F_dtype=F_dtype)
 
-        def one(r=r):
-            r.frame(scene, stream=s)
+        def one(r=r, st=None):
+            r.frame(scene, stream=st)
             if g_rgb is not None:
                 if gs is not None:
-                    psi.psi_grads_zero(ctx, gs, scene.n, scene.D, s)
-                r.backward(scene, g_rgb, g_F, g_T, grads=grads, stream=s)
+                    psi.psi_grads_zero(ctx, gs, scene.n, scene.D, st)
+                r.backward(scene, g_rgb, g_F, g_T, grads=grads, stream=st)
         one()
-        runs[th] = one
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+            one(st=cap)
+        graphs[th] = g
+        keep.append(r)
     torch.cuda.synchronize()
     ms = {th: float("inf") for th in heights}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(rounds):
+    with torch.cuda.stream(s):
         for th in heights:
-            e0.record(s)
-            for _ in range(reps):
-                runs[th]()
-            e1.record(s)
-            torch.cuda.synchronize()
-            ms[th] = min(ms[th], e0.elapsed_time(e1) / reps)
-    del runs
+            graphs[th].replay()
+        for _ in range(rounds):
+            for th in heights:
+                e0.record(s)
+                for _ in range(reps):
+                    graphs[th].replay()
+                e1.record(s)
+                torch.cuda.synchronize()
+                ms[th] = min(ms[th], e0.elapsed_time(e1) / reps)
+    del graphs, keep
     best = min(ms, key=ms.get)
     o = copy.copy(opts)
     o.tile_h = best
