@@ -328,8 +328,8 @@ int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi
 /* ---- launch-shape autotuner for a4 and a5 (no counterpart in the paper) ---
  * The compositing kernels are compiled in PSI_RENDER_SHAPES launch shapes:
  * bit 0 of a shape builds the kernel for the other number of resident CTAs
- * per SM (top_k <= 8: forward 3 -> 4, adjoint 4 -> 3 with saved state and
- * 3 -> 4 without; larger K and dense features: 2 -> 1), i.e. registers per
+ * per SM (top_k <= 8: forward and adjoint 3 -> 4; larger K and dense
+ * features: 2 -> 1), i.e. registers per
  * thread against occupancy; bit 1 composites dense features
  * (top_k = 0, dim a multiple of 32) 16 channels per pass instead of 32;
  * bit 2 is the persistent launch: a few CTAs per SM, each taking tiles

@@ -664,12 +664,12 @@ constexpr int kOccTile8 = 5;
 template <int KMAX, int CH, bool SAVED, bool LP>
 cudaError_t launch_kcsl(const FrameParams &fp, const FeatView &f, const BwdArgs &a, bool alt, cudaStream_t st)
 {
-    // K <= 8: 4 CTAs per SM with the saved state (56 registers), 3 when pass A
-    // recomputes it; larger K (register Top-K of 16 or 32) and dense: 2 (the
-    // alternative shape: the other one of 3/4, resp. 1)
+    // K <= 8: 3 CTAs per SM (the 4-CTA build, 56 registers, spills in the
+    // per-record reductions), larger K (register Top-K of 16 or 32) and dense:
+    // 2 (the alternative shape: 4, resp. 1)
     constexpr bool small = KMAX > 0 && KMAX <= 8;
-    constexpr int occ = small ? (SAVED ? 4 : 3) : 2;
-    constexpr int occ_alt = small ? (SAVED ? 3 : 4) : 1;
+    constexpr int occ = small ? 3 : 2;
+    constexpr int occ_alt = small ? 4 : 1;
     return alt ? launch_kcslo<KMAX, CH, SAVED, LP, occ_alt>(fp, f, a, st)
                : launch_kcslo<KMAX, CH, SAVED, LP, occ>(fp, f, a, st);
 }
