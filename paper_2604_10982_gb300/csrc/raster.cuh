@@ -189,7 +189,6 @@ struct Pipe {
     float4 rec[kPS][kPB][kRecF4];
     uint32_t val[kPS][kPB];
     uint64_t full[kPS], ready[kPS], empty[kPS];
-    uint64_t gather[8]; // per pixel warp: bulk copies of its selected feature rows (forward)
     int alive;
     int abort;
 };
@@ -205,7 +204,6 @@ __device__ __forceinline__ void pipe_init(Pipe &P, int alive)
         mbar_init(&P.ready[s], 1);
         mbar_init(&P.empty[s], alive);
     }
-    for (int w = 0; w < 8; ++w) mbar_init(&P.gather[w], 1);
     P.alive = alive;
     P.abort = 0;
     fence_mbar_init();
@@ -220,8 +218,6 @@ __device__ __forceinline__ void pipe_inval(Pipe &P)
         asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.ready[s])) : "memory");
         asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.empty[s])) : "memory");
     }
-    for (int w = 0; w < 8; ++w)
-        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&P.gather[w])) : "memory");
 }
 
 // Grid of a persistent compositing launch: occ CTAs per SM, at most one per tile.
@@ -483,49 +479,6 @@ __device__ __forceinline__ void load_feat(const void *__restrict__ base, int64_t
 #pragma unroll
         for (int k = 0; k < CH / 16; ++k) {
             const uint4 v = __ldg(p + k);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const uint32_t byte = (w[h] >> (8 * b)) & 0xFFu;
-                    const uint32_t bits = ((byte & 0x80u) << 24) | ((byte & 0x7Fu) << 20);
-                    f[16 * k + 4 * h + b] = __uint_as_float(bits) * 0x1p120f;
-                }
-            }
-        }
-    }
-}
-
-// CH (16) channels [c0, c0+CH) of a feature row held in shared memory (a
-// staged copy of the global row, same encoding as load_feat).
-template <int DT, int CH>
-__device__ __forceinline__ void load_feat_smem(const unsigned char *row, int c0, float *f)
-{
-    if constexpr (DT == PSI_F32) {
-        const float4 *p = reinterpret_cast<const float4 *>(row + c0 * 4);
-#pragma unroll
-        for (int k = 0; k < CH / 4; ++k) {
-            const float4 v = p[k];
-            f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
-        }
-    } else if constexpr (DT == PSI_BF16) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(row + c0 * 2);
-#pragma unroll
-        for (int k = 0; k < CH / 8; ++k) {
-            const uint4 v = p[k];
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                f[8 * k + 2 * h] = __uint_as_float(w[h] << 16);
-                f[8 * k + 2 * h + 1] = __uint_as_float(w[h] & 0xFFFF0000u);
-            }
-        }
-    } else {
-        const uint4 *p = reinterpret_cast<const uint4 *>(row + c0);
-#pragma unroll
-        for (int k = 0; k < CH / 16; ++k) {
-            const uint4 v = p[k];
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {

@@ -43,12 +43,8 @@ struct FwdArgs {
 
 // One tile of the frame (the whole CTA; P freshly initialised by thread 0
 // below). TH: tile height (16x16 or 16x8 tiles).
-// per pixel warp: staging area of the selected feature rows (see fwd_tile)
-constexpr int kStageBytes = 2176;
-
 template <int KMAX, int DT, int CH, bool LP, int TH>
-__device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a, Pipe &P, unsigned char *gstage,
-                                         uint32_t tile)
+__device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a, Pipe &P, uint32_t tile)
 {
     constexpr int PW = pixel_warps(TH);
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -144,11 +140,11 @@ __device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a
             if (lane == 0) atomicSub(&P.alive, 1);
         }
     }
-    // warp-uniform from here on: the staged gather below uses warp collectives
-    if (__any_sync(0xffffffffu, vload(P.abort) != 0)) return;
+    if (vload(P.abort)) return;
+    if (!inside) return;
 
-    const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
-    if (inside && a.write_rgb) {
+    const int64_t pix = cam.pix_base + static_cast<int64_t>(py) * cam.W + px;
+    if (a.write_rgb) {
         a.rgb[pix] = cr;
         a.rgb[fp.n_pix_total + pix] = cg;
         a.rgb[2 * fp.n_pix_total + pix] = cb;
@@ -157,76 +153,28 @@ __device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a
     }
 
     if constexpr (KMAX == 0) {
-        if (inside && a.F && a.feat) store_feat<CH>(a.F, a.F_bf16 != 0, pix, a.D, a.c0, facc, a.fscale);
+        if (a.F && a.feat) store_feat<CH>(a.F, a.F_bf16 != 0, pix, a.D, a.c0, facc, a.fscale);
     } else {
         top.sort_by_pos();
         int32_t sid[KMAX];
 #pragma unroll
         for (int s = 0; s < KMAX; ++s)
-            sid[s] = (inside && top.valid(s, K))
-                         ? static_cast<int32_t>(static_cast<int64_t>(a.vals[list0 + top.p[s]]) - surf0)
-                         : -1;
-        if (inside && a.topk_ids) {
+            sid[s] = top.valid(s, K) ? static_cast<int32_t>(static_cast<int64_t>(a.vals[list0 + top.p[s]]) - surf0) : -1;
+        if (a.topk_ids) {
             int32_t *dst = a.topk_ids + pix * K;
 #pragma unroll
             for (int s = 0; s < KMAX; ++s)
                 if (s < K) dst[s] = sid[s];
         }
-        if (inside && a.topk_w) {
+        if (a.topk_w) {
             float *dst = a.topk_w + pix * K;
 #pragma unroll
             for (int s = 0; s < KMAX; ++s)
                 if (s < K) dst[s] = sid[s] >= 0 ? top.w[s] : 0.0f;
         }
         if ((a.F || a.argmax) && a.feat) {
-            // Stage the warp's most common selected rows in shared memory: the
-            // distinct ids are taken in increasing order (a warp minimum per
-            // round) up to the staging capacity, one bulk copy per row (lane k
-            // copies row k), completion on the warp's barrier. Neighbouring
-            // pixels select many of the same surfels, so a row shared by
-            // several lanes is read from global memory once. Rows past the
-            // capacity are read directly; every pixel still sums its slots in
-            // list order.
-            constexpr int esz = DT == PSI_F32 ? 4 : (DT == PSI_BF16 ? 2 : 1);
-            const int rowb = a.D * esz;
-            const int stride = rowb + 16; // 16-byte skew between rows: fewer bank conflicts
-            const int cap = min(32, kStageBytes / stride);
-            unsigned char *stage = gstage + static_cast<size_t>(wid) * kStageBytes;
-            int stg[KMAX];
-#pragma unroll
-            for (int s = 0; s < KMAX; ++s) stg[s] = -1;
-            int n_st = 0;
-            uint32_t my_row = 0xffffffffu; // the id lane k copies
-            while (n_st < cap) {
-                uint32_t mine = 0xffffffffu;
-#pragma unroll
-                for (int s = 0; s < KMAX; ++s)
-                    if (sid[s] >= 0 && stg[s] < 0) mine = min(mine, static_cast<uint32_t>(sid[s]));
-                const uint32_t cur = __reduce_min_sync(0xffffffffu, mine);
-                if (cur == 0xffffffffu) break;
-#pragma unroll
-                for (int s = 0; s < KMAX; ++s)
-                    if (static_cast<uint32_t>(sid[s]) == cur) stg[s] = n_st;
-                if (lane == n_st) my_row = cur;
-                ++n_st;
-            }
-            bool staged = false;
-            if (n_st > 0) {
-                const uint32_t par = 0; // one use of the barrier per tile
-                if (lane == 0) mbar_arrive_expect_tx(&P.gather[wid], static_cast<uint32_t>(n_st * rowb));
-                __syncwarp();
-                if (lane < n_st)
-                    bulk_g2s(stage + lane * stride,
-                             static_cast<const unsigned char *>(a.feat) + static_cast<size_t>(my_row) * rowb,
-                             static_cast<uint32_t>(rowb), &P.gather[wid]);
-                staged = __all_sync(0xffffffffu, mbar_wait(&P.gather[wid], par, a.status, kSiteRenderFwd));
-                if (!staged) {
-                    // let the copies land before the shared memory is released
-                    if (lane == 0) mbar_wait(&P.gather[wid], par, a.status, kSiteDrain);
-                    __syncwarp();
-                    return;
-                }
-            }
+            // 16 channels per chunk keeps the gather's registers low (one
+            // 32-byte BF16 row slice = two 16-byte loads per selected surfel)
             constexpr int CB = 16;
             float best = -__int_as_float(0x7f800000);
             int arg = 0;
@@ -238,14 +186,11 @@ __device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a
                 for (int s = 0; s < KMAX; ++s) {
                     if (sid[s] < 0) continue;
                     float f[CB];
-                    if (stg[s] >= 0)
-                        load_feat_smem<DT, CB>(stage + stg[s] * stride, c0, f);
-                    else
-                        load_feat<DT, CB>(a.feat, sid[s], a.D, c0, f, a.wide);
+                    load_feat<DT, CB>(a.feat, sid[s], a.D, c0, f, a.wide);
 #pragma unroll
                     for (int c = 0; c < CB; ++c) acc[c] = __fmaf_rn(top.w[s], f[c], acc[c]);
                 }
-                if (inside && a.F) store_feat<CB>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
+                if (a.F) store_feat<CB>(a.F, a.F_bf16 != 0, pix, a.D, c0, acc, a.fscale);
                 if (a.argmax) {
 #pragma unroll
                     for (int c = 0; c < CB; ++c) {
@@ -257,7 +202,7 @@ __device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a
                     }
                 }
             }
-            if (inside && a.argmax) a.argmax[pix] = (1.0f - T < 1e-4f) ? -1 : arg;
+            if (a.argmax) a.argmax[pix] = (1.0f - T < 1e-4f) ? -1 : arg;
         }
     }
 }
@@ -273,11 +218,10 @@ __global__ void __launch_bounds__(pipe_threads(TH), OCC)
     render_fwd_kernel(const __grid_constant__ FrameParams fp, FwdArgs a)
 {
     __shared__ __align__(128) Pipe P;
-    __shared__ __align__(128) unsigned char gstage[(KMAX > 0 ? pixel_warps(TH) : 1) * kStageBytes];
     __shared__ uint32_t s_next;
     uint32_t i = blockIdx.x;
     while (true) {
-        fwd_tile<KMAX, DT, CH, LP, TH>(fp, a, P, gstage, a.ranges[2 * fp.n_tiles_total + i]);
+        fwd_tile<KMAX, DT, CH, LP, TH>(fp, a, P, a.ranges[2 * fp.n_tiles_total + i]);
         if (!a.work) break;
         __syncthreads(); // every warp is done with this tile's pipeline
         if (threadIdx.x == 0) {
