@@ -140,12 +140,18 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t *__re
     uint32_t val[kItems];
     uint32_t rank[kItems];
     const uint32_t lt = (1u << lane) - 1u;
+    // all of the thread's loads first, so that they are in flight together
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         const int64_t idx = blk0 + wid * (32 * kItems) + i * 32 + lane;
         const bool ok = idx < n;
-        key[i] = ok ? keys_in[idx] : 0ull;
-        val[i] = ok ? vals_in[idx] : 0u;
+        key[i] = ok ? __ldcs(keys_in + idx) : 0ull;
+        val[i] = ok ? __ldcs(vals_in + idx) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const int64_t idx = blk0 + wid * (32 * kItems) + i * 32 + lane;
+        const bool ok = idx < n;
         const uint32_t d = ok ? static_cast<uint32_t>((key[i] >> shift) & mask) : (kBins + lane);
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = 0;
