@@ -46,7 +46,9 @@ enum psi_status {
     PSI_ERR_CUDA = 2,
     PSI_ERR_CAPACITY = 3,  /* device: more (tile, surfel) pairs than the key buffer holds */
     PSI_ERR_TIMEOUT = 4,   /* device: a bounded wait gave up (the results are invalid) */
-    PSI_ERR_UNSUPPORTED = 5
+    PSI_ERR_UNSUPPORTED = 5,
+    PSI_ERR_BOUNDS = 6     /* device, debug build only: an index taken from data failed a bounds
+                              check; the access was clamped to a valid one (results invalid) */
 };
 
 /* Tile-intersection modes (Sec. 5, "Precise Tile Intersection"):
@@ -164,9 +166,11 @@ void psi_ctx_destroy(psi_ctx *ctx);
 /* Message of the last failing call on ctx (never NULL; "" if none). */
 const char *psi_last_error(const psi_ctx *ctx);
 /* Synchronises `stream`, copies the device status word to *status_out
- * (0 = clean, else a PSI_ERR_* code; TIMEOUT before CAPACITY before
- * INVALID_ARG) and *detail (may be NULL): for PSI_ERR_CAPACITY the pair count
- * the overflowing frame needed, for PSI_ERR_TIMEOUT the code of the first wait
+ * (0 = clean, else a PSI_ERR_* code; TIMEOUT before BOUNDS before CAPACITY
+ * before INVALID_ARG) and *detail (may be NULL): for PSI_ERR_CAPACITY the pair
+ * count the overflowing frame needed, for PSI_ERR_BOUNDS 100 + the check site
+ * (1 tile of the launch order, 2 tile range, 3 record index of a list entry,
+ * 4 surfel id of a selected slot), for PSI_ERR_TIMEOUT the code of the first wait
  * that gave up (1 render, 2/3 adjoint passes, 4-6 decode, 7 drain,
  * 8 sort); then
  * clears the word. */
@@ -184,6 +188,14 @@ int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64
  * copy to the device: not inside a stream capture. */
 #define PSI_WAIT_LIMIT_MAX_NS 10000000000ull
 int psi_ctx_set_wait_limit_ns(psi_ctx *ctx, uint64_t ns);
+
+/* 1 if this library was built with PSI_DEBUG: every index the pipeline
+ * kernels take from data (the tile launch order, tile ranges, the record
+ * index of a list entry, the surfel ids of selected slots, the caller's saved
+ * Top-K ids) is checked against its buffer before use; a failure raises
+ * PSI_ERR_BOUNDS with the check site and the access is clamped to a valid
+ * index instead of faulting. 0 for the release build, which has no checks. */
+int psi_debug_checks(void);
 
 /* Kernels psi_ctx_time_kernel can bracket: those that share an entry point
  * with other kernels (psi_render_bwd launches the feature kernel, the list

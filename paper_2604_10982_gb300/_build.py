@@ -13,6 +13,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpsi.so")
+# the same sources compiled with PSI_DEBUG: bounds checks of the indices the
+# pipeline kernels take from data (see psi_debug_checks in psi.h)
+OUT_DEBUG = os.path.join(OUT, "debug")
+LIB_DEBUG = os.path.join(OUT, "libpsi_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "project.cu", "intersect.cu", "sort.cu", "render_fwd.cu", "render_bwd.cu", "feat_bwd.cu",
            "decode.cu", "labels.cu", "regularisers.cu", "frames.cu", "attention.cu", "geometry.cu", "quantize.cu"]
@@ -32,25 +36,27 @@ def _deps():
     return glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "psi.h")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, debug: bool = False) -> str:
+    """Build libpsi.so (or, with debug, libpsi_debug.so) if a source changed."""
+    lib, out = (LIB_DEBUG, OUT_DEBUG) if debug else (LIB, OUT)
+    if not force and not needs_build(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
-                     "--expt-relaxed-constexpr"]
+                     "--expt-relaxed-constexpr"] + (["-DPSI_DEBUG"] if debug else [])
     if ptxas_v:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        obj = os.path.join(out, src.replace(".cu", ".o"))
         cmd = [nvcc] + common + (["-fmad=false"] if src in NO_FMAD else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -63,13 +69,19 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
 
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> None:
+    """The release and the debug library, their translation units compiled in parallel."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        list(ex.map(lambda d: build(force=force, debug=d), (False, True)))
 
 
 if __name__ == "__main__":

@@ -197,16 +197,30 @@ int psi_status_fetch(psi_ctx *ctx, psi_stream stream, int32_t *status_out, int64
     e = cudaMemset(ctx->status, 0, psi::kDevStatusReportBytes);
     if (e != cudaSuccess) return cuda_fail(ctx, "psi_status_fetch", e);
     int code = PSI_OK;
-    // report the most severe: timeout, then capacity, then invalid argument
+    // report the most severe: timeout, then a failed bounds check (debug
+    // builds), then capacity, then invalid argument
     if (h.flags & (1 << PSI_ERR_TIMEOUT))
         code = PSI_ERR_TIMEOUT;
+    else if (h.flags & (1 << PSI_ERR_BOUNDS))
+        code = PSI_ERR_BOUNDS;
     else if (h.flags & (1 << PSI_ERR_CAPACITY))
         code = PSI_ERR_CAPACITY;
     else if (h.flags & (1 << PSI_ERR_INVALID_ARG))
         code = PSI_ERR_INVALID_ARG;
     *status_out = code;
-    if (detail) *detail = code == PSI_ERR_TIMEOUT ? static_cast<int64_t>(h.wait_site) : static_cast<int64_t>(h.required_pairs);
+    if (detail)
+        *detail = (code == PSI_ERR_TIMEOUT || code == PSI_ERR_BOUNDS) ? static_cast<int64_t>(h.wait_site)
+                                                                      : static_cast<int64_t>(h.required_pairs);
     return PSI_OK;
+}
+
+int psi_debug_checks(void)
+{
+#ifdef PSI_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 void psi_default_opts(psi_render_opts *o)

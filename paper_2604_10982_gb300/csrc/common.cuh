@@ -29,6 +29,25 @@ __device__ __forceinline__ void raise_status(DevStatus *st, int code)
     if (st) atomicOr(&st->flags, 1 << code);
 }
 
+// Bounds checks of the debug build (PSI_DEBUG): indices that come from data
+// are checked before use; a failure records 100 + the site in the status
+// word's site field, raises PSI_ERR_BOUNDS and the caller clamps the access.
+// The release build compiles the checks away.
+enum CheckSite { kChkTile = 1, kChkRange = 2, kChkRecord = 3, kChkFeatRow = 4 };
+#ifdef PSI_DEBUG
+__device__ __forceinline__ bool check_index(bool ok, int site, DevStatus *st)
+{
+    if (!ok && st) {
+        atomicCAS(&st->wait_site, 0, 100 + site);
+        raise_status(st, PSI_ERR_BOUNDS);
+    }
+    return ok;
+}
+#define PSI_CHECK(cond, site, st) ::psi::check_index((cond), (site), (st))
+#else
+#define PSI_CHECK(cond, site, st) true
+#endif
+
 // wait sites (reported by psi_status_fetch on PSI_ERR_TIMEOUT)
 enum WaitSite {
     kSiteRenderFwd = 1,
@@ -235,7 +254,7 @@ cudaError_t launch_render_fwd(const FrameParams &fp, const FeatView &f, const fl
 
 size_t render_bwd_workspace_bytes(int64_t n_records, int64_t n_pix, int top_k);
 cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int32_t *topk_ids, const float *topk_w,
-                            const float *g_F, float *kd, float *g_feat, cudaStream_t st);
+                            const float *g_F, float *kd, float *g_feat, DevStatus *status, cudaStream_t st);
 cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const FeatView &f, const float4 *records,
                               const uint32_t *vals, const uint32_t *ranges, const float *g_rgb, const float *g_F,
                               const float *g_T, const psi_fwd_out *saved, const psi_grads &g, void *ws,

@@ -29,6 +29,7 @@ struct FeatBwdArgs {
     const float *g_F;        // [P_total, D]
     float *kd;               // [P_total, K]
     float *g_feat;           // [N, D] or NULL
+    DevStatus *status;
 };
 
 template <int KMAX, int DT>
@@ -52,6 +53,8 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
 #pragma unroll
     for (int s = 0; s < KMAX; ++s) {
         id[s] = (inside && s < K) ? a.topk_ids[pix * K + s] : -1;
+        // debug builds: a saved id must be -1 or a surfel of the table
+        if (!PSI_CHECK(id[s] >= -1 && id[s] < fp.n, kChkFeatRow, a.status)) id[s] = -1;
         w[s] = id[s] >= 0 ? a.topk_w[pix * K + s] : 0.0f;
     }
 
@@ -169,7 +172,7 @@ cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FeatBwdArgs
 } // namespace
 
 cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int32_t *topk_ids, const float *topk_w,
-                            const float *g_F, float *kd, float *g_feat, cudaStream_t st)
+                            const float *g_F, float *kd, float *g_feat, DevStatus *status, cudaStream_t st)
 {
     if (fp.n_tiles_total == 0 || fp.top_k <= 0 || !f.data || !g_F) return cudaSuccess;
     FeatBwdArgs a{};
@@ -182,6 +185,7 @@ cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int3
     a.g_F = g_F;
     a.kd = kd;
     a.g_feat = g_feat;
+    a.status = status;
     if (fp.top_k <= 8) return launch_k<8>(fp, f, a, st);
     if (fp.top_k <= 16) return launch_k<16>(fp, f, a, st);
     return launch_k<32>(fp, f, a, st);

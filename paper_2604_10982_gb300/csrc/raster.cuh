@@ -274,8 +274,11 @@ __device__ __forceinline__ void transform_record(float4 *r, int tile_x0, int til
 // alive. Returns false on a timeout (status raised, abort set).
 __device__ __forceinline__ bool pipe_produce(Pipe &P, const uint32_t *__restrict__ vals, int64_t list0, int n,
                                              bool reverse, const float4 *__restrict__ records, int tile_x0,
-                                             int tile_y0, DevStatus *st, int site)
+                                             int tile_y0, DevStatus *st, int site, uint32_t rec_lo = 0,
+                                             uint32_t rec_hi = 0xffffffffu)
 {
+    (void)rec_lo;
+    (void)rec_hi;
     const int lane = threadIdx.x & 31;
     const int nb = (n + kPB - 1) / kPB;
     int issued = 0, done = 0; // batches issued / transformed
@@ -308,7 +311,12 @@ __device__ __forceinline__ bool pipe_produce(Pipe &P, const uint32_t *__restrict
             if (free_) {
                 int cnt;
                 const int lo = batch_range(issued, n, reverse, cnt);
-                for (int j = lane; j < cnt; j += 32) P.val[s][j] = vals[list0 + lo + j];
+                for (int j = lane; j < cnt; j += 32) {
+                    uint32_t r = vals[list0 + lo + j];
+                    // debug builds: a list entry must be a record of this tile's view
+                    if (!PSI_CHECK(r >= rec_lo && r < rec_hi, kChkRecord, st)) r = rec_lo;
+                    P.val[s][j] = r;
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive_expect_tx(&P.full[s], static_cast<uint32_t>(cnt) * (16u * kRecF4));
                 __syncwarp();

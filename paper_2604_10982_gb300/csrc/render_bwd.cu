@@ -162,8 +162,11 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
     const int local = static_cast<int>(tile - cam.tile_base);
     const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
     const int64_t list0 = a.ranges[2 * tile];
-    const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    if (!PSI_CHECK(a.ranges[2 * tile + 1] >= a.ranges[2 * tile], kChkRange, a.status)) n = 0;
     const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
+    const uint32_t rec_lo = static_cast<uint32_t>(surf0);
+    const uint32_t rec_hi = static_cast<uint32_t>(surf0 + fp.n);
     const int K = KMAX > 0 ? fp.top_k : 0;
     // a 16x8 tile plays the upper or lower half of its 16x16 tile (see the
     // forward kernel): same folded records, same per-pixel float32 sequence
@@ -198,7 +201,7 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
             last = a.saved_last[pix];
         }
     } else if (producer) {
-        pipe_produce(P, a.vals, list0, n, false, a.records, tileX, tileY, a.status, kSiteRenderBwdA);
+        pipe_produce(P, a.vals, list0, n, false, a.records, tileX, tileY, a.status, kSiteRenderBwdA, rec_lo, rec_hi);
     } else {
         const int nb = (n + kPB - 1) / kPB;
         bool wdone = __all_sync(0xffffffffu, done);
@@ -250,12 +253,18 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
             top.sort_by_pos();
 #pragma unroll
             for (int s = 0; s < KMAX; ++s)
+            {
                 kid[s] = (inside && top.valid(s, K))
                              ? static_cast<int>(static_cast<int64_t>(a.vals[list0 + top.p[s]]) - surf0)
                              : -1;
+                if (!PSI_CHECK(kid[s] >= -1 && kid[s] < fp.n, kChkFeatRow, a.status)) kid[s] = -1;
+            }
         } else {
 #pragma unroll
-            for (int s = 0; s < KMAX; ++s) kid[s] = (inside && s < K) ? a.saved_topk[pix * K + s] : -1;
+            for (int s = 0; s < KMAX; ++s) {
+                kid[s] = (inside && s < K) ? a.saved_topk[pix * K + s] : -1;
+                if (!PSI_CHECK(kid[s] >= -1 && kid[s] < fp.n, kChkFeatRow, a.status)) kid[s] = -1;
+            }
         }
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) kd[s] = 0.0f;
@@ -310,7 +319,8 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
     }
     const int maxlast = s_maxlast;
     if (producer) {
-        pipe_produce(P, a.vals, list0, maxlast, true, a.records, tileX, tileY, a.status, kSiteRenderBwdB);
+        pipe_produce(P, a.vals, list0, maxlast, true, a.records, tileX, tileY, a.status, kSiteRenderBwdB, rec_lo,
+                     rec_hi);
         return;
     }
     // entries at or beyond every lane's last composited surfel are skipped by the warp
@@ -509,7 +519,9 @@ __global__ void __launch_bounds__(pipe_threads(TH), OCC)
     __shared__ uint32_t s_next;
     uint32_t i = blockIdx.x;
     while (true) {
-        bwd_tile<KMAX, DT, CH, SAVED, LP, TH>(fp, a, P, s_maxlast, a.ranges[2 * fp.n_tiles_total + i]);
+        const uint32_t tile = a.ranges[2 * fp.n_tiles_total + i];
+        if (PSI_CHECK(tile < fp.n_tiles_total, kChkTile, a.status))
+            bwd_tile<KMAX, DT, CH, SAVED, LP, TH>(fp, a, P, s_maxlast, tile);
         if (!a.work) break;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -748,7 +760,7 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
             // feature terms from the saved selection: kd for the walk, dL/df
             float *kd = reinterpret_cast<float *>(static_cast<char *>(ws) + moments_bytes(R, lp));
             mark(PSI_KERNEL_BWD_FEAT, 0);
-            e = launch_feat_bwd(fp, f, saved->topk_ids, saved->topk_w, a.g_F, kd, a.g_feat, st);
+            e = launch_feat_bwd(fp, f, saved->topk_ids, saved->topk_w, a.g_F, kd, a.g_feat, status, st);
             if (e != cudaSuccess) return e;
             mark(PSI_KERNEL_BWD_FEAT, 1);
             a.kd_saved = kd;

@@ -53,8 +53,11 @@ __device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a
     const int local = static_cast<int>(tile - cam.tile_base);
     const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
     const int64_t list0 = a.ranges[2 * tile];
-    const int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    if (!PSI_CHECK(a.ranges[2 * tile + 1] >= a.ranges[2 * tile], kChkRange, a.status)) n = 0;
     const int nb = (n + kPB - 1) / kPB;
+    const uint32_t rec_lo = static_cast<uint32_t>(static_cast<int64_t>(v) * fp.n);
+    const uint32_t rec_hi = static_cast<uint32_t>(static_cast<int64_t>(v + 1) * fp.n);
 
     // A 16x8 tile is the upper or lower half of the 16x16 tile it lies in:
     // records are folded at that 16x16 tile's origin and its pixel warps play
@@ -65,7 +68,8 @@ __device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a
     if (tid == 0) pipe_init(P, PW);
     __syncthreads();
     if (wid == PW) {
-        pipe_produce(P, a.vals, list0, n, false, a.records, tx * kTile, ty * TH - oy, a.status, kSiteRenderFwd);
+        pipe_produce(P, a.vals, list0, n, false, a.records, tx * kTile, ty * TH - oy, a.status, kSiteRenderFwd,
+                     rec_lo, rec_hi);
         return;
     }
 
@@ -158,8 +162,10 @@ __device__ __forceinline__ void fwd_tile(const FrameParams &fp, const FwdArgs &a
         top.sort_by_pos();
         int32_t sid[KMAX];
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s)
+        for (int s = 0; s < KMAX; ++s) {
             sid[s] = top.valid(s, K) ? static_cast<int32_t>(static_cast<int64_t>(a.vals[list0 + top.p[s]]) - surf0) : -1;
+            if (!PSI_CHECK(sid[s] >= -1 && sid[s] < fp.n, kChkFeatRow, a.status)) sid[s] = -1;
+        }
         if (a.topk_ids) {
             int32_t *dst = a.topk_ids + pix * K;
 #pragma unroll
@@ -221,7 +227,9 @@ __global__ void __launch_bounds__(pipe_threads(TH), OCC)
     __shared__ uint32_t s_next;
     uint32_t i = blockIdx.x;
     while (true) {
-        fwd_tile<KMAX, DT, CH, LP, TH>(fp, a, P, a.ranges[2 * fp.n_tiles_total + i]);
+        const uint32_t tile = a.ranges[2 * fp.n_tiles_total + i];
+        // debug builds: the launch order must name a tile of the frame (uniform for the CTA)
+        if (PSI_CHECK(tile < fp.n_tiles_total, kChkTile, a.status)) fwd_tile<KMAX, DT, CH, LP, TH>(fp, a, P, tile);
         if (!a.work) break;
         __syncthreads(); // every warp is done with this tile's pipeline
         if (threadIdx.x == 0) {

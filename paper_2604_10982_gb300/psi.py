@@ -13,9 +13,10 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpsi.so")
+# PSI_LIBRARY=debug selects the bounds-checked build (libpsi_debug.so)
+LIB_PATH = os.path.join(HERE, "_build", "libpsi_debug.so" if os.environ.get("PSI_LIBRARY") == "debug" else "libpsi.so")
 
-PSI_OK, PSI_ERR_INVALID_ARG, PSI_ERR_CUDA, PSI_ERR_CAPACITY, PSI_ERR_TIMEOUT, PSI_ERR_UNSUPPORTED = range(6)
+PSI_OK, PSI_ERR_INVALID_ARG, PSI_ERR_CUDA, PSI_ERR_CAPACITY, PSI_ERR_TIMEOUT, PSI_ERR_UNSUPPORTED, PSI_ERR_BOUNDS = range(7)
 SPHERE, AABB, EXACT = 0, 1, 2
 F32, BF16, FP8_E4M3 = 0, 1, 2
 KERNEL_BWD_FEAT, KERNEL_BWD_WALK = 1, 2  # enum psi_kernel_id
@@ -99,6 +100,7 @@ def lib():
                                      ctypes.POINTER(PsiFwdOut), ctypes.POINTER(PsiGrads), _P, sz, _P]
         L.psi_ctx_time_kernel.argtypes = [_P, ctypes.c_int, _P, _P]
         L.psi_ctx_set_wait_limit_ns.argtypes = [_P, ctypes.c_uint64]
+        L.psi_debug_checks.argtypes = []
         L.psi_quantize_features.argtypes = [_P, _P, _i64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
         L.psi_grads_zero.argtypes = [_P, ctypes.POINTER(PsiGrads), _i64, ctypes.c_int, _P]
         L.psi_tune_render_fwd.argtypes = [_P, ctypes.POINTER(PsiFeatures), _P, _P, _P, ctypes.POINTER(PsiCamera),
