@@ -6,11 +6,12 @@
 // over the tile list:
 //     kd_j     = <gF, f_j>                 (enters s_j of the list walk)
 //     dL/df_j += omega_j gF                (summed over the pixels selecting j)
-// One CTA per tile, one thread per pixel (same pixel layout as the
+// One CTA per 16x16 tile, one thread per pixel (same pixel layout as the
 // compositing kernels). kd is written per (pixel, slot) for the list walk.
-// dL/df is aggregated per tile in shared memory (see the kernel), so that each
-// pixel's gF row is read once per 32-channel chunk rather than once per
-// selected surfel.
+// dL/df is aggregated per warp: the warp visits the distinct surfels its 32
+// pixels selected (ascending id), accumulates omega gF over the selecting
+// pixels with lanes across channels (coalesced gF rows), and adds the row to
+// dL/df with one 16-byte atomic per lane.
 #include "raster.cuh"
 
 namespace psi {
@@ -30,13 +31,6 @@ struct FeatBwdArgs {
     float *g_feat;           // [N, D] or NULL
     DevStatus *status;
 };
-
-// the shared accumulator of the dL/df pass: rows, the id table (power of two)
-constexpr int kAccRows = 128;
-constexpr int kHashBits = 11;
-constexpr int kHash = 1 << kHashBits;
-constexpr uint8_t kRowDirect = 0xFE; // past the accumulator: added to dL/df directly
-constexpr uint8_t kRowNone = 0xFF;   // empty slot
 
 template <int KMAX, int DT>
 __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
@@ -98,91 +92,68 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
         for (int s = 0; s < KMAX; ++s)
             if (s < K) a.kd[pix * K + s] = kd[s];
     }
-    if (!a.g_feat) return; // uniform over the CTA
+    if (!a.g_feat) return;
 
-    // dL/df_j += omega_j gF. The tile's distinct selected surfels get rows of
-    // a shared accumulator (ids hashed into a shared table, rows handed out
-    // in table order); per chunk of 32 channels each warp walks its 32 pixels
-    // with lanes across channels -- one coalesced read of each gF row chunk --
-    // and adds omega gF to the row of every surfel the pixel selected (shared
-    // atomics, conflict-free: lane = channel); the rows then go to dL/df with
-    // one coalesced atomic pass each. Surfels past the accumulator's rows (or
-    // a full table) are added to dL/df directly.
-    __shared__ int s_key[kHash];
-    __shared__ int s_row[kHash];
-    __shared__ int s_id[kAccRows];
-    __shared__ unsigned int s_n;
-    __shared__ float s_acc[kAccRows][32];
-    __shared__ uint8_t s_d[256][KMAX];
-    const int nthr = blockDim.x, wid = tid >> 5, nwarp = nthr >> 5;
-    for (int h = tid; h < kHash; h += nthr) s_key[h] = -1;
-    if (tid == 0) s_n = 0;
-    __syncthreads();
-    auto home = [](int id) { return static_cast<int>((static_cast<uint32_t>(id) * 2654435761u) >> (32 - kHashBits)); };
+    // dL/df_j += omega_j gF, one distinct surfel of the warp at a time
+    const int nv = a.D >> 2; // float4 chunks per row (D <= 256: lanes cover lane and lane + 32)
+    uint32_t used = 0;       // slots already added
+    while (true) {
+        uint32_t mine = 0xffffffffu;
 #pragma unroll
-    for (int s = 0; s < KMAX; ++s) {
-        if (id[s] < 0) continue;
-        int h = home(id[s]);
-        for (int probe = 0; probe < kHash; ++probe, h = (h + 1) & (kHash - 1)) {
-            const int prev = atomicCAS(&s_key[h], -1, id[s]);
-            if (prev == -1 || prev == id[s]) break;
-        }
-    }
-    __syncthreads();
-    for (int h = tid; h < kHash; h += nthr) {
-        const int k = s_key[h];
-        if (k >= 0) {
-            const unsigned int r = atomicAdd(&s_n, 1u);
-            s_row[h] = r < kAccRows ? static_cast<int>(r) : kRowDirect;
-            if (r < kAccRows) s_id[r] = k;
-        }
-    }
-    __syncthreads();
-    const int nrows = min(static_cast<int>(s_n), kAccRows);
+        for (int s = 0; s < KMAX; ++s)
+            if (id[s] >= 0 && !((used >> s) & 1u)) mine = min(mine, static_cast<uint32_t>(id[s]));
+        const uint32_t cur = __reduce_min_sync(0xffffffffu, mine);
+        if (cur == 0xffffffffu) break;
+        float wsel = 0.0f;
+        bool has = false;
 #pragma unroll
-    for (int s = 0; s < KMAX; ++s) {
-        uint8_t d = kRowNone;
-        if (id[s] >= 0) {
-            d = kRowDirect; // unless found below
-            int h = home(id[s]);
-            for (int probe = 0; probe < kHash; ++probe, h = (h + 1) & (kHash - 1)) {
-                const int k = s_key[h];
-                if (k == id[s]) {
-                    d = static_cast<uint8_t>(s_row[h]);
-                    break;
+        for (int s = 0; s < KMAX; ++s)
+            if (static_cast<uint32_t>(id[s]) == cur) { // ids are distinct within a pixel's set
+                wsel = w[s];
+                has = true;
+                used |= 1u << s;
+            }
+        uint32_t m = __ballot_sync(0xffffffffu, has);
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+        while (m) {
+            // up to four selecting pixels per round so their gF loads overlap
+            int Ls[4];
+            int nL = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                Ls[q] = m ? __ffs(m) - 1 : 0;
+                if (m) {
+                    m &= m - 1;
+                    ++nL;
                 }
-                if (k == -1) break;
             }
-        }
-        s_d[tid][s] = d;
-    }
-    __syncthreads();
-    for (int c0 = 0; c0 < a.D; c0 += 32) {
-        for (int k = tid; k < nrows * 32; k += nthr) (&s_acc[0][0])[k] = 0.0f;
-        __syncthreads();
-        const int c = c0 + lane;
-        const bool on = c < a.D;
-#pragma unroll 1
-        for (int q = 0; q < 32; ++q) {
-            const long long pq = __shfl_sync(0xffffffffu, static_cast<long long>(pix), q);
-            if (!__shfl_sync(0xffffffffu, inside, q)) continue;
-            const float g = on ? __ldg(a.g_F + pq * a.D + c) : 0.0f;
+            float wq[4];
+            float4 g0[4], g1[4];
 #pragma unroll
-            for (int s = 0; s < KMAX; ++s) {
-                const uint8_t d = s_d[wid * 32 + q][s];
-                const float wq = __shfl_sync(0xffffffffu, w[s], q);
-                const int iq = __shfl_sync(0xffffffffu, id[s], q);
-                if (d == kRowNone || !on) continue;
-                if (d < kAccRows)
-                    atomicAdd(&s_acc[d][lane], wq * g);
-                else
-                    atomicAdd(a.g_feat + static_cast<int64_t>(iq) * a.D + c, wq * g);
+            for (int q = 0; q < 4; ++q) {
+                const bool on = q < nL;
+                wq[q] = __shfl_sync(0xffffffffu, wsel, Ls[q]);
+                const long long pL = __shfl_sync(0xffffffffu, static_cast<long long>(pix), Ls[q]);
+                const float4 *row = reinterpret_cast<const float4 *>(a.g_F + pL * a.D);
+                g0[q] = (on && lane < nv) ? __ldg(row + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                g1[q] = (on && lane + 32 < nv) ? __ldg(row + lane + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!on) wq[q] = 0.0f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc0.x = fmaf(wq[q], g0[q].x, acc0.x);
+                acc0.y = fmaf(wq[q], g0[q].y, acc0.y);
+                acc0.z = fmaf(wq[q], g0[q].z, acc0.z);
+                acc0.w = fmaf(wq[q], g0[q].w, acc0.w);
+                acc1.x = fmaf(wq[q], g1[q].x, acc1.x);
+                acc1.y = fmaf(wq[q], g1[q].y, acc1.y);
+                acc1.z = fmaf(wq[q], g1[q].z, acc1.z);
+                acc1.w = fmaf(wq[q], g1[q].w, acc1.w);
             }
         }
-        __syncthreads();
-        for (int r = wid; r < nrows; r += nwarp)
-            if (on) atomicAdd(a.g_feat + static_cast<int64_t>(s_id[r]) * a.D + c, s_acc[r][lane]);
-        __syncthreads();
+        float4 *dst = reinterpret_cast<float4 *>(a.g_feat + static_cast<int64_t>(cur) * a.D);
+        if (lane < nv) atomicAdd(dst + lane, acc0);
+        if (lane + 32 < nv) atomicAdd(dst + lane + 32, acc1);
     }
 }
 
