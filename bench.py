@@ -144,25 +144,40 @@ def job_throughput(steps_per_rank: int, world: int, max_ms: float) -> float:
     return world * steps_per_rank / (max_ms / 1000.0)
 
 
-def roofline_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current sources of that kernel (its .cu file and the headers it
-    includes, hashed together in the listed order; else None)."""
+def roofline_traffic(kernel: str, pairs: float, view: str):
+    """DRAM bytes (read + write) of one launch of `kernel` on a frame with
+    `pairs` (tile, surfel) pairs, from the committed small-case ncu captures
+    (profiles/roofline_traffic.json): one launch captured at two surfel counts
+    of the same view gives a line, bytes = fixed + per_pair x pairs (the
+    per-pixel buffers make the fixed part, the records and list entries the
+    part that grows with the pairs), evaluated at this frame's pair count.
+    Returns (bytes, note), or (None, reason) unless the captures were taken on
+    the current sources of that kernel (its .cu file and the headers it
+    includes, hashed together in the listed order) and on a view of this size."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
-        return None
+        return None, "no committed captures"
     e = d.get(kernel)
     if not e:
-        return None
+        return None, f"no capture of {kernel}"
     h = hashlib.sha256()
     try:
         for name in e["sources"]:
             h.update(open(os.path.join(ROOT, "paper_2604_10982_gb300", "csrc", name), "rb").read())
     except (OSError, KeyError):
-        return None
-    return e["bytes_per_launch"] if h.hexdigest()[:16] == e.get("sha256_16") else None
+        return None, "sources missing"
+    if h.hexdigest()[:16] != e.get("sha256_16"):
+        return None, f"{kernel} changed since its capture"
+    if e.get("view") != view:
+        return None, f"captured on a {e.get('view')} view"
+    (p1, b1), (p2, b2) = [(pt["pairs"], pt["dram_read"] + pt["dram_write"]) for pt in e["points"][:2]]
+    per_pair = (b2 - b1) / (p2 - p1)
+    fixed = b1 - per_pair * p1
+    return fixed + per_pair * pairs, (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                                      f"{p1} and {p2} pairs ({e['view']}), fixed {fixed / 1e6:.1f} MB + "
+                                      f"{per_pair:.1f} B per pair at this frame's {pairs:.0f} pairs")
 
 
 def measured_peaks():
@@ -382,9 +397,10 @@ def run_psi(args):
         tuned = {"tile": f"16x{int(opts.tile_h)}", "frame_ms_per_tile_height": tile_ms,
                  "forward": {"ms_per_shape": [round(x, 4) for x in tr["fwd"][0]], "shape": tr["fwd"][1]},
                  "adjoint": {"ms_per_shape": [round(x, 4) for x in tr["bwd"][0]], "shape": tr["bwd"][1]},
-                 "shapes": "bit 0: the other CTAs-per-SM build (K<=8: 3<->4, else 2->1); bit 1: dense 16-channel passes; "
-                           "bit 2: persistent launch (tile counter); -1: shape does not apply; tile height and shapes "
-                           "timed on frame 0 before the graphs are captured"}
+                 "shapes": "bit 0: the other CTAs-per-SM build (K<=8: forward 3->4, adjoint from saved state 4->3, else 2->1); "
+                           "bit 1: dense 16-channel passes; bit 2: persistent launch (tile counter); bit 3: adjoint "
+                           "walk with two pixels per lane instead of one (saved state, K>0); -1: shape does not apply; "
+                           "tile height and shapes timed on frame 0 before the graphs are captured"}
     torch.cuda.synchronize()
     use_graph = not args.no_graph
     graphs = None
@@ -526,10 +542,13 @@ def run_psi(args):
 
     # ---- roofline of the dominant kernel
     mean_stage = stage.mean(0)
+    # the list walk's kernel: the paired form if the tuned adjoint shape has bit 3
+    walk_name = ("render_bwd_pair_kernel" if psi.psi_ctx_get_render_shape(ctx, 1, r.opts, psi.BF16, 1) & 8
+                 else "render_bwd_kernel")
     kernel_ms = {"render_fwd_kernel": float(mean_stage[names.index("render_fwd")]),
                  "decode_kernel": float(mean_stage[names.index("decode")]),
                  "feat_bwd_kernel": float(kern[:, 0].mean()),
-                 "render_bwd_kernel": float(kern[:, 1].mean())}
+                 walk_name: float(kern[:, 1].mean())}
     dom = max(kernel_ms, key=kernel_ms.get)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -541,7 +560,7 @@ def run_psi(args):
         flop = 20.0 * np.mean(nlast_sum) + 2.0 * K * D * np.mean(nonempty)
         roof = {"bound": "alu", "achieved": flop / launch_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                 "work": "20 FP32 flop per (pixel, list entry up to its last composited surfel) + 2KD per pixel"}
-    elif dom == "render_bwd_kernel":
+    elif dom == walk_name:
         flop = 40.0 * np.mean(nlast_sum)
         roof = {"bound": "alu", "achieved": flop / launch_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                 "work": "40 FP32 flop per (pixel, list entry up to its last composited surfel): twice the "
@@ -558,7 +577,8 @@ def run_psi(args):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["peak_source"] = ("measured HBM copy bandwidth (MEASURED_PEAKS.json)" if roof["bound"] == "hbm" else
                            f"derived: {n_sm} SMs (device) x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz")
-    roof["traffic"] = roofline_traffic(dom)
+    roof["traffic"], roof["traffic_source"] = roofline_traffic(dom, float(np.mean(pairs)),
+                                                              f"{cams[0].width}x{cams[0].height}")
     roof["launch_ms"] = kernel_ms[dom]
 
     # ---- end to end through the public API with host buffers: each step's

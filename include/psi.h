@@ -170,7 +170,8 @@ const char *psi_last_error(const psi_ctx *ctx);
  * before INVALID_ARG) and *detail (may be NULL): for PSI_ERR_CAPACITY the pair
  * count the overflowing frame needed, for PSI_ERR_BOUNDS 100 + the check site
  * (1 tile of the launch order, 2 tile range, 3 record index of a list entry,
- * 4 surfel id of a selected slot), for PSI_ERR_TIMEOUT the code of the first wait
+ * 4 surfel id of a selected slot, 5 a saved last position past its tile's
+ * list), for PSI_ERR_TIMEOUT the code of the first wait
  * that gave up (1 render, 2/3 adjoint passes, 4-6 decode, 7 drain,
  * 8 sort); then
  * clears the word. */
@@ -340,15 +341,18 @@ int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi
 /* ---- launch-shape autotuner for a4 and a5 (no counterpart in the paper) ---
  * The compositing kernels are compiled in PSI_RENDER_SHAPES launch shapes:
  * bit 0 of a shape builds the kernel for the other number of resident CTAs
- * per SM (top_k <= 8: forward and adjoint 3 -> 4; larger K and dense
- * features: 2 -> 1), i.e. registers per
+ * per SM (top_k <= 8: forward and recomputing adjoint 3 -> 4, adjoint from
+ * saved state 4 -> 3, its paired walk 4 -> 3; larger K and dense features:
+ * 2 -> 1), i.e. registers per
  * thread against occupancy; bit 1 composites dense features
  * (top_k = 0, dim a multiple of 32) 16 channels per pass instead of 32;
  * bit 2 is the persistent launch: a few CTAs per SM, each taking tiles
  * (of all views) longest list first from a work counter kept in the context
  * (the last CTA resets it, so compositing calls through one context must not
- * overlap on the GPU). With 16x8 tiles (psi_render_opts.tile_h = 8) the
- * kernels have one occupancy and bit 0 changes nothing.
+ * overlap on the GPU); bit 3 (adjoint from saved state with top_k > 0 only)
+ * walks the lists with two pixels per thread instead of one. With 16x8 tiles
+ * (psi_render_opts.tile_h = 8) the kernels have one occupancy and bit 0
+ * changes nothing.
  * Every shape computes the same result: the forward bit for bit, the adjoint
  * up to the order of its float32 atomic additions. Which one is fastest
  * depends on K, the feature dtype, the scene and the resolution, so it is
@@ -368,7 +372,7 @@ int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi
  * psi_ctx_set_render_shape / psi_ctx_get_render_shape write or read the
  * stored shape directly: which = 0 forward, 1 adjoint; feat_dtype a
  * psi_dtype, or -1 without features; saved 0/1 (adjoint only). */
-#define PSI_RENDER_SHAPES 8
+#define PSI_RENDER_SHAPES 16
 int psi_tune_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records, const uint32_t *vals,
                         const uint32_t *tile_ranges, const psi_camera *cams, int n_views, int64_t n_surfels,
                         const psi_render_opts *o, const psi_fwd_out *out, int reps, float *ms, int *best,

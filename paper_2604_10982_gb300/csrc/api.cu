@@ -381,8 +381,8 @@ uint8_t &bwd_shape(psi_ctx *ctx, const psi::FrameParams &fp, const psi::FeatView
 // then `reps` times between two events on the stream; ms[shape] = mean ms
 // (-1: shape does not exist), *best = the fastest.
 template <class Launch>
-int time_shapes(psi_ctx *ctx, int D, int K, int reps, cudaStream_t st, Launch launch, float *ms, int *best,
-                const char *who)
+int time_shapes(psi_ctx *ctx, int D, int K, bool pair_walk, int reps, cudaStream_t st, Launch launch, float *ms,
+                int *best, const char *who)
 {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
@@ -394,7 +394,7 @@ int time_shapes(psi_ctx *ctx, int D, int K, int reps, cudaStream_t st, Launch la
     int b = -1;
     for (int sh = 0; sh < psi::kShapes && e == cudaSuccess; ++sh) {
         ms[sh] = -1.0f;
-        if (!psi::render_shape_valid(D, K, sh)) continue;
+        if (!psi::render_shape_valid(D, K, sh, pair_walk)) continue;
         e = launch(sh);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch(sh);
@@ -526,7 +526,7 @@ int psi_tune_render_fwd(psi_ctx *ctx, const psi_features *f, const void *records
         return psi::launch_render_fwd(fp, fv, static_cast<const float4 *>(records), vals, tile_ranges, *out,
                                       ctx->status, st, shape);
     };
-    rc = time_shapes(ctx, fv.data ? fv.dim : 16, fp.top_k, reps, st, launch, ms, best, "psi_tune_render_fwd");
+    rc = time_shapes(ctx, fv.data ? fv.dim : 16, fp.top_k, false, reps, st, launch, ms, best, "psi_tune_render_fwd");
     if (rc) return rc;
     fwd_shape(ctx, fp, fv) = static_cast<uint8_t>(*best);
     return PSI_OK;
@@ -552,7 +552,8 @@ int psi_tune_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *
         return psi::launch_render_bwd(fp, *s, fv, static_cast<const float4 *>(records), vals, tile_ranges, g_rgb, g_F,
                                       g_T, saved, *grads, workspace, ctx->status, st, nullptr, shape);
     };
-    rc = time_shapes(ctx, fv.data ? fv.dim : 16, fp.top_k, reps, st, launch, ms, best, "psi_tune_render_bwd");
+    rc = time_shapes(ctx, fv.data ? fv.dim : 16, fp.top_k, saved != nullptr && fp.top_k > 0, reps, st, launch, ms, best,
+                     "psi_tune_render_bwd");
     if (rc) return rc;
     bwd_shape(ctx, fp, fv, saved != nullptr) = static_cast<uint8_t>(*best);
     // the gradient buffers served as scratch: leave them zeroed

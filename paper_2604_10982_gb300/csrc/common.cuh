@@ -33,7 +33,7 @@ __device__ __forceinline__ void raise_status(DevStatus *st, int code)
 // are checked before use; a failure records 100 + the site in the status
 // word's site field, raises PSI_ERR_BOUNDS and the caller clamps the access.
 // The release build compiles the checks away.
-enum CheckSite { kChkTile = 1, kChkRange = 2, kChkRecord = 3, kChkFeatRow = 4 };
+enum CheckSite { kChkTile = 1, kChkRange = 2, kChkRecord = 3, kChkFeatRow = 4, kChkLast = 5 };
 #ifdef PSI_DEBUG
 __device__ __forceinline__ bool check_index(bool ok, int site, DevStatus *st)
 {
@@ -229,22 +229,26 @@ struct FeatView {
 // the autotuner: bit 0 builds the kernel for the alternative number of CTAs
 // per SM (registers per thread against occupancy), bit 1 composites dense
 // features (K = 0) 16 channels per pass instead of 32, bit 2 launches the
-// persistent form (a few CTAs per SM fetching tiles from a counter). Every
-// shape computes the same result.
+// persistent form (a few CTAs per SM fetching tiles from a counter), bit 3
+// runs the adjoint's walk from saved state with a Top-K selection two pixels
+// per lane instead of one. Every shape computes the same result.
 constexpr int kShapeAltOcc = 1;
 constexpr int kShapeAltChunk = 2;
 constexpr int kShapePersistent = 4;
-constexpr int kShapes = 8;
+constexpr int kShapePairWalk = 8;
+constexpr int kShapes = 16;
 // channels per pass of the dense feature path for this shape
 inline int render_channel_chunk(int D, int K, int shape)
 {
     const int ch = (D % 32 == 0) ? 32 : 16;
     return (K == 0 && (shape & kShapeAltChunk)) ? 16 : ch;
 }
-// shapes that differ from shape 0 in something that exists for (D, K)
-inline bool render_shape_valid(int D, int K, int shape)
+// shapes that differ from shape 0 in something that exists for (D, K) and
+// the kernel (pair_walk: the adjoint from saved state with K > 0)
+inline bool render_shape_valid(int D, int K, int shape, bool pair_walk)
 {
     if (shape < 0 || shape >= kShapes) return false;
+    if ((shape & kShapePairWalk) && !pair_walk) return false;
     return !(shape & kShapeAltChunk) || (K == 0 && D % 32 == 0);
 }
 

@@ -6,12 +6,15 @@
 // over the tile list:
 //     kd_j     = <gF, f_j>                 (enters s_j of the list walk)
 //     dL/df_j += omega_j gF                (summed over the pixels selecting j)
-// One CTA per 16x16 tile, one thread per pixel (same pixel layout as the
-// compositing kernels). kd is written per (pixel, slot) for the list walk.
-// dL/df is aggregated per warp: the warp visits the distinct surfels its 32
-// pixels selected (ascending id), accumulates omega gF over the selecting
-// pixels with lanes across channels (coalesced gF rows), and adds the row to
-// dL/df with one 16-byte atomic per lane.
+// One CTA per 16x16 tile (16 x TH for other tile heights), one thread per
+// pixel (same pixel layout as the compositing kernels) for the bookkeeping;
+// the arithmetic runs with lanes across channels. Each warp visits the
+// distinct surfels its 32 pixels selected, in ascending id (every lane keeps
+// its set sorted by id, so its next surfel is always its first slot). For one
+// surfel the warp reads the feature row once and the gF row of each selecting
+// pixel once (both coalesced): the row feeds omega gF into the surfel's
+// dL/df (one 16-byte atomic per lane per surfel) and, through a cross-lane
+// sum, the pixel's kd.
 #include "raster.cuh"
 
 namespace psi {
@@ -23,7 +26,6 @@ struct FeatBwdArgs {
     const void *feat;
     const float *fscale;
     int D;
-    bool wide; // feature rows read 32 bytes at a time
     const int32_t *topk_ids; // [P_total, K]
     const float *topk_w;     // [P_total, K]
     const float *g_F;        // [P_total, D]
@@ -32,7 +34,60 @@ struct FeatBwdArgs {
     DevStatus *status;
 };
 
-template <int KMAX, int DT>
+// Sum 4 per-lane values over the warp (a transposing butterfly, 6 shuffles):
+// afterwards lane l holds the total of value index l >> 3.
+__device__ __forceinline__ float warp_transpose_sum4(float v[4], int lane)
+{
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[k] : v[k + 2];
+        const float keep = hi ? v[k + 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    {
+        const bool hi = lane & 8;
+        const float send = hi ? v[0] : v[1];
+        const float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 4);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
+// Four channels [c, c + 4) of feature row i as float32 (before the scale).
+template <int DT>
+__device__ __forceinline__ float4 load_feat4(const void *__restrict__ base, int64_t i, int D, int c)
+{
+    if constexpr (DT == PSI_F32) {
+        return __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(base) + i * D + c));
+    } else if constexpr (DT == PSI_BF16) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(static_cast<const __nv_bfloat16 *>(base) + i * D + c));
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u), __uint_as_float(u.y << 16),
+                           __uint_as_float(u.y & 0xFFFF0000u));
+    } else {
+        // FP8 E4M3: the 7 magnitude bits at float bits [20, 27), times 2^120
+        // (see load_feat)
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(static_cast<const uint8_t *>(base) + i * D + c));
+        float f[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t byte = (w >> (8 * b)) & 0xFFu;
+            f[b] = __uint_as_float(((byte & 0x80u) << 24) | ((byte & 0x7Fu) << 20)) * 0x1p120f;
+        }
+        return make_float4(f[0], f[1], f[2], f[3]);
+    }
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
+{
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
+}
+
+// NCH: 16-byte channel chunks per lane (1: D <= 128, 2: D <= 256).
+template <int KMAX, int DT, int NCH>
 __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
 {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -48,75 +103,78 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
     const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
     const int K = fp.top_k;
 
-    int id[KMAX];
+    // the pixel's selected set sorted by surfel id (empty slots: 0xffffffff,
+    // last), with each slot's weight and its index in the saved set
+    uint32_t id[KMAX];
     float w[KMAX];
+    int so[KMAX];
 #pragma unroll
     for (int s = 0; s < KMAX; ++s) {
-        id[s] = (inside && s < K) ? a.topk_ids[pix * K + s] : -1;
+        int i = (inside && s < K) ? a.topk_ids[pix * K + s] : -1;
         // debug builds: a saved id must be -1 or a surfel of the table
-        if (!PSI_CHECK(id[s] >= -1 && id[s] < fp.n, kChkFeatRow, a.status)) id[s] = -1;
-        w[s] = id[s] >= 0 ? a.topk_w[pix * K + s] : 0.0f;
+        if (!PSI_CHECK(i >= -1 && i < fp.n, kChkFeatRow, a.status)) i = -1;
+        id[s] = static_cast<uint32_t>(i);
+        w[s] = i >= 0 ? a.topk_w[pix * K + s] : 0.0f;
+        so[s] = s;
     }
-
-    // kd_j = <gF, f_j> (dequantised f: per-channel scale folded into gF)
-    if (inside) {
-        float kd[KMAX];
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) kd[s] = 0.0f;
-        for (int c0 = 0; c0 < a.D; c0 += 16) {
-            float g[16];
+    for (int round = 0; round < KMAX; ++round) {
 #pragma unroll
-            for (int c = 0; c < 16; c += 4) {
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(a.g_F + pix * a.D + c0 + c));
-                const float sc0 = a.fscale ? __ldg(a.fscale + c0 + c) : 1.0f;
-                const float sc1 = a.fscale ? __ldg(a.fscale + c0 + c + 1) : 1.0f;
-                const float sc2 = a.fscale ? __ldg(a.fscale + c0 + c + 2) : 1.0f;
-                const float sc3 = a.fscale ? __ldg(a.fscale + c0 + c + 3) : 1.0f;
-                g[c] = q.x * sc0;
-                g[c + 1] = q.y * sc1;
-                g[c + 2] = q.z * sc2;
-                g[c + 3] = q.w * sc3;
-            }
-#pragma unroll
-            for (int s = 0; s < KMAX; ++s) {
-                if (id[s] < 0) continue;
-                float f[16];
-                load_feat<DT, 16>(a.feat, id[s], a.D, c0, f, a.wide);
-                float acc = kd[s];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) acc = __fmaf_rn(g[c], f[c], acc);
-                kd[s] = acc;
+        for (int s = (round & 1); s + 1 < KMAX; s += 2) {
+            if (id[s] > id[s + 1]) {
+                const uint32_t ti = id[s];
+                id[s] = id[s + 1];
+                id[s + 1] = ti;
+                const float tw = w[s];
+                w[s] = w[s + 1];
+                w[s + 1] = tw;
+                const int ts = so[s];
+                so[s] = so[s + 1];
+                so[s + 1] = ts;
             }
         }
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s)
-            if (s < K) a.kd[pix * K + s] = kd[s];
     }
-    if (!a.g_feat) return;
 
-    // dL/df_j += omega_j gF, one distinct surfel of the warp at a time
-    const int nv = a.D >> 2; // float4 chunks per row (D <= 256: lanes cover lane and lane + 32)
-    uint32_t used = 0;       // slots already added
+    // lane l owns channels [4l, 4l + 4) and [4l + 128, 4l + 132) (D <= 256)
+    const int nv = a.D >> 2;
+    const bool c0on = lane < nv, c1on = NCH > 1 && lane + 32 < nv;
+    float4 sc0 = make_float4(1.f, 1.f, 1.f, 1.f), sc1 = sc0;
+    if (a.fscale) {
+        const float *p = a.fscale + 4 * lane; // the scale array has no alignment beyond 4 bytes
+        if (c0on) sc0 = make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+        if (c1on) sc1 = make_float4(__ldg(p + 128), __ldg(p + 129), __ldg(p + 130), __ldg(p + 131));
+    }
+    const unsigned lt = (1u << lane) - 1u; // lanes below this one
     while (true) {
-        uint32_t mine = 0xffffffffu;
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s)
-            if (id[s] >= 0 && !((used >> s) & 1u)) mine = min(mine, static_cast<uint32_t>(id[s]));
-        const uint32_t cur = __reduce_min_sync(0xffffffffu, mine);
+        const uint32_t cur = __reduce_min_sync(0xffffffffu, id[0]);
         if (cur == 0xffffffffu) break;
-        float wsel = 0.0f;
-        bool has = false;
+        const bool has = id[0] == cur; // ids are distinct within a pixel's set
+        const float wsel = w[0];
+        const int64_t kdi = pix * K + so[0];
+        if (has) {
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s)
-            if (static_cast<uint32_t>(id[s]) == cur) { // ids are distinct within a pixel's set
-                wsel = w[s];
-                has = true;
-                used |= 1u << s;
+            for (int s = 0; s + 1 < KMAX; ++s) {
+                id[s] = id[s + 1];
+                w[s] = w[s + 1];
+                so[s] = so[s + 1];
             }
+            id[KMAX - 1] = 0xffffffffu;
+        }
         uint32_t m = __ballot_sync(0xffffffffu, has);
+        // the surfel's feature row (dequantised), this lane's channels
+        float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
+        if (c0on) {
+            f0 = load_feat4<DT>(a.feat, cur, a.D, 4 * lane);
+            f0 = make_float4(f0.x * sc0.x, f0.y * sc0.y, f0.z * sc0.z, f0.w * sc0.w);
+        }
+        if (c1on) {
+            f1 = load_feat4<DT>(a.feat, cur, a.D, 4 * lane + 128);
+            f1 = make_float4(f1.x * sc1.x, f1.y * sc1.y, f1.z * sc1.z, f1.w * sc1.w);
+        }
         float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
         while (m) {
             // up to four selecting pixels per round so their gF loads overlap
+            const uint32_t before = m;
             int Ls[4];
             int nL = 0;
 #pragma unroll
@@ -127,17 +185,17 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
                     ++nL;
                 }
             }
-            float wq[4];
+            const uint32_t taken = before & ~m;
+            float wq[4], part[4];
             float4 g0[4], g1[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const bool on = q < nL;
-                wq[q] = __shfl_sync(0xffffffffu, wsel, Ls[q]);
+                wq[q] = on ? __shfl_sync(0xffffffffu, wsel, Ls[q]) : 0.0f;
                 const long long pL = __shfl_sync(0xffffffffu, static_cast<long long>(pix), Ls[q]);
                 const float4 *row = reinterpret_cast<const float4 *>(a.g_F + pL * a.D);
-                g0[q] = (on && lane < nv) ? __ldg(row + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
-                g1[q] = (on && lane + 32 < nv) ? __ldg(row + lane + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (!on) wq[q] = 0.0f;
+                g0[q] = (on && c0on) ? __ldg(row + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                g1[q] = (on && c1on) ? __ldg(row + lane + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -149,24 +207,38 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
                 acc1.y = fmaf(wq[q], g1[q].y, acc1.y);
                 acc1.z = fmaf(wq[q], g1[q].z, acc1.z);
                 acc1.w = fmaf(wq[q], g1[q].w, acc1.w);
+                part[q] = dot4(g1[q], f1, dot4(g0[q], f0, 0.0f));
             }
+            // kd of the round's pixels: lane 8q holds the q-th total
+            const float tot = warp_transpose_sum4(part, lane);
+            const int myq = min(__popc(taken & lt), 3);
+            const float mykd = __shfl_sync(0xffffffffu, tot, 8 * myq);
+            if ((taken >> lane) & 1u) a.kd[kdi] = mykd;
         }
-        float4 *dst = reinterpret_cast<float4 *>(a.g_feat + static_cast<int64_t>(cur) * a.D);
-        if (lane < nv) atomicAdd(dst + lane, acc0);
-        if (lane + 32 < nv) atomicAdd(dst + lane + 32, acc1);
+        if (a.g_feat) {
+            float4 *dst = reinterpret_cast<float4 *>(a.g_feat + static_cast<int64_t>(cur) * a.D);
+            if (c0on) atomicAdd(dst + lane, acc0);
+            if (c1on) atomicAdd(dst + lane + 32, acc1);
+        }
     }
+}
+
+template <int KMAX, int NCH>
+cudaError_t launch_kn(const FrameParams &fp, const FeatView &f, const FeatBwdArgs &a, cudaStream_t st)
+{
+    const unsigned grid = static_cast<unsigned>(fp.n_tiles_total);
+    switch (f.dtype) {
+    case PSI_BF16: feat_bwd_kernel<KMAX, PSI_BF16, NCH><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+    case PSI_FP8_E4M3: feat_bwd_kernel<KMAX, PSI_FP8_E4M3, NCH><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+    default: feat_bwd_kernel<KMAX, PSI_F32, NCH><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+    }
+    return cudaGetLastError();
 }
 
 template <int KMAX>
 cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FeatBwdArgs &a, cudaStream_t st)
 {
-    const unsigned grid = static_cast<unsigned>(fp.n_tiles_total);
-    switch (f.dtype) {
-    case PSI_BF16: feat_bwd_kernel<KMAX, PSI_BF16><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
-    case PSI_FP8_E4M3: feat_bwd_kernel<KMAX, PSI_FP8_E4M3><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
-    default: feat_bwd_kernel<KMAX, PSI_F32><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
-    }
-    return cudaGetLastError();
+    return f.dim > 128 ? launch_kn<KMAX, 2>(fp, f, a, st) : launch_kn<KMAX, 1>(fp, f, a, st);
 }
 
 } // namespace
@@ -177,7 +249,6 @@ cudaError_t launch_feat_bwd(const FrameParams &fp, const FeatView &f, const int3
     if (fp.n_tiles_total == 0 || fp.top_k <= 0 || !f.data || !g_F) return cudaSuccess;
     FeatBwdArgs a{};
     a.feat = f.data;
-    a.wide = feat_rows_wide(f.data, f.dim, f.dtype);
     a.fscale = f.scale;
     a.D = f.dim;
     a.topk_ids = topk_ids;

@@ -28,6 +28,8 @@
 // saturated, pass B back to front from the largest last-composited position
 // of the tile; a warp visits only the records that meet its 8x4 block, and in
 // pass B only those before the last surfel of one of its pixels.
+// With the forward's saved state and a Top-K selection, pass B also exists
+// in a form with two pixels per lane (bwd_tile_pair below; a launch shape).
 // A second kernel turns the per-record moments into gradients of mu, t_u,
 // t_v, s_u, s_v through the camera.
 #include "raster.cuh"
@@ -138,6 +140,58 @@ __device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
     return v[0];
 }
 
+// The saved Top-K set of one pixel met during pass B. The saved ids are in
+// list order, so walking back to front the next selected surfel the pixel
+// meets is always the last of its set not met yet: one compare per (record,
+// pixel). Keeps that id and its <gF, f>, the one after it (prefetched when
+// one is met, so its load has a whole stretch of the walk to land) and the
+// slot before that.
+struct SavedSel {
+    int nid, nnid, ptr;
+    float nkd, nnkd;
+
+    __device__ __forceinline__ void init(const BwdArgs &a, int64_t pix, int K, int64_t n_surf, bool on)
+    {
+        nid = nnid = ptr = -1;
+        nkd = nnkd = 0.0f;
+        if (!on || !a.kd_saved) return;
+        const int32_t *ids = a.saved_topk + pix * K;
+        const float *kds = a.kd_saved + pix * K;
+#pragma unroll 4
+        for (int s = 0; s < K; ++s) {
+            int id = ids[s];
+            // debug builds: a saved id must be -1 or a surfel of the table
+            if (!PSI_CHECK(id >= -1 && id < n_surf, kChkFeatRow, a.status)) id = -1;
+            if (id >= 0) {
+                nnid = nid;
+                nnkd = nkd;
+                nid = id;
+                nkd = kds[s];
+                ptr = s - 2;
+            }
+        }
+    }
+
+    // <gF, f_sid> if sid is the pixel's next selected surfel (then advance), else 0
+    __device__ __forceinline__ float match(const BwdArgs &a, int64_t pix, int K, int64_t n_surf, int sid)
+    {
+        if (sid != nid) return 0.0f;
+        const float dot = nkd;
+        nid = nnid;
+        nkd = nnkd;
+        nnid = -1;
+        nnkd = 0.0f;
+        if (ptr >= 0) {
+            int id = a.saved_topk[pix * K + ptr];
+            if (!PSI_CHECK(id >= -1 && id < n_surf, kChkFeatRow, a.status)) id = -1;
+            nnid = id;
+            nnkd = a.kd_saved[pix * K + ptr];
+        }
+        --ptr;
+        return dot;
+    }
+};
+
 // Up to this many contributing lanes add their values with their own 16-byte
 // vector reductions (3 or 4 per lane) instead of reducing over the warp first.
 constexpr int kDirectLanes = 4;
@@ -200,6 +254,9 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
             T = a.saved_T[pix];
             last = a.saved_last[pix];
         }
+        // a saved last position lies within the tile's list (it bounds the walk)
+        if (!PSI_CHECK(last >= 0 && last <= n, kChkLast, a.status)) last = 0;
+        last = min(max(last, 0), n);
     } else if (producer) {
         pipe_produce(P, a.vals, list0, n, false, a.records, tileX, tileY, a.status, kSiteRenderBwdA, rec_lo, rec_hi);
     } else {
@@ -248,6 +305,7 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
     // and <gF, f_j> for each selected surfel
     float kd[KMAX > 0 ? KMAX : 1];
     int kid[KMAX > 0 ? KMAX : 1];
+    SavedSel sel_saved; // the saved set (ext_feat), met in reverse list order
     if constexpr (KMAX > 0) {
         if constexpr (recompute) {
             top.sort_by_pos();
@@ -259,21 +317,11 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
                              : -1;
                 if (!PSI_CHECK(kid[s] >= -1 && kid[s] < fp.n, kChkFeatRow, a.status)) kid[s] = -1;
             }
-        } else {
-#pragma unroll
-            for (int s = 0; s < KMAX; ++s) {
-                kid[s] = (inside && s < K) ? a.saved_topk[pix * K + s] : -1;
-                if (!PSI_CHECK(kid[s] >= -1 && kid[s] < fp.n, kChkFeatRow, a.status)) kid[s] = -1;
-            }
         }
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) kd[s] = 0.0f;
         if (ext_feat) {
-            if (a.kd_saved && inside) {
-#pragma unroll
-                for (int s = 0; s < KMAX; ++s)
-                    if (s < K) kd[s] = a.kd_saved[pix * K + s];
-            }
+            sel_saved.init(a, pix, K, fp.n, inside);
         } else if (a.g_F && a.feat && inside) {
             for (int c0 = 0; c0 < a.D; c0 += 16) {
                 float g[16];
@@ -376,7 +424,9 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
                         const float Tj = Tc * inv;
                         w = e.alpha * Tj;
                         float dot = 0.0f;
-                        if constexpr (KMAX > 0) {
+                        if constexpr (ext_feat) {
+                            dot = sel_saved.match(a, pix, K, fp.n, static_cast<int>(sid));
+                        } else if constexpr (KMAX > 0) {
 #pragma unroll
                             for (int s = 0; s < KMAX; ++s)
                                 if (kid[s] == static_cast<int>(sid)) {
@@ -504,6 +554,231 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
             }
         }
         pipe_release(P, b);
+    }
+}
+
+// Pixel warps of the paired walk: one 8x8 block each (two pixels per lane).
+__host__ __device__ constexpr int pair_warps(int TH) { return TH / 4; }
+__host__ __device__ constexpr int pair_threads(int TH) { return 32 * (pair_warps(TH) + 1); }
+
+// Pass B from the forward's saved state with a Top-K selection (the feature
+// terms <gF, f_j> come from the per-pixel feature kernel): two pixels per
+// lane. A pixel warp covers an 8x8 block, rows ly and ly + 4 in each lane
+// (two of the 8x4 blocks of the record masks), so the per-record work that
+// does not depend on the pixel -- the staged record's loads, the vote, the
+// cross-lane reduction and its atomics -- is paid once for 64 pixels; a lane
+// adds its two pixels' values before the reduction.
+// The saved set is matched as in the one-pixel walk (SavedSel).
+template <bool LP, int TH>
+__device__ __forceinline__ void bwd_tile_pair(const FrameParams &fp, const BwdArgs &a, Pipe &P, int &s_maxlast,
+                                              uint32_t tile)
+{
+    constexpr int PW = pair_warps(TH);
+    constexpr int kM = moments_per_record(LP);
+    constexpr int kSums = LP ? 13 : 11; // colour (3), dL/do, moments
+    constexpr int kSlots = LP ? 16 : 12;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const bool producer = wid == PW;
+    const int v = view_of_tile(fp, tile);
+    const ViewParams &cam = fp.v[v];
+    const int local = static_cast<int>(tile - cam.tile_base);
+    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
+    const int64_t list0 = a.ranges[2 * tile];
+    int n = static_cast<int>(a.ranges[2 * tile + 1] - a.ranges[2 * tile]);
+    if (!PSI_CHECK(a.ranges[2 * tile + 1] >= a.ranges[2 * tile], kChkRange, a.status)) n = 0;
+    const int64_t surf0 = static_cast<int64_t>(v) * fp.n;
+    const uint32_t rec_lo = static_cast<uint32_t>(surf0);
+    const uint32_t rec_hi = static_cast<uint32_t>(surf0 + fp.n);
+    const int K = fp.top_k;
+    // a 16x8 tile plays the upper or lower half of its 16x16 tile (records are
+    // folded to the 16x16 origin, as in the forward kernel)
+    const int oy = (ty * TH) & 15;
+    const int tileX = tx * kTile, tileY = ty * TH - oy;
+    const int y0 = oy + 8 * (wid >> 1);        // first row of the warp's 8x8 block
+    const int blk = (y0 >> 2) * 2 + (wid & 1); // its upper 8x4 mask block; the lower one is blk + 2
+    const int lxi = (wid & 1) * 8 + (lane & 7);
+    const float lx = static_cast<float>(lxi);
+
+    if (tid == 0) {
+        pipe_init(P, PW);
+        s_maxlast = 0;
+    }
+    __syncthreads();
+
+    float ly[2], Tc[2], suffix[2], gr[2], gg[2], gb[2];
+    int last[2];
+    int64_t pix[2];
+    SavedSel sel[2]; // each pixel's saved set, met in reverse list order
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int lyi = y0 + (lane >> 3) + 4 * h;
+        ly[h] = static_cast<float>(lyi);
+        const int px = tileX + lxi, py = tileY + lyi;
+        const bool inside = !producer && px < cam.W && py < cam.H;
+        pix[h] = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
+        float T = 1.0f;
+        int l = 0;
+        if (inside) {
+            T = a.saved_T[pix[h]];
+            l = a.saved_last[pix[h]];
+        }
+        // a saved last position lies within the tile's list (it bounds the walk)
+        if (!PSI_CHECK(l >= 0 && l <= n, kChkLast, a.status)) l = 0;
+        last[h] = min(max(l, 0), n);
+        Tc[h] = T;
+        sel[h].init(a, pix[h], K, fp.n, inside);
+        gr[h] = inside ? a.g_rgb[pix[h]] : 0.0f;
+        gg[h] = inside ? a.g_rgb[fp.n_pix_total + pix[h]] : 0.0f;
+        gb[h] = inside ? a.g_rgb[2 * fp.n_pix_total + pix[h]] : 0.0f;
+        const float gt = (inside && a.g_T) ? a.g_T[pix[h]] : 0.0f;
+        suffix[h] = __fmul_rn(T, gt); // sum_{k>j} omega_k s_k + T_final gT
+    }
+    // entries at or beyond every pixel's last composited surfel are skipped by the warp
+    int warp_last = max(last[0], last[1]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
+    if (!producer && lane == 0 && warp_last > 0) atomicMax(&s_maxlast, warp_last);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+    if (producer) {
+        pipe_produce(P, a.vals, list0, maxlast, true, a.records, tileX, tileY, a.status, kSiteRenderBwdB, rec_lo,
+                     rec_hi);
+        return;
+    }
+
+    const int nbB = (maxlast + kPB - 1) / kPB;
+    for (int b = 0; b < nbB; ++b) {
+        if (!pipe_wait_ready(P, b, a.status, kSiteRenderBwdB)) break;
+        const int st = b % kPS;
+        int cnt;
+        const int lo = batch_range(b, maxlast, true, cnt);
+        const int limit = min(cnt, warp_last - lo); // entries [0, limit) of the batch can matter
+        if (limit > 0) {
+            uint32_t hw[kPB / 32];
+#pragma unroll
+            for (int q = 0; q < kPB / 32; ++q) {
+                const int j = q * 32 + lane;
+                hw[q] = __ballot_sync(0xffffffffu, j < cnt && ((__float_as_uint(P.rec[st][j][4].z) >> blk) & 5u));
+            }
+#pragma unroll 1
+            for (int q = kPB / 32 - 1; q >= 0; --q) {
+                uint32_t bits = q == 0 ? hw[0] : q == 1 ? hw[1] : q == 2 ? hw[2] : hw[3];
+                const int room = limit - q * 32;
+                if (room <= 0) continue;
+                if (room < 32) bits &= (1u << room) - 1u;
+#pragma unroll 1
+                for (; bits;) {
+                    const int jj = 31 - __clz(bits);
+                    bits &= ~(1u << jj);
+                    const int j = q * 32 + jj;
+                    const int pos = lo + j;
+                    const Rec r = load_rec(P.rec[st][j]);
+                    Eval e[2];
+                    bool act[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) act[h] = pos < last[h] && eval_alpha<LP>(r, lx, ly[h], e[h]);
+                    const uint32_t amask = __ballot_sync(0xffffffffu, act[0] || act[1]);
+                    if (!amask) continue;
+                    const uint32_t rid = P.val[st][j];
+                    const int sid = static_cast<int>(static_cast<int64_t>(rid) - surf0);
+                    const float4 col = P.rec[st][j][3];
+                    float vals[kSlots];
+#pragma unroll
+                    for (int k2 = 0; k2 < kSlots; ++k2) vals[k2] = 0.0f;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (!act[h]) continue;
+                        const float one_m = __fsub_rn(1.0f, e[h].alpha);
+                        const float inv = rcp_approx(one_m); // one_m >= 0.01
+                        const float Tj = Tc[h] * inv;
+                        const float w = e[h].alpha * Tj;
+                        const float dot = sel[h].match(a, pix[h], K, fp.n, sid);
+                        const float sj = gr[h] * col.y + gg[h] * col.z + gb[h] * col.w + dot;
+                        const float dLda = Tj * sj - suffix[h] * inv;
+                        suffix[h] = fmaf(w, sj, suffix[h]);
+                        Tc[h] = Tj;
+                        vals[0] += w * gr[h];
+                        vals[1] += w * gg[h];
+                        vals[2] += w * gb[h];
+                        if (LP && !e[h].clamped && e[h].filt) {
+                            // rho = 2 |x - p0|^2: dL/dp0 = (-a / 2)(-4 (x - p0))
+                            const float aa = dLda * e[h].alpha;
+                            vals[3] += dLda * e[h].G;
+                            vals[kSlots > 12 ? 11 : 0] += 2.0f * aa * e[h].dx;
+                            vals[kSlots > 12 ? 12 : 0] += 2.0f * aa * e[h].dy;
+                        } else if (!e[h].clamped) {
+                            const float rq = rcp_approx(e[h].q2);
+                            const float u = e[h].q0 * rq, vv = e[h].q1 * rq;
+                            const float d2 = u * u + vv * vv;
+                            const float aa = dLda * e[h].alpha;
+                            vals[3] += dLda * e[h].G;
+                            vals[4] += aa * u * u;
+                            vals[5] += aa * u * vv;
+                            vals[6] += aa * vv * vv;
+                            vals[7] += aa * u;
+                            vals[8] += aa * vv;
+                            vals[9] += aa * d2 * u;
+                            vals[10] += aa * d2 * vv;
+                        }
+                    }
+                    if (__popc(amask) <= kDirectLanes) {
+                        if (act[0] || act[1]) {
+                            float4 *dst = reinterpret_cast<float4 *>(a.moments + static_cast<int64_t>(rid) * kM);
+#pragma unroll
+                            for (int k4 = 0; k4 < kM / 4; ++k4)
+                                atomicAdd(dst + k4, make_float4(vals[4 * k4], vals[4 * k4 + 1], vals[4 * k4 + 2],
+                                                                vals[4 * k4 + 3]));
+                        }
+                    } else {
+                        float tot;
+                        int idx;
+                        bool mine;
+                        if constexpr (LP) {
+                            tot = warp_transpose_sum16(vals, lane);
+                            idx = (lane >> 1) & 15;
+                            mine = (lane & 1) == 0 && idx < kSums;
+                        } else {
+                            tot = warp_transpose_sum12(vals, lane);
+                            const int g = ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                            idx = ((lane >> 4) & 1) * 6 + ((lane >> 3) & 1) * 3 + g;
+                            mine = (lane & 1) == 0 && g < 3;
+                        }
+                        if (mine && tot != 0.0f) atomicAdd(a.moments + static_cast<int64_t>(rid) * kM + idx, tot);
+                    }
+                }
+            }
+        }
+        pipe_release(P, b);
+    }
+}
+
+template <bool LP, int OCC, int TH = 16>
+__global__ void __launch_bounds__(pair_threads(TH), OCC)
+    render_bwd_pair_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
+{
+    __shared__ __align__(128) Pipe P;
+    __shared__ int s_maxlast;
+    __shared__ uint32_t s_next;
+    uint32_t i = blockIdx.x;
+    while (true) {
+        const uint32_t tile = a.ranges[2 * fp.n_tiles_total + i];
+        if (PSI_CHECK(tile < fp.n_tiles_total, kChkTile, a.status)) bwd_tile_pair<LP, TH>(fp, a, P, s_maxlast, tile);
+        if (!a.work) break;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_next = vload(P.abort) ? 0xffffffffu : gridDim.x + atomicAdd(&a.work[0], 1u);
+            pipe_inval(P);
+        }
+        __syncthreads();
+        i = s_next;
+        if (i >= fp.n_tiles_total) break;
+    }
+    if (a.work && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.work[1], 1u) == gridDim.x - 1) {
+            a.work[0] = 0u;
+            a.work[1] = 0u;
+        }
     }
 }
 
@@ -676,14 +951,35 @@ constexpr int kOccTile8 = 5;
 template <int KMAX, int CH, bool SAVED, bool LP>
 cudaError_t launch_kcsl(const FrameParams &fp, const FeatView &f, const BwdArgs &a, bool alt, cudaStream_t st)
 {
-    // K <= 8: 3 CTAs per SM (the 4-CTA build, 56 registers, spills in the
-    // per-record reductions), larger K (register Top-K of 16 or 32) and dense:
-    // 2 (the alternative shape: 4, resp. 1)
+    // K <= 8: 3 CTAs per SM when pass A recomputes the Top-K set (the 4-CTA
+    // build spills in the per-record reductions), 4 from saved state (56
+    // registers, no Top-K in registers); larger K (register Top-K of 16 or
+    // 32) and dense: 2 (the alternative shape: 4 resp. 3, and 1)
     constexpr bool small = KMAX > 0 && KMAX <= 8;
-    constexpr int occ = small ? 3 : 2;
-    constexpr int occ_alt = small ? 4 : 1;
+    constexpr int occ = small ? (SAVED ? 4 : 3) : 2;
+    constexpr int occ_alt = small ? (SAVED ? 3 : 4) : 1;
     return alt ? launch_kcslo<KMAX, CH, SAVED, LP, occ_alt>(fp, f, a, st)
                : launch_kcslo<KMAX, CH, SAVED, LP, occ>(fp, f, a, st);
+}
+
+// Paired walk (saved state, Top-K): 4 pixel warps for a 16x16 tile, 2 for 16x8.
+template <bool LP, int OCC, int TH>
+cudaError_t launch_pair_o(const FrameParams &fp, const BwdArgs &a, cudaStream_t st)
+{
+    unsigned grid = fp.n_tiles_total;
+    if (a.work) grid = persistent_grid(fp.n_tiles_total, OCC);
+    render_bwd_pair_kernel<LP, OCC, TH><<<grid, pair_threads(TH), 0, st>>>(fp, a);
+    return cudaGetLastError();
+}
+
+constexpr int kOccPair = 4, kOccPairAlt = 3, kOccPair8 = 5; // 43 KB of shared memory per CTA
+
+cudaError_t launch_pair(const FrameParams &fp, const BwdArgs &a, bool alt, cudaStream_t st)
+{
+    if (fp.tile_h == 8) return launch_pair_o<false, kOccPair8, 8>(fp, a, st);
+    if (fp.lowpass)
+        return alt ? launch_pair_o<true, kOccPairAlt, 16>(fp, a, st) : launch_pair_o<true, kOccPair, 16>(fp, a, st);
+    return alt ? launch_pair_o<false, kOccPairAlt, 16>(fp, a, st) : launch_pair_o<false, kOccPair, 16>(fp, a, st);
 }
 
 template <int KMAX, int CH, bool SAVED>
@@ -771,7 +1067,9 @@ cudaError_t launch_render_bwd(const FrameParams &fp, const psi_surfels &s, const
     const bool alt = shape & kShapeAltOcc;
     a.work = (shape & kShapePersistent) ? status->work + 2 : nullptr;
     mark(PSI_KERNEL_BWD_WALK, 0);
-    if (fp.tile_h == 8)
+    if (a.saved_T && K > 0 && (shape & kShapePairWalk))
+        e = launch_pair(fp, a, alt, st);
+    else if (fp.tile_h == 8)
         e = a.saved_T ? launch_kcslo<8, 16, true, false, kOccTile8, 8>(fp, f, a, st)
                       : launch_kcslo<8, 16, false, false, kOccTile8, 8>(fp, f, a, st);
     else if (K == 0)

@@ -306,7 +306,7 @@ def psi_render_bwd(ctx, s, feats, records, vals, tile_ranges, cams_arr, n_views,
                                    workspace.numel() * workspace.element_size(), _stream(stream)), "psi_render_bwd")
 
 
-RENDER_SHAPES = 8
+RENDER_SHAPES = 16
 
 
 def psi_tune_render_fwd(ctx, feats, records, vals, tile_ranges, cams_arr, n_views, n_surfels, opts, out: PsiFwdOut,

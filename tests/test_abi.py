@@ -67,7 +67,7 @@ def test_render_shape_calls_check_arguments(lib):
     v = ctypes.c_int(-1)
     assert lib.psi_ctx_set_render_shape(None, 0, ctypes.byref(o), psi.F32, 0, 1) == psi.PSI_ERR_INVALID_ARG
     assert lib.psi_ctx_get_render_shape(None, 1, ctypes.byref(o), psi.F32, 1, ctypes.byref(v)) == psi.PSI_ERR_INVALID_ARG
-    assert psi.RENDER_SHAPES == 8
+    assert psi.RENDER_SHAPES == 16
 
 
 def test_context_creation_without_a_device_fails_cleanly(lib):

@@ -49,8 +49,8 @@ def _outputs(r):
     return outs
 
 
-def _valid(K, D=32):
-    return [s for s in range(8) if not (s & 2) or (K == 0 and D % 32 == 0)]
+def _valid(K, D=32, pair_walk=False):
+    return [s for s in range(16) if (not (s & 2) or (K == 0 and D % 32 == 0)) and (not (s & 8) or pair_walk)]
 
 
 @pytest.mark.parametrize("K,lowpass", [(0, False), (8, False), (16, False), (8, True)])
@@ -58,7 +58,7 @@ def test_every_shape_same_result(ctx, box, K, lowpass):
     from paper_2604_10982_gb300 import psi
     scene, r, (gC, gF, gT) = _setup(ctx, box, K, lowpass)
     ref_f, ref_g = None, None
-    for shape in _valid(K):
+    for shape in _valid(K, pair_walk=K > 0):
         for which, saved in ((0, 0), (1, 1), (1, 0)):
             psi.psi_ctx_set_render_shape(ctx, which, r.opts, psi.F32, saved, shape)
             assert psi.psi_ctx_get_render_shape(ctx, which, r.opts, psi.F32, saved) == shape
@@ -92,9 +92,9 @@ def test_tuner_stores_fastest_and_zeroes_grads(ctx, box, K):
     assert ctx.status_fetch()[0] == 0
     for which, key, saved in ((0, "fwd", 0), (1, "bwd", 1)):
         ms, best = rep[key]
-        valid = _valid(K)
+        valid = _valid(K, pair_walk=which == 1 and K > 0)
         assert best in valid
-        assert all(ms[s] > 0 for s in valid) and all(ms[s] == -1 for s in range(8) if s not in valid)
+        assert all(ms[s] > 0 for s in valid) and all(ms[s] == -1 for s in range(16) if s not in valid)
         assert ms[best] == min(ms[s] for s in valid)
         assert psi.psi_ctx_get_render_shape(ctx, which, r.opts, psi.F32, saved) == best
     for k in KEYS:

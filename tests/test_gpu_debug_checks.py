@@ -114,3 +114,19 @@ def test_bad_list_entry_is_caught(ctx):
     r.render(scene)
     st, site = ctx.status_fetch()
     assert st == psi.PSI_ERR_BOUNDS and site == 103, (st, site)
+
+
+def test_bad_saved_last_position_is_caught(ctx):
+    """A saved last-composited position past the end of its tile's list (it
+    bounds the adjoint's reverse walk)."""
+    if not _debug_loaded():
+        pytest.skip("needs the debug build (runs in the child process of the test above)")
+    from paper_2604_10982_gb300 import psi
+    w, scene, r = _frame(ctx)
+    r.n_last.view(-1)[777] = 1 << 20
+    P = r.n_pix
+    gC = torch.ones(3, P, device="cuda")
+    gF = torch.ones(P, 32, device="cuda")
+    r.backward(scene, gC, gF)
+    st, site = ctx.status_fetch()
+    assert st == psi.PSI_ERR_BOUNDS and site == 105, (st, site)
