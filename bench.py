@@ -421,9 +421,10 @@ def run_psi(args):
         torch.cuda.synchronize()
 
     # Two streams: the forward and the adjoint run in order on the main
-    # stream; gradient zeroing (needs nothing of the frame) and the decode
-    # (reads only forward outputs, as the adjoint does) run on a side stream
-    # and overlap them. The frame ends when both streams are done.
+    # stream; gradient zeroing (needs nothing of the frame; started beside
+    # the forward compositing) and the decode (reads only forward outputs, as
+    # the adjoint does) run on a side stream and overlap them. The frame ends
+    # when both streams are done.
     main_s = torch.cuda.current_stream(dev)
     side = torch.cuda.Stream(device=dev)
     zero_done = torch.cuda.Event()
@@ -441,15 +442,19 @@ def run_psi(args):
         fns = stage_fns(f)
         rec = (lambda name, s: evs[name].record(s)) if evs is not None else (lambda name, s: None)
         rec("start", main_s)
-        side.wait_stream(main_s)  # the previous frame's adjoint is done with the gradients
+        for n in ("project", "intersect", "sort"):
+            run_stage(f, n, fns)
+            rec(n, main_s)
+        # the zeroing (1.7 GB of gradient buffers) overlaps the compositing,
+        # which is issue-bound, rather than the HBM-bound binning and sort
+        side.wait_stream(main_s)  # also: the previous frame's adjoint is done with the gradients
         with torch.cuda.stream(side):
             rec("zero0", side)
             run_stage(f, "zero_grads", fns)
             rec("zero1", side)
             zero_done.record(side)
-        for n in ("project", "intersect", "sort", "render_fwd"):
-            run_stage(f, n, fns)
-            rec(n, main_s)
+        run_stage(f, "render_fwd", fns)
+        rec("render_fwd", main_s)
         side.wait_stream(main_s)  # decode after the forward
         with torch.cuda.stream(side):
             rec("dec0", side)

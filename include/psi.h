@@ -334,8 +334,8 @@ int psi_render_bwd(psi_ctx *ctx, const psi_surfels *s, const psi_features *f, co
                    psi_stream stream);
 
 /* Zero every non-NULL member of *grads ([n, 3], [n, 2], [n], [n, dim] floats
- * as laid out in psi_grads) on `stream` with asynchronous memsets, before an
- * accumulating psi_render_bwd. No counterpart in the paper. */
+ * as laid out in psi_grads; 4-byte aligned) on `stream` with one kernel,
+ * before an accumulating psi_render_bwd. No counterpart in the paper. */
 int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi_stream stream);
 
 /* ---- launch-shape autotuner for a4 and a5 (no counterpart in the paper) ---

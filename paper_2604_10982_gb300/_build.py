@@ -19,7 +19,7 @@ OUT_DEBUG = os.path.join(OUT, "debug")
 LIB_DEBUG = os.path.join(OUT, "libpsi_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "project.cu", "intersect.cu", "sort.cu", "render_fwd.cu", "render_bwd.cu", "feat_bwd.cu",
-           "decode.cu", "labels.cu", "regularisers.cu", "frames.cu", "attention.cu", "geometry.cu", "quantize.cu"]
+           "decode.cu", "labels.cu", "regularisers.cu", "frames.cu", "attention.cu", "geometry.cu", "quantize.cu", "fill.cu"]
 # the binning path takes integer decisions in float32 with an explicit
 # operation order: forbid FMA contraction there as well
 NO_FMAD = {"project.cu", "intersect.cu"}

@@ -742,15 +742,10 @@ int psi_grads_zero(psi_ctx *ctx, const psi_grads *grads, int64_t n, int dim, psi
     DeviceGuard g(ctx->device);
     auto st = reinterpret_cast<cudaStream_t>(stream);
     const size_t N = static_cast<size_t>(n);
-    struct { float *p; size_t w; } parts[] = {{grads->mu, 3},    {grads->tu, 3},      {grads->tv, 3},
-                                              {grads->scale, 2}, {grads->opacity, 1}, {grads->rgb, 3},
-                                              {grads->feat, static_cast<size_t>(dim)}};
-    for (const auto &pt : parts) {
-        if (!pt.p || pt.w == 0 || N == 0) continue;
-        cudaError_t e = cudaMemsetAsync(pt.p, 0, N * pt.w * sizeof(float), st);
-        if (e != cudaSuccess) return cuda_fail(ctx, "psi_grads_zero", e);
-    }
-    return PSI_OK;
+    float *const ptrs[] = {grads->mu, grads->tu, grads->tv, grads->scale, grads->opacity, grads->rgb, grads->feat};
+    const int64_t counts[] = {3 * n, 3 * n, 3 * n, 2 * n, n, 3 * n, static_cast<int64_t>(N) * dim};
+    cudaError_t e = psi::launch_zero_parts(ptrs, counts, 7, st);
+    return e == cudaSuccess ? PSI_OK : cuda_fail(ctx, "psi_grads_zero", e);
 }
 
 int psi_quat_frames(psi_ctx *ctx, const float *q, int64_t n, float *tu, float *tv, psi_stream stream)

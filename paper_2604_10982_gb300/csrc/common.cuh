@@ -273,6 +273,10 @@ cudaError_t launch_attention_bwd(const psi_surfels &s, const void *feat, int C, 
                                  float *gQ, float *gWQ, float *gWK, float *gWV, float *g_feat, float *g_mu, void *ws,
                                  DevStatus *status, cudaStream_t st, const char **why);
 cudaError_t launch_quantize(const float *f, int64_t n, int dim, int dtype, void *q, float *scale, cudaStream_t st);
+// fill.cu: zero up to kFillMaxParts float buffers (NULL or empty ones skipped)
+// with one small kernel (one CTA per SM)
+constexpr int kFillMaxParts = 8;
+cudaError_t launch_zero_parts(float *const *ptrs, const int64_t *counts, int n_parts, cudaStream_t st);
 cudaError_t launch_frames(const float *q, int64_t n, float *tu, float *tv, cudaStream_t st);
 cudaError_t launch_frames_bwd(const float *q, int64_t n, const float *g_tu, const float *g_tv, float *g_q,
                               cudaStream_t st);

@@ -86,9 +86,45 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
     return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
 }
 
+// Slot indices of a pixel's sorted set: KMAX <= 8 packs them as nibbles of
+// one word (fewer registers: four CTAs per SM fit), larger sets keep an array.
+template <int KMAX, bool PACK = (KMAX <= 8)>
+struct SlotOrder {
+    int so[KMAX];
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) so[s] = s;
+    }
+    __device__ __forceinline__ void swap(int s)
+    {
+        const int t = so[s];
+        so[s] = so[s + 1];
+        so[s + 1] = t;
+    }
+    __device__ __forceinline__ int first() const { return so[0]; }
+    __device__ __forceinline__ void pop()
+    {
+#pragma unroll
+        for (int s = 0; s + 1 < KMAX; ++s) so[s] = so[s + 1];
+    }
+};
+template <int KMAX>
+struct SlotOrder<KMAX, true> {
+    uint32_t so; // nibble s: the saved slot of sorted position s
+    __device__ __forceinline__ void init() { so = 0x76543210u; }
+    __device__ __forceinline__ void swap(int s)
+    {
+        const uint32_t x = ((so >> (4 * s)) ^ (so >> (4 * s + 4))) & 0xFu;
+        so ^= (x << (4 * s)) | (x << (4 * s + 4));
+    }
+    __device__ __forceinline__ int first() const { return static_cast<int>(so & 0xFu); }
+    __device__ __forceinline__ void pop() { so >>= 4; }
+};
+
 // NCH: 16-byte channel chunks per lane (1: D <= 128, 2: D <= 256).
 template <int KMAX, int DT, int NCH>
-__global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
+__global__ void __launch_bounds__(256, (KMAX <= 8 && NCH == 1) ? 4 : 1) feat_bwd_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t tile = blockIdx.x;
@@ -107,7 +143,8 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
     // last), with each slot's weight and its index in the saved set
     uint32_t id[KMAX];
     float w[KMAX];
-    int so[KMAX];
+    SlotOrder<KMAX> so;
+    so.init();
 #pragma unroll
     for (int s = 0; s < KMAX; ++s) {
         int i = (inside && s < K) ? a.topk_ids[pix * K + s] : -1;
@@ -115,7 +152,6 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
         if (!PSI_CHECK(i >= -1 && i < fp.n, kChkFeatRow, a.status)) i = -1;
         id[s] = static_cast<uint32_t>(i);
         w[s] = i >= 0 ? a.topk_w[pix * K + s] : 0.0f;
-        so[s] = s;
     }
 #pragma unroll
     for (int round = 0; round < KMAX; ++round) {
@@ -128,9 +164,7 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
                 const float tw = w[s];
                 w[s] = w[s + 1];
                 w[s + 1] = tw;
-                const int ts = so[s];
-                so[s] = so[s + 1];
-                so[s + 1] = ts;
+                so.swap(s);
             }
         }
     }
@@ -150,15 +184,15 @@ __global__ void __launch_bounds__(256) feat_bwd_kernel(const __grid_constant__ F
         if (cur == 0xffffffffu) break;
         const bool has = id[0] == cur; // ids are distinct within a pixel's set
         const float wsel = w[0];
-        const int64_t kdi = pix * K + so[0];
+        const int64_t kdi = pix * K + so.first();
         if (has) {
 #pragma unroll
             for (int s = 0; s + 1 < KMAX; ++s) {
                 id[s] = id[s + 1];
                 w[s] = w[s + 1];
-                so[s] = so[s + 1];
             }
             id[KMAX - 1] = 0xffffffffu;
+            so.pop();
         }
         uint32_t m = __ballot_sync(0xffffffffu, has);
         // the surfel's feature row (dequantised), this lane's channels
