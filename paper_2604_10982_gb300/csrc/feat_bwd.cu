@@ -122,28 +122,14 @@ struct SlotOrder<KMAX, true> {
     __device__ __forceinline__ void pop() { so >>= 4; }
 };
 
-// NCH: 16-byte channel chunks per lane (1: D <= 128, 2: D <= 256).
-template <int KMAX, int DT, int NCH>
-__global__ void __launch_bounds__(256, (KMAX <= 8 && NCH == 1) ? 4 : 1) feat_bwd_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
+// The pixel's saved set sorted by surfel id (odd-even transposition
+// network; empty slots hold 0xffffffff and sort last), with each slot's
+// weight and its index in the saved set.
+template <int KMAX>
+__device__ __forceinline__ void load_sorted_set(const FrameParams &fp, const FeatBwdArgs &a, bool inside, int64_t pix,
+                                                uint32_t id[KMAX], float w[KMAX], SlotOrder<KMAX> &so)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
-    const uint32_t tile = blockIdx.x;
-    const int v = view_of_tile(fp, tile);
-    const ViewParams &cam = fp.v[v];
-    const int local = static_cast<int>(tile - cam.tile_base);
-    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-    int lxi, lyi;
-    pixel_of_thread(tid, lxi, lyi);
-    const int px = tx * kTile + lxi, py = ty * fp.tile_h + lyi; // blockDim = 16 x tile height
-    const bool inside = px < cam.W && py < cam.H;
-    const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
     const int K = fp.top_k;
-
-    // the pixel's selected set sorted by surfel id (empty slots: 0xffffffff,
-    // last), with each slot's weight and its index in the saved set
-    uint32_t id[KMAX];
-    float w[KMAX];
-    SlotOrder<KMAX> so;
     so.init();
 #pragma unroll
     for (int s = 0; s < KMAX; ++s) {
@@ -168,6 +154,31 @@ __global__ void __launch_bounds__(256, (KMAX <= 8 && NCH == 1) ? 4 : 1) feat_bwd
             }
         }
     }
+}
+
+// NCH: 16-byte channel chunks per lane (1: D <= 128, 2: D <= 256).
+template <int KMAX, int DT, int NCH>
+__global__ void __launch_bounds__(256, (KMAX <= 8 && NCH == 1) ? 4 : 1) feat_bwd_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t tile = blockIdx.x;
+    const int v = view_of_tile(fp, tile);
+    const ViewParams &cam = fp.v[v];
+    const int local = static_cast<int>(tile - cam.tile_base);
+    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
+    int lxi, lyi;
+    pixel_of_thread(tid, lxi, lyi);
+    const int px = tx * kTile + lxi, py = ty * fp.tile_h + lyi; // blockDim = 16 x tile height
+    const bool inside = px < cam.W && py < cam.H;
+    const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
+    const int K = fp.top_k;
+
+    // the pixel's selected set sorted by surfel id (empty slots: 0xffffffff,
+    // last), with each slot's weight and its index in the saved set
+    uint32_t id[KMAX];
+    float w[KMAX];
+    SlotOrder<KMAX> so;
+    load_sorted_set<KMAX>(fp, a, inside, pix, id, w, so);
 
     // lane l owns channels [4l, 4l + 4) and [4l + 128, 4l + 132) (D <= 256)
     const int nv = a.D >> 2;
@@ -257,6 +268,104 @@ __global__ void __launch_bounds__(256, (KMAX <= 8 && NCH == 1) ? 4 : 1) feat_bwd
     }
 }
 
+// D <= 128 and K <= 8: the warp takes its 32 pixels in two passes of 16
+// (lanes 16h .. 16h + 15, the upper and lower half of its 8x4 block). A pass
+// first loads the g_F rows of its 16 pixels into registers (lanes across
+// channels: 16 float4 per lane, all loads in flight together), then visits
+// the distinct surfels its pixels selected in ascending id; per surfel only
+// the feature row is read (the next surfel's row is requested before the
+// current one is used). omega gF goes into the surfel's dL/df as above; the
+// 16 pixels' partial dots <gF, f> are summed by one transposing butterfly.
+// Against the per-surfel rounds above, no g_F row is read twice.
+template <int DT>
+__global__ void __launch_bounds__(256, 2) feat_bwd_reg_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
+{
+    constexpr int KMAX = 8;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t tile = blockIdx.x;
+    const int v = view_of_tile(fp, tile);
+    const ViewParams &cam = fp.v[v];
+    const int local = static_cast<int>(tile - cam.tile_base);
+    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
+    int lxi, lyi;
+    pixel_of_thread(tid, lxi, lyi);
+    const int px = tx * kTile + lxi, py = ty * fp.tile_h + lyi; // blockDim = 16 x tile height
+    const bool inside = px < cam.W && py < cam.H;
+    const int64_t pix = cam.pix_base + static_cast<int64_t>(min(py, cam.H - 1)) * cam.W + min(px, cam.W - 1);
+    const int K = fp.top_k;
+
+    uint32_t id[KMAX];
+    float w[KMAX];
+    SlotOrder<KMAX> so;
+    load_sorted_set<KMAX>(fp, a, inside, pix, id, w, so);
+
+    // lane l owns channels [4l, 4l + 4)
+    const bool con = lane < (a.D >> 2);
+    float4 sc = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (a.fscale && con) {
+        const float *p = a.fscale + 4 * lane; // the scale array has no alignment beyond 4 bytes
+        sc = make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+    }
+    auto feat_row = [&](uint32_t i) {
+        if (!con || i == 0xffffffffu) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 f = load_feat4<DT>(a.feat, i, a.D, 4 * lane);
+        return make_float4(f.x * sc.x, f.y * sc.y, f.z * sc.z, f.w * sc.w);
+    };
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const bool mine_pass = (lane >> 4) == h;
+        float4 G[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            const int src = 16 * h + p;
+            const long long pL = __shfl_sync(0xffffffffu, static_cast<long long>(pix), src);
+            const int inL = __shfl_sync(0xffffffffu, inside ? 1 : 0, src);
+            G[p] = (inL && con) ? __ldg(reinterpret_cast<const float4 *>(a.g_F + pL * a.D) + lane)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        uint32_t cur = __reduce_min_sync(0xffffffffu, mine_pass ? id[0] : 0xffffffffu);
+        float4 f = feat_row(cur);
+        while (cur != 0xffffffffu) {
+            const bool has = mine_pass && id[0] == cur; // ids are distinct within a pixel's set
+            const float wsel = w[0];
+            const long long kdi = static_cast<long long>(pix * K + so.first());
+            if (has) {
+#pragma unroll
+                for (int s = 0; s + 1 < KMAX; ++s) {
+                    id[s] = id[s + 1];
+                    w[s] = w[s + 1];
+                }
+                id[KMAX - 1] = 0xffffffffu;
+                so.pop();
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, has) >> (16 * h);
+            const uint32_t nxt = __reduce_min_sync(0xffffffffu, mine_pass ? id[0] : 0xffffffffu);
+            const float4 fn = feat_row(nxt);
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            float part[16];
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                part[p] = 0.0f;
+                if ((m >> p) & 1u) {
+                    const float wp = __shfl_sync(0xffffffffu, wsel, 16 * h + p);
+                    acc.x = fmaf(wp, G[p].x, acc.x);
+                    acc.y = fmaf(wp, G[p].y, acc.y);
+                    acc.z = fmaf(wp, G[p].z, acc.z);
+                    acc.w = fmaf(wp, G[p].w, acc.w);
+                    part[p] = dot4(G[p], f, 0.0f);
+                }
+            }
+            // lane l ends with the total of the pass's pixel l >> 1
+            const float tot = warp_transpose_sum16(part, lane);
+            const long long kdw = __shfl_sync(0xffffffffu, kdi, 16 * h + (lane >> 1));
+            if ((lane & 1) == 0 && ((m >> (lane >> 1)) & 1u)) a.kd[kdw] = tot;
+            if (a.g_feat && con) atomicAdd(reinterpret_cast<float4 *>(a.g_feat + static_cast<int64_t>(cur) * a.D) + lane, acc);
+            cur = nxt;
+            f = fn;
+        }
+    }
+}
+
 template <int KMAX, int NCH>
 cudaError_t launch_kn(const FrameParams &fp, const FeatView &f, const FeatBwdArgs &a, cudaStream_t st)
 {
@@ -272,6 +381,15 @@ cudaError_t launch_kn(const FrameParams &fp, const FeatView &f, const FeatBwdArg
 template <int KMAX>
 cudaError_t launch_k(const FrameParams &fp, const FeatView &f, const FeatBwdArgs &a, cudaStream_t st)
 {
+    if (KMAX == 8 && f.dim <= 128) {
+        const unsigned grid = static_cast<unsigned>(fp.n_tiles_total);
+        switch (f.dtype) {
+        case PSI_BF16: feat_bwd_reg_kernel<PSI_BF16><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+        case PSI_FP8_E4M3: feat_bwd_reg_kernel<PSI_FP8_E4M3><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+        default: feat_bwd_reg_kernel<PSI_F32><<<grid, 16 * fp.tile_h, 0, st>>>(fp, a); break;
+        }
+        return cudaGetLastError();
+    }
     return f.dim > 128 ? launch_kn<KMAX, 2>(fp, f, a, st) : launch_kn<KMAX, 1>(fp, f, a, st);
 }
 

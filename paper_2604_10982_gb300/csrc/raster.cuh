@@ -528,5 +528,42 @@ __device__ __forceinline__ void store_feat(void *F, bool bf16, int64_t pix, int 
     }
 }
 
+// ------------------------------------------------------------ warp sums
+// Sum 16 per-lane values over the warp (transposing butterfly, 16 shuffles):
+// afterwards lane l (and l ^ 1) holds the total of value index
+// 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l).
+__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane)
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[k] : v[k + 8];
+        const float keep = hi ? v[k + 8] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[k] : v[k + 4];
+        const float keep = hi ? v[k + 4] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool hi = lane & 4;
+        const float send = hi ? v[k] : v[k + 2];
+        const float keep = hi ? v[k + 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1];
+        const float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
 } // namespace raster
 } // namespace psi
