@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=6)
     ap.add_argument("--ablation-frames", type=int, default=6, help="frames per Table-3 row (0: skip)")
     ap.add_argument("--label-frames", type=int, default=8, help="frames of the instance-label path (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=10, help="replays of the 16-view batch graph (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -547,12 +547,14 @@ def run_psi(args):
 
     # ---- roofline of the dominant kernel
     mean_stage = stage.mean(0)
+    # the feature kernel: the register-resident form for K <= 8 and D <= 128
+    feat_name = "feat_bwd_reg_kernel" if (K <= 8 and D <= 128) else "feat_bwd_kernel"
     # the list walk's kernel: the paired form if the tuned adjoint shape has bit 3
     walk_name = ("render_bwd_pair_kernel" if psi.psi_ctx_get_render_shape(ctx, 1, r.opts, psi.BF16, 1) & 8
                  else "render_bwd_kernel")
     kernel_ms = {"render_fwd_kernel": float(mean_stage[names.index("render_fwd")]),
                  "decode_kernel": float(mean_stage[names.index("decode")]),
-                 "feat_bwd_kernel": float(kern[:, 0].mean()),
+                 feat_name: float(kern[:, 0].mean()),
                  walk_name: float(kern[:, 1].mean())}
     dom = max(kernel_ms, key=kernel_ms.get)
     peaks = measured_peaks()
@@ -570,7 +572,7 @@ def run_psi(args):
         roof = {"bound": "alu", "achieved": flop / launch_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                 "work": "40 FP32 flop per (pixel, list entry up to its last composited surfel): twice the "
                         "forward's 20 (the adjoint of the alpha evaluation and blend)"}
-    elif dom == "feat_bwd_kernel":
+    elif dom == feat_name:
         byts = r.n_pix * (4.0 * D + 12.0 * K) + np.mean(uniq_sel) * (2.0 * D + 8.0 * D)
         roof = {"bound": "hbm", "achieved": byts / launch_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "work": "per pixel gF row + K ids, weights, dots; per selected surfel its BF16 row and dL/df row read+write"}

@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(256, (KMAX <= 8 && NCH == 1) ? 4 : 1) feat_bwd
 // the distinct surfels its pixels selected in ascending id; per surfel only
 // the feature row is read (the next surfel's row is requested before the
 // current one is used). omega gF goes into the surfel's dL/df as above; the
-// 16 pixels' partial dots <gF, f> are summed by one transposing butterfly.
+// 16 pixels' partial dots <gF, f> are summed by one transposing butterfly
+// (one per half-row holding a selecting pixel measured slower).
 // Against the per-surfel rounds above, no g_F row is read twice.
 template <int DT>
 __global__ void __launch_bounds__(256, 2) feat_bwd_reg_kernel(const __grid_constant__ FrameParams fp, FeatBwdArgs a)
