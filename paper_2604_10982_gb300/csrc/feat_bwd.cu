@@ -57,35 +57,6 @@ __device__ __forceinline__ float warp_transpose_sum4(float v[4], int lane)
     return v[0];
 }
 
-// Four channels [c, c + 4) of feature row i as float32 (before the scale).
-template <int DT>
-__device__ __forceinline__ float4 load_feat4(const void *__restrict__ base, int64_t i, int D, int c)
-{
-    if constexpr (DT == PSI_F32) {
-        return __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(base) + i * D + c));
-    } else if constexpr (DT == PSI_BF16) {
-        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(static_cast<const __nv_bfloat16 *>(base) + i * D + c));
-        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u), __uint_as_float(u.y << 16),
-                           __uint_as_float(u.y & 0xFFFF0000u));
-    } else {
-        // FP8 E4M3: the 7 magnitude bits at float bits [20, 27), times 2^120
-        // (see load_feat)
-        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(static_cast<const uint8_t *>(base) + i * D + c));
-        float f[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint32_t byte = (w >> (8 * b)) & 0xFFu;
-            f[b] = __uint_as_float(((byte & 0x80u) << 24) | ((byte & 0x7Fu) << 20)) * 0x1p120f;
-        }
-        return make_float4(f[0], f[1], f[2], f[3]);
-    }
-}
-
-__device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
-{
-    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
-}
-
 // Slot indices of a pixel's sorted set: KMAX <= 8 packs them as nibbles of
 // one word (fewer registers: four CTAs per SM fit), larger sets keep an array.
 template <int KMAX, bool PACK = (KMAX <= 8)>
