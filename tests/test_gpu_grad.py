@@ -132,6 +132,17 @@ def test_grad_quantised_features_d128(ctx, dtype):
     _grad_compare(ctx, w, multi_cams()[:2], o, 128, feat_dtype=psi.BF16 if dtype == "bf16" else psi.FP8_E4M3)
 
 
+@pytest.mark.parametrize("K,D,dtype", [(16, 64, "bf16"), (8, 256, "bf16"), (32, 48, "fp8")])
+def test_grad_feature_kernel_forms(ctx, K, D, dtype):
+    """The feature adjoint outside its register-resident form (K > 8 or
+    D > 128: every selecting pixel's g_F row read per surfel, two channel
+    chunks per lane at D = 256), against the oracle."""
+    from paper_2604_10982_gb300 import psi
+    w = sg.dense_box(n=3000, d=D)
+    o = orc.Opts(mode=orc.EXACT, top_k=K, opacity_radius=True)
+    _grad_compare(ctx, w, multi_cams()[:2], o, D, feat_dtype=psi.BF16 if dtype == "bf16" else psi.FP8_E4M3)
+
+
 def test_grad_rgb_only(ctx):
     w = sg.dense_box(n=3000, d=16)
     o = orc.Opts(mode=orc.SPHERE, top_k=0)

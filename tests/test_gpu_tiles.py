@@ -112,3 +112,31 @@ def test_tile16x8_rejects_dense_and_lowpass(ctx, box):
         with pytest.raises(psi.PsiError):
             r = pl.Renderer(ctx, scene.n, cams, opts_of(o), 1024)
             r.project(scene)
+
+
+def test_tile16x8_paired_walk_equals_single(ctx):
+    """16x8 tiles with the adjoint's paired walk (launch shape bit 3, two
+    pixel warps of 8x8 blocks per tile), alone and persistent: the same
+    gradients as the one-pixel walk up to the order of float32 atomics."""
+    from paper_2604_10982_gb300 import pipeline as pl, psi
+    w = sg.dense_box(n=4000, d=32)
+    cams = multi_cams()
+    o = orc.Opts(mode=orc.EXACT, top_k=8, opacity_radius=True, tile_h=8)
+    scene = pl.DeviceScene(w.surfels, w.features, feat_dtype=psi.BF16)
+    r = pl.make_renderer(ctx, scene, cams, opts_of(o), D=32)
+    r.frame(scene)
+    P = r.n_pix
+    g = torch.Generator(device="cpu").manual_seed(7)
+    gC, gF, gT = torch.randn(3, P, generator=g).cuda(), torch.randn(P, 32, generator=g).cuda(), torch.randn(P, generator=g).cuda()
+    out = {}
+    for shape in (0, 8, 12):
+        psi.psi_ctx_set_render_shape(ctx, 1, r.opts, psi.BF16, 1, shape)
+        out[shape] = r.backward(scene, gC, gF, gT)
+        torch.cuda.synchronize()
+        assert ctx.status_fetch()[0] == 0
+    psi.psi_ctx_set_render_shape(ctx, 1, r.opts, psi.BF16, 1, 0)
+    for shape in (8, 12):
+        for k, ref in out[0].items():
+            a, b = out[shape][k].double(), ref.double()
+            assert torch.count_nonzero(b).item() > 0, k
+            assert torch.linalg.norm(a - b).item() <= 1e-5 * torch.linalg.norm(b).item(), (shape, k)
