@@ -320,11 +320,14 @@ __global__ void __launch_bounds__(256, 2) feat_bwd_reg_kernel(const __grid_const
                 part[p] = 0.0f;
                 if ((m >> p) & 1u) {
                     const float wp = __shfl_sync(0xffffffffu, wsel, 16 * h + p);
-                    acc.x = fmaf(wp, G[p].x, acc.x);
-                    acc.y = fmaf(wp, G[p].y, acc.y);
-                    acc.z = fmaf(wp, G[p].z, acc.z);
-                    acc.w = fmaf(wp, G[p].w, acc.w);
-                    part[p] = dot4(G[p], f, 0.0f);
+                    // packed FMAs, two channels each
+                    const float2 w2 = make_float2(wp, wp);
+                    const float2 lo = __ffma2_rn(w2, make_float2(G[p].x, G[p].y), make_float2(acc.x, acc.y));
+                    const float2 hi = __ffma2_rn(w2, make_float2(G[p].z, G[p].w), make_float2(acc.z, acc.w));
+                    acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    const float2 d = __ffma2_rn(make_float2(G[p].z, G[p].w), make_float2(f.z, f.w),
+                                                __fmul2_rn(make_float2(G[p].x, G[p].y), make_float2(f.x, f.y)));
+                    part[p] = d.x + d.y;
                 }
             }
             // lane l ends with the total of the pass's pixel l >> 1

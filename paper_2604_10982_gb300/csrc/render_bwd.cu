@@ -453,8 +453,11 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
                         const float dLda = Tj * sj - suffix * inv;
                         suffix = fmaf(w, sj, suffix);
                         Tc = Tj;
-                        vals[0] = w * gr;
-                        vals[1] = w * gg;
+                        // products in pairs where they share a factor (packed
+                        // multiplies, each rounded as the scalar one)
+                        const float2 c01 = __fmul2_rn(make_float2(w, w), make_float2(gr, gg));
+                        vals[0] = c01.x;
+                        vals[1] = c01.y;
                         vals[2] = w * gb;
                         if (LP && !e.clamped && e.filt) {
                             // rho = 2 |x - p0|^2: dL/dp0 = (-a / 2)(-4 (x - p0))
@@ -464,17 +467,21 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
                             vals[kSlots > 12 ? 12 : 0] = 2.0f * aa * e.dy;
                         } else if (!e.clamped) {
                             const float rq = rcp_approx(e.q2);
-                            const float u = e.q0 * rq, vv = e.q1 * rq;
-                            const float d2 = u * u + vv * vv;
+                            const float2 uv = __fmul2_rn(make_float2(e.q0, e.q1), make_float2(rq, rq)); // (u, v)
+                            const float d2 = uv.x * uv.x + uv.y * uv.y;
                             const float aa = dLda * e.alpha;
                             vals[3] = dLda * e.G;
-                            vals[4] = aa * u * u;
-                            vals[5] = aa * u * vv;
-                            vals[6] = aa * vv * vv;
-                            vals[7] = aa * u;
-                            vals[8] = aa * vv;
-                            vals[9] = aa * d2 * u;
-                            vals[10] = aa * d2 * vv;
+                            const float2 t = __fmul2_rn(make_float2(aa, aa), uv);          // a (u, v)
+                            const float2 tu = __fmul2_rn(make_float2(t.x, t.x), uv);       // a u (u, v)
+                            const float ad = aa * d2;
+                            const float2 td = __fmul2_rn(make_float2(ad, ad), uv);         // a d^2 (u, v)
+                            vals[4] = tu.x;
+                            vals[5] = tu.y;
+                            vals[6] = t.y * uv.y;
+                            vals[7] = t.x;
+                            vals[8] = t.y;
+                            vals[9] = td.x;
+                            vals[10] = td.y;
                         }
                     }
                     add_record_sums<LP>(vals, act, amask, lane, a.moments + static_cast<int64_t>(rid) * kM);
