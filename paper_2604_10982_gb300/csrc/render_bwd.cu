@@ -204,7 +204,12 @@ __device__ __forceinline__ void add_record_sums(float *vals, bool act, uint32_t 
 // (<gF, f_j> and dL/df) come from the per-pixel feature kernel instead of this
 // walk. CH (channel chunk) matters only for K = 0.
 // One tile (the whole CTA; P freshly initialised by thread 0 below).
-template <int KMAX, int DT, int CH, bool SAVED, bool LP, int TH>
+// NW (dense features with D = 16, e.g. the depth/normal table): each pixel's
+// g_F row is held in registers for the whole walk, and dL/df of a record is
+// summed over the warp by one 16-value transposing butterfly (one atomic per
+// channel) instead of the lanes-across-channels rounds, which would leave 28
+// of 32 lanes idle at 16 channels.
+template <int KMAX, int DT, int CH, bool SAVED, bool LP, int TH, bool NW = false>
 __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a, Pipe &P, int &s_maxlast,
                                          uint32_t tile)
 {
@@ -383,6 +388,12 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
     const float gg = inside ? a.g_rgb[fp.n_pix_total + pix] : 0.0f;
     const float gb = inside ? a.g_rgb[2 * fp.n_pix_total + pix] : 0.0f;
     const float gt = (inside && a.g_T) ? a.g_T[pix] : 0.0f;
+    // NW: the pixel's g_F row
+    float gfr[NW ? 16 : 1];
+    if constexpr (NW) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) gfr[c] = (inside && a.g_F) ? __ldg(a.g_F + pix * 16 + c) : 0.0f;
+    }
     float Tc = T;                    // T after the current surfel, walking back
     float suffix = __fmul_rn(T, gt); // sum_{k>j} omega_k s_k + T_final gT
     const int nbB = (maxlast + kPB - 1) / kPB;
@@ -435,6 +446,17 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
                                     sel = true;
                                     dot = kd[s];
                                 }
+                        } else if (NW && a.g_F && a.feat) {
+                            sel = true;
+                            float f[16];
+                            load_feat<DT, 16>(a.feat, sid, 16, 0, f, a.wide);
+                            if (a.fscale) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) dot = fmaf(gfr[c] * __ldg(a.fscale + c), f[c], dot);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) dot = fmaf(gfr[c], f[c], dot);
+                            }
                         } else if (a.g_F && a.feat) {
                             // dense features: every composited surfel is selected
                             sel = true;
@@ -485,7 +507,16 @@ __device__ __forceinline__ void bwd_tile(const FrameParams &fp, const BwdArgs &a
                         }
                     }
                     add_record_sums<LP>(vals, act, amask, lane, a.moments + static_cast<int64_t>(rid) * kM);
-                    if (want_feat) {
+                    if (NW && want_feat) {
+                        if (__any_sync(0xffffffffu, act && sel)) {
+                            float v[16];
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) v[c] = (act && sel) ? w * gfr[c] : 0.0f;
+                            // lane l ends with the total of channel l >> 1
+                            const float tot = warp_transpose_sum16(v, lane);
+                            if ((lane & 1) == 0 && tot != 0.0f) atomicAdd(a.g_feat + sid * 16 + (lane >> 1), tot);
+                        }
+                    } else if (want_feat) {
                         uint32_t selmask = __ballot_sync(0xffffffffu, act && sel);
                         if (selmask) {
                             // lane l owns channels [4l, 4l+4) (+128 for D=256) of the surfel's
@@ -746,7 +777,7 @@ __global__ void __launch_bounds__(pair_threads(TH), OCC)
 // OCC: CTAs per SM the kernel is built for (the launch shape the autotuner
 // picks). Tiles longest list first; the persistent launch (a.work set) fetches
 // further tiles from the context's counter as the forward kernel does.
-template <int KMAX, int DT, int CH, bool SAVED, bool LP, int OCC, int TH = 16>
+template <int KMAX, int DT, int CH, bool SAVED, bool LP, int OCC, int TH = 16, bool NW = false>
 __global__ void __launch_bounds__(pipe_threads(TH), OCC)
     render_bwd_kernel(const __grid_constant__ FrameParams fp, BwdArgs a)
 {
@@ -757,7 +788,7 @@ __global__ void __launch_bounds__(pipe_threads(TH), OCC)
     while (true) {
         const uint32_t tile = a.ranges[2 * fp.n_tiles_total + i];
         if (PSI_CHECK(tile < fp.n_tiles_total, kChkTile, a.status))
-            bwd_tile<KMAX, DT, CH, SAVED, LP, TH>(fp, a, P, s_maxlast, tile);
+            bwd_tile<KMAX, DT, CH, SAVED, LP, TH, NW>(fp, a, P, s_maxlast, tile);
         if (!a.work) break;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -895,6 +926,19 @@ cudaError_t launch_kcslo(const FrameParams &fp, const FeatView &f, const BwdArgs
     unsigned grid = fp.n_tiles_total;
     if (a.work) grid = persistent_grid(fp.n_tiles_total, OCC);
     constexpr int nt = pipe_threads(TH);
+    if constexpr (KMAX == 0 && CH == 16) {
+        // dense 16-channel tables: the register-held g_F row
+        if (f.data && f.dim == 16) {
+            switch (f.dtype) {
+            case PSI_BF16: render_bwd_kernel<0, PSI_BF16, 16, SAVED, LP, OCC, TH, true><<<grid, nt, 0, st>>>(fp, a); break;
+            case PSI_FP8_E4M3:
+                render_bwd_kernel<0, PSI_FP8_E4M3, 16, SAVED, LP, OCC, TH, true><<<grid, nt, 0, st>>>(fp, a);
+                break;
+            default: render_bwd_kernel<0, PSI_F32, 16, SAVED, LP, OCC, TH, true><<<grid, nt, 0, st>>>(fp, a); break;
+            }
+            return cudaGetLastError();
+        }
+    }
     switch (f.data ? f.dtype : PSI_F32) {
     case PSI_BF16: render_bwd_kernel<KMAX, PSI_BF16, CH, SAVED, LP, OCC, TH><<<grid, nt, 0, st>>>(fp, a); break;
     case PSI_FP8_E4M3:
