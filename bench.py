@@ -437,8 +437,10 @@ def run_psi(args):
         else:
             fns[i]()
 
-    def run_frame(f, evs=None, kev=None):
-        """evs: per-stage events (dict) or None; kev: the adjoint's kernel events."""
+    def run_frame(f, evs=None, kev=None, before_bwd=None):
+        """evs: per-stage events (dict) or None; kev: the adjoint's kernel events;
+        before_bwd: called just before the adjoint (the end-to-end loop waits
+        there for the frame's upstream gradients, which only the adjoint reads)."""
         fns = stage_fns(f)
         rec = (lambda name, s: evs[name].record(s)) if evs is not None else (lambda name, s: None)
         rec("start", main_s)
@@ -461,6 +463,8 @@ def run_psi(args):
             run_stage(f, "decode", fns)
             rec("dec1", side)
         main_s.wait_event(zero_done)
+        if before_bwd is not None:
+            before_bwd()
         if kev is not None:
             psi.psi_ctx_time_kernel(ctx, psi.KERNEL_BWD_FEAT, kev[0], kev[1])
             psi.psi_ctx_time_kernel(ctx, psi.KERNEL_BWD_WALK, kev[2], kev[3])
@@ -634,9 +638,8 @@ def run_psi(args):
             b = k & 1
             if k + 1 < args.e2e_steps:
                 h2d(k + 1)
-            main.wait_event(ev_ready[b])
             gC, gF, gT = bufs[b]  # the adjoint stage reads these names
-            run_frame(fidx(k))
+            run_frame(fidx(k), before_bwd=lambda ev=ev_ready[b]: main.wait_event(ev))
             ev_used[b].record(main)
             ids_h.copy_(ids, non_blocking=True)
             rgb_h.copy_(r.rgb, non_blocking=True)
@@ -649,8 +652,8 @@ def run_psi(args):
                "d2h_bytes_per_step": int(ids_h.numel() * 4 + rgb_h.numel() * 4),
                "h2d_ms_per_step": float(h2d_ms), "steps": int(args.e2e_steps),
                "what": "per step: upstream gradients copied from pinned host memory (side stream, double-buffered, "
-                       "overlapping the previous step), the frame (all stages), ids and RGB read back to pinned host "
-                       "memory"}
+                       "overlapping the previous step; the frame waits for them before its adjoint), the frame (all "
+                       "stages), ids and RGB read back to pinned host memory"}
 
     # ---- plain FP32 form (paper's Baseline row): SPHERE bounds, dense FP32 features
     plain = None
