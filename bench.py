@@ -602,14 +602,18 @@ def run_psi(args):
         rgb_h = torch.empty(3, r.n_pix, dtype=torch.float32).pin_memory()
         main = torch.cuda.current_stream(dev)
         copy_stream = torch.cuda.Stream(device=dev)
-        bufs = [(gC, gF, gT), (torch.empty_like(gC), torch.empty_like(gF), torch.empty_like(gT))]
-        ev_ready = [torch.cuda.Event() for _ in range(2)]
-        ev_used = [torch.cuda.Event() for _ in range(2)]
+        # three device buffers, copies issued two steps ahead: the copy stream
+        # never waits for the step that is still reading the previous buffer
+        NB = 3
+        bufs = [(gC, gF, gT)] + [(torch.empty_like(gC), torch.empty_like(gF), torch.empty_like(gT))
+                                 for _ in range(NB - 1)]
+        ev_ready = [torch.cuda.Event() for _ in range(NB)]
+        ev_used = [torch.cuda.Event() for _ in range(NB)]
 
         def h2d(k):
-            b = k & 1
-            if k >= 2:
-                copy_stream.wait_event(ev_used[b])  # step k-2 is done with this buffer
+            b = k % NB
+            if k >= NB:
+                copy_stream.wait_event(ev_used[b])  # step k-NB is done with this buffer
             with torch.cuda.stream(copy_stream):
                 for dst, src in zip(bufs[b], (gC_h, gF_h, gT_h)):
                     dst.copy_(src, non_blocking=True)
@@ -634,10 +638,12 @@ def run_psi(args):
         e0.record(main)
         copy_stream.wait_event(e0)
         h2d(0)
+        if args.e2e_steps > 1:
+            h2d(1)
         for k in range(args.e2e_steps):
-            b = k & 1
-            if k + 1 < args.e2e_steps:
-                h2d(k + 1)
+            b = k % NB
+            if k + 2 < args.e2e_steps:
+                h2d(k + 2)
             gC, gF, gT = bufs[b]  # the adjoint stage reads these names
             run_frame(fidx(k), before_bwd=lambda ev=ev_ready[b]: main.wait_event(ev))
             ev_used[b].record(main)
@@ -651,8 +657,8 @@ def run_psi(args):
                "h2d_bytes_per_step": int(gC_h.numel() * 4 + gF_h.numel() * 4 + gT_h.numel() * 4),
                "d2h_bytes_per_step": int(ids_h.numel() * 4 + rgb_h.numel() * 4),
                "h2d_ms_per_step": float(h2d_ms), "steps": int(args.e2e_steps),
-               "what": "per step: upstream gradients copied from pinned host memory (side stream, double-buffered, "
-                       "overlapping the previous step; the frame waits for them before its adjoint), the frame (all "
+               "what": "per step: upstream gradients copied from pinned host memory (side stream, three device "
+                       "buffers, issued two steps ahead; the frame waits for them before its adjoint), the frame (all "
                        "stages), ids and RGB read back to pinned host memory"}
 
     # ---- plain FP32 form (paper's Baseline row): SPHERE bounds, dense FP32 features
